@@ -622,9 +622,11 @@ static inline double clampd(double v, double lo, double hi) {
 /* One face in canonical order (L = lower id).  O10: d = x_R - x_L,
  * A = V_L psi_R(x_L) B_L d + V_R psi_L(x_R) B_R d with V = 1/n and
  * psi_b(x_a) = W(r, H_a) / n_a (zero outside H_a).  O11: s = H_L/(H_L+H_R),
- * v_f = v_L + s (v_R - v_L); W_L = W_L + g_L . (s d), W_R = W_R + g_R . ((s-1) d);
+ * v_f = v_L + s (v_R - v_L); W_L = W_L + g_L . (s d), W_R = W_R + g_R . (s_R (-d));
  * Hancock: + (dt/2) (-rho div v, -grad P / rho, -gamma P div v) with the
- * particle's own limited gradients; clamp each field to
+ * particle's own limited gradients (the face point seen from R is
+ * x_R + s_R (x_L - x_R) with s_R = H_R / (H_L + H_R), the same point);
+ * clamp each field to
  * [min(f_L, f_R), max(f_L, f_R)]; if rho or P <= 0 on a side use the
  * particle states.  O12: HLLC along n = A/|A| in the face frame; MFM rates
  * to L: dp = -P* A, dE = -P* (S* + v_f . n) |A|. */
@@ -657,8 +659,10 @@ int gzo_pair(const double* xL, double HL, double nL, const double* WL, const dou
     for (int a = 0; a < 3; ++a) vf[a] = WL[1 + a] + s * (WR[1 + a] - WL[1 + a]);
     if (Amag == 0.0) return 0;
     double nh[3] = {A[0] / Amag, A[1] / Amag, A[2] / Amag};
+    /* face point x_f = x_L + s d = x_R + s_R (x_L - x_R), s_R = H_R / (H_L + H_R) */
+    double sR = HR / (HL + HR);
     double sdL[3] = {s * d[0], s * d[1], s * d[2]};
-    double sdR[3] = {(s - 1.0) * d[0], (s - 1.0) * d[1], (s - 1.0) * d[2]};
+    double sdR[3] = {sR * -d[0], sR * -d[1], sR * -d[2]};
     double FL[5], FR[5];
     for (int q = 0; q < 5; ++q) {
         FL[q] = WL[q] + ((gL[q * 3 + 0] * sdL[0] + gL[q * 3 + 1] * sdL[1]) + gL[q * 3 + 2] * sdL[2]);
