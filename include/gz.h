@@ -1,0 +1,236 @@
+/*
+ * gz.h -- C ABI of the GB300 meshless finite-mass (MFM) hydrodynamics library.
+ *
+ * Method: GIZMO's Lagrangian mesh-free finite-volume Godunov scheme in its
+ * meshless finite-mass form (GIZMO public-release paper: "Hydrodynamics" item
+ * of the physics list, and the "Arbitrary (Moving) Meshes" section, where the
+ * mesh moves with the fluid), in a periodic unit box ("periodic ... boundary
+ * conditions" item) with a gamma-law equation of state and one global CFL
+ * timestep.  The paper prints no formula for the scheme; the readings used
+ * here are labelled O1..O14 and restated at each call below:
+ *
+ *   O1  minimum-image offsets d = x_j - x_i in the unit box
+ *   O2  cubic-spline kernel W(r, H) = 8/(pi H^3) w(r/H), support radius H
+ *   O3  neighbour set N_i = {j != i : r_ij < H_i}
+ *   O4  H_i solves (4 pi/3) H^3 n_i(H) = N_ngb (bracketed Newton)
+ *   O5  n_i = sum_{N_i + i} W(r_ij, H_i); V_i = 1/n_i; rho_i = m_i n_i
+ *   O6  psi_j(x_i) = W(r_ij, H_i) / n_i
+ *   O7  E_i = sum psi_j d d^T, B_i = E_i^-1
+ *   O8  least-squares gradients g = B_i sum (f_j - f_i) d psi_j
+ *   O9  per-particle limiter alpha_i (beta = 1, face point at s_ij = H_i/(H_i+H_j))
+ *   O10 flux pairs r < max(H_i, H_j); face area
+ *       A_ij = V_i psi_j(x_i) B_i d + V_j psi_i(x_j) B_j d
+ *   O11 linear reconstruction + Hancock half step + pairwise clamp
+ *   O12 HLLC (Davis wave speeds) in the face frame; MFM rates
+ *       dp_i/dt = -sum P* A_ij, dE_i/dt = -sum P* (S* + v_f . n) |A_ij|
+ *   O13 dt = cfl * min_i 2 V_i^(1/3) / max_j v_sig,ij
+ *   O14 kick, trapezoid drift, periodic wrap, u floor
+ *
+ * Conventions
+ *   - Every call returns a gz_status; no exception or abort crosses the ABI.
+ *     Calls are asynchronous on the context's CUDA stream; conditions found
+ *     on the device are recorded in a device status word read (with a stream
+ *     synchronisation) by gz_get_status.  gz_last_error gives host-side text.
+ *   - Particle arrays are device pointers owned by the caller, one contiguous
+ *     array per field (structure of arrays).  Their element type is float for
+ *     GZ_MIXED32 and double for GZ_FP64 (ids are always int64).  The library
+ *     never frees or keeps them beyond a call.  Outputs are written in the
+ *     caller's particle order; internal sorting is invisible.
+ *   - The context owns all scratch memory (sort buffers, cell ranges,
+ *     neighbour lists, gradients, rates) and frees it in gz_destroy.
+ *   - Boxes: a context holds nboxes independent periodic unit boxes; box b's
+ *     particles are the contiguous slice [sum_{c<b} counts[c], ...).  Every
+ *     box has its own cell grid and its own CFL timestep.
+ *   - Ids must be unique non-negative int64 (within each box); every pair
+ *     quantity is evaluated in the order (lower id, higher id), so both
+ *     particles of a pair receive bitwise-opposite rate contributions.
+ */
+#ifndef GZ_H
+#define GZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t gz_status;
+
+/* Return codes. */
+#define GZ_OK 0
+#define GZ_E_INVAL 1     /* invalid argument (null pointer, bad size, bad params) */
+#define GZ_E_NOMEM 2     /* device allocation failed                             */
+#define GZ_E_CUDA 3      /* a CUDA runtime call failed (text in gz_last_error)    */
+#define GZ_E_DEVICE 4    /* device status word has error bits set (gz_get_status) */
+
+/* Device status bits (gz_get_status).  Error bits: */
+#define GZ_S_HCONV (1u << 0)        /* h-iteration hit max_iter (O4)               */
+#define GZ_S_SINGULAR (1u << 1)     /* det(E) <= 0 or kappa > 1e8 (O7); B = 0 used  */
+#define GZ_S_NONFINITE (1u << 2)    /* non-finite input or output value            */
+#define GZ_S_NBR_OVERFLOW (1u << 3) /* a neighbour list exceeded its capacity       */
+#define GZ_S_HLIM (1u << 4)         /* support radius reached h_lim                 */
+/* Informational bits (counted, not errors): */
+#define GZ_S_FALLBACK (1u << 8)     /* first-order face states used (O11)           */
+#define GZ_S_PSTAR_NEG (1u << 9)    /* HLLC P* < 0 clamped to 0 (O12)               */
+#define GZ_S_UFLOOR (1u << 10)      /* u floored after the update (O14)             */
+#define GZ_S_KAPPA_FP64 (1u << 11)  /* E re-inverted in FP64 (kappa > kappa_max)    */
+#define GZ_S_ERROR_MASK 0xFFu
+
+/* Counter slots of gz_get_status. */
+#define GZ_C_HCONV 0
+#define GZ_C_SINGULAR 1
+#define GZ_C_NONFINITE 2
+#define GZ_C_NBR_OVERFLOW 3
+#define GZ_C_FALLBACK 4
+#define GZ_C_PSTAR_NEG 5
+#define GZ_C_UFLOOR 6
+#define GZ_C_KAPPA_FP64 7
+#define GZ_NCOUNTERS 8
+
+/* Precision modes. */
+#define GZ_FP64 0    /* every step in double                                          */
+#define GZ_MIXED32 1 /* float state and pair math; double for the Newton update of H,
+                        the E inversion when kappa > kappa_max, and the per-particle
+                        rate accumulation and update                                 */
+
+typedef struct {
+    double gamma;        /* adiabatic index (5/3)                                     */
+    double ngb;          /* effective neighbour number N_ngb (32)                     */
+    double tol;          /* h-iteration stops when |f| <= tol * ngb (1e-6)            */
+    double cfl;          /* CFL factor (0.2)                                          */
+    double kappa_max;    /* FP64 re-inversion threshold for cond(E) (100)            */
+    double beta;         /* limiter factor (1)                                        */
+    double u_floor_frac; /* floor = u_floor_frac * lower median of u at step start   */
+    double h_lim;        /* support radius stays below this (0.5)                    */
+    double cell_factor;  /* cell length = cell_factor * H0 of the box (1.0)          */
+    int32_t precision;   /* GZ_FP64 or GZ_MIXED32                                     */
+    int32_t hancock;     /* 1: half-step predictor on face states (1)                */
+    int32_t max_iter;    /* cap on f evaluations of the h-iteration (64)             */
+    int32_t max_ngb;     /* capacity of each particle's neighbour list (128)         */
+} gz_params;
+
+/* Structure-of-arrays particle set; every pointer is device memory with N
+ * elements (float or double per precision; id int64).  h is the support
+ * radius H (kernel is zero for r >= H). */
+typedef struct {
+    void* x;
+    void* y;
+    void* z;
+    void* vx;
+    void* vy;
+    void* vz;
+    void* m;
+    void* u; /* specific internal energy */
+    void* h;
+    const int64_t* id;
+} gz_particles;
+
+typedef struct gz_ctx gz_ctx;
+
+/* Fills *out with the defaults listed in gz_params.  Never fails for a
+ * non-null pointer. */
+gz_status gz_default_params(gz_params* out);
+
+/* Creates a context for nboxes boxes with counts[b] particles each (host
+ * array).  cuda_stream is a cudaStream_t (NULL = default stream); all work is
+ * enqueued on it.  Allocates all scratch on the current device.  Errors:
+ * GZ_E_INVAL (null out/counts/params, nboxes < 1, a count < 1, invalid
+ * params), GZ_E_NOMEM. */
+gz_status gz_create(const gz_params* params, int32_t nboxes, const int64_t* counts,
+                    void* cuda_stream, gz_ctx** out);
+
+/* Frees the context and its scratch (synchronises its stream). */
+gz_status gz_destroy(gz_ctx* ctx);
+
+/* O3-O5.  Reads x, y, z, h (h = initial guess of H) and id; solves the
+ * h-iteration for every particle and writes the converged H back into h,
+ * the kernel number density n into n_out, and the number of f evaluations
+ * into iters_out (int32).  n_out and iters_out may be NULL.  The neighbour
+ * lists of the final H are kept in the context (gz_get_neighbours). */
+gz_status gz_density(gz_ctx* ctx, gz_particles* p, void* n_out, int32_t* iters_out);
+
+/* O6-O9 with the given H (p->h) and n (device, N values): writes the
+ * limited gradients of (rho, vx, vy, vz, P) to grad_out as [15][N]
+ * (row = field*3 + axis) and B = E^-1 to B_out as [6][N] (xx, xy, xz, yy,
+ * yz, zz).  Either output may be NULL. */
+gz_status gz_gradients(gz_ctx* ctx, const gz_particles* p, const void* n, void* grad_out,
+                       void* B_out);
+
+/* O13 with the given H and n: writes the per-particle signal-speed step
+ * 2 V_i^(1/3)/max_j v_sig,ij into dt_i_out ([N], double, may be NULL) and
+ * cfl * min over each box into dt_box_out ([nboxes] doubles, device). */
+gz_status gz_timestep(gz_ctx* ctx, const gz_particles* p, const void* n, double* dt_i_out,
+                      double* dt_box_out);
+
+/* O10-O12 with the given H, n, limited gradients grad ([15][N]) and B
+ * ([6][N]) and half-step time dt (the Hancock predictor uses dt/2): writes
+ * dp/dt to dpdt ([3][N] doubles) and dE/dt to dEdt ([N] doubles). */
+gz_status gz_hydro_fluxes(gz_ctx* ctx, const gz_particles* p, const void* n, const void* grad,
+                          const void* B, double dt, double* dpdt, double* dEdt);
+
+/* One full step O4-O14 in place on p (x, y, z, vx, vy, vz, u, h updated;
+ * m and id read only).  dt_fixed > 0 uses that step for every box;
+ * otherwise each box takes its CFL step.  dt_used_dev (device, nboxes
+ * doubles, may be NULL) receives the steps used.  No host synchronisation. */
+gz_status gz_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev);
+
+/* Adjoint of one gz_step (all of O4-O14 with the step dt held fixed and
+ * neighbour sets frozen at their forward values).  p_start is the state the
+ * forward step started from (it is not modified); gbar_end holds dL/d(state
+ * after the step) for x, y, z, vx, vy, vz, u (m, h, id ignored; arrays in the
+ * working precision); gbar_start receives dL/d(state before the step) for
+ * x, y, z, vx, vy, vz, u and m.  dt is the step the forward used. */
+gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt,
+                           const gz_particles* gbar_end, gz_particles* gbar_start);
+
+/* Copies the neighbour lists of the last gz_density / gz_step: count_out
+ * ([N] int32, device) and, if ids_out is non-NULL, the neighbours' ids into
+ * ids_out ([cap][N] int64, slot-major, device; unused slots = -1).  Lists are
+ * in enumeration order, not sorted. */
+gz_status gz_get_neighbours(gz_ctx* ctx, int32_t* count_out, int64_t* ids_out, int32_t cap);
+
+/* Synchronises the context stream and returns the accumulated device status
+ * bits, the smallest particle id involved in an error (-1 if none) and, if
+ * counters is non-NULL, GZ_NCOUNTERS event counts.  reset != 0 clears them.
+ * Returns GZ_E_DEVICE when any error bit is set, GZ_E_CUDA on a CUDA error. */
+gz_status gz_get_status(gz_ctx* ctx, uint32_t* bits, int64_t* first_bad_id, int64_t* counters,
+                        int32_t reset);
+
+/* Pass indices of the per-pass profile. */
+#define GZ_PASS_SORT 0      /* S1 binning, radix sort, permutation            */
+#define GZ_PASS_DENSITY 1   /* S2 h-iteration and neighbour lists             */
+#define GZ_PASS_LISTS 2     /* neighbour lists for a given H                  */
+#define GZ_PASS_REVERSE 3   /* reverse flux pairs                             */
+#define GZ_PASS_PRIM 4      /* primitives rho, P, c                           */
+#define GZ_PASS_GRAD 5      /* S3 gradients, limiter (+ S5 signal speed)      */
+#define GZ_PASS_FLUX 6      /* S4 pairwise HLLC fluxes                        */
+#define GZ_PASS_UPDATE 7    /* S6 kick, drift, wrap, u floor (+ dt finalise) */
+#define GZ_NPASSES 8
+
+/* Host-side facts about the context: info[0] kernel launches issued so far,
+ * info[1] N, info[2] nboxes, info[3] cells of all boxes, info[4] neighbour
+ * list capacity, info[5] reverse list capacity.  n = entries wanted (<= 6). */
+gz_status gz_get_info(gz_ctx* ctx, int64_t* info, int32_t n);
+
+/* Ordered flux pairs sum_i |P_i| of the last pass that built pair lists
+ * (device reduction; synchronises the stream). */
+gz_status gz_pair_count(gz_ctx* ctx, int64_t* ordered_pairs);
+
+/* enable != 0: record CUDA events on the context stream around every pass of
+ * subsequent calls (a few microseconds per pass).  gz_profile_read
+ * synchronises and returns the accumulated milliseconds and invocation
+ * counts per pass (GZ_NPASSES entries each); reset != 0 clears them. */
+gz_status gz_profile_enable(gz_ctx* ctx, int32_t enable);
+gz_status gz_profile_read(gz_ctx* ctx, double* ms, int64_t* calls, int32_t reset);
+
+/* Text of the last host-side error of this context ("" if none). */
+const char* gz_last_error(gz_ctx* ctx);
+
+/* Library version string. */
+const char* gz_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GZ_H */

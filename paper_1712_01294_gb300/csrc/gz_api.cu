@@ -1,0 +1,518 @@
+// C ABI of the library (declared in include/gz.h): context management and
+// the orchestration of the passes on the context's stream.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "gz_launch.cuh"
+
+using namespace gz;
+
+struct gz_ctx {
+    Ctx c;
+};
+
+namespace {
+
+const char* kVersion = "gz-mfm 0.1 (sm_103a)";
+
+gz_status fail(gz_ctx* ctx, gz_status code, const std::string& msg) {
+    if (ctx) ctx->c.err = msg;
+    return code;
+}
+
+gz_status cuda_check(gz_ctx* ctx, cudaError_t e, const char* where) {
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(ctx, GZ_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return GZ_OK;
+}
+
+bool params_ok(const gz_params* p, std::string& why) {
+    if (!(p->gamma > 1.0)) return why = "gamma must be > 1", false;
+    if (!(p->ngb >= 1.0)) return why = "ngb must be >= 1", false;
+    if (!(p->tol > 0.0)) return why = "tol must be > 0", false;
+    if (!(p->cfl > 0.0)) return why = "cfl must be > 0", false;
+    if (!(p->kappa_max > 0.0)) return why = "kappa_max must be > 0", false;
+    if (!(p->beta > 0.0)) return why = "beta must be > 0", false;
+    if (!(p->u_floor_frac >= 0.0)) return why = "u_floor_frac must be >= 0", false;
+    if (!(p->h_lim > 0.0 && p->h_lim <= 0.5)) return why = "h_lim must be in (0, 0.5]", false;
+    if (!(p->cell_factor > 0.0)) return why = "cell_factor must be > 0", false;
+    if (p->precision != GZ_FP64 && p->precision != GZ_MIXED32)
+        return why = "precision must be GZ_FP64 or GZ_MIXED32", false;
+    if (p->max_iter < 1) return why = "max_iter must be >= 1", false;
+    if (p->max_ngb < 8 || p->max_ngb > 4096) return why = "max_ngb must be in [8, 4096]", false;
+    return true;
+}
+
+int ceil_log2(long long v) {
+    int b = 0;
+    while ((1ll << b) < v) ++b;
+    return b;
+}
+
+cudaEvent_t take_event(Ctx& c) {
+    if (!c.ev_pool.empty()) {
+        cudaEvent_t e = c.ev_pool.back();
+        c.ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Records an event pair around one pass when profiling is on.
+struct Pass {
+    Ctx& c;
+    int id;
+    cudaEvent_t a = nullptr;
+    Pass(Ctx& c_, int id_) : c(c_), id(id_) {
+        if (c.prof) {
+            a = take_event(c);
+            cudaEventRecord(a, c.stream);
+        }
+    }
+    ~Pass() {
+        if (c.prof && a) {
+            cudaEvent_t b = take_event(c);
+            cudaEventRecord(b, c.stream);
+            c.pending.push_back({id, a, b});
+        }
+    }
+};
+
+gz_status check_particles(gz_ctx* ctx, const gz_particles* p, bool need_vel) {
+    if (!p) return fail(ctx, GZ_E_INVAL, "null particle set");
+    if (!p->x || !p->y || !p->z || !p->h || !p->id || !p->m || !p->u)
+        return fail(ctx, GZ_E_INVAL, "null particle array");
+    if (need_vel && (!p->vx || !p->vy || !p->vz)) return fail(ctx, GZ_E_INVAL, "null velocity array");
+    return GZ_OK;
+}
+
+template <typename T>
+gz_status do_density(gz_ctx* ctx, gz_particles* p, void* n_out, int32_t* iters_out) {
+    Ctx& c = ctx->c;
+    cudaError_t e;
+    {
+        Pass t(c, GZ_PASS_SORT);
+        e = sort_and_bin<T>(c, *p, nullptr);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_DENSITY);
+        e = run_density<T>(c);
+    }
+    if (e == cudaSuccess) e = unpermute_T<T>(c, (const T*)c.sh, (T*)p->h, 1);
+    if (e == cudaSuccess && n_out) e = unpermute_T<T>(c, (const T*)c.sn, (T*)n_out, 1);
+    if (e == cudaSuccess && iters_out) e = unpermute_i(c, c.iters, iters_out);
+    c.nbr_valid = 1;
+    return cuda_check(ctx, e, "gz_density");
+}
+
+template <typename T>
+gz_status prepare_given(gz_ctx* ctx, const gz_particles* p, const void* n, bool reverse) {
+    Ctx& c = ctx->c;
+    cudaError_t e;
+    {
+        Pass t(c, GZ_PASS_SORT);
+        e = sort_and_bin<T>(c, *p, n);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_LISTS);
+        e = run_build_lists<T>(c);
+    }
+    if (e == cudaSuccess && reverse) {
+        Pass t(c, GZ_PASS_REVERSE);
+        e = run_reverse<T>(c);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_PRIM);
+        e = run_prim<T>(c);
+    }
+    c.nbr_valid = 1;
+    return cuda_check(ctx, e, "prepare");
+}
+
+template <typename T>
+gz_status do_gradients(gz_ctx* ctx, const gz_particles* p, const void* n, void* grad_out, void* B_out) {
+    gz_status s = prepare_given<T>(ctx, p, n, false);
+    if (s) return s;
+    Ctx& c = ctx->c;
+    cudaError_t e;
+    {
+        Pass t(c, GZ_PASS_GRAD);
+        e = run_gradients<T>(c, false);
+    }
+    if (e == cudaSuccess) e = run_grad_out<T>(c, (T*)grad_out, (T*)B_out);
+    return cuda_check(ctx, e, "gz_gradients");
+}
+
+template <typename T>
+gz_status do_timestep(gz_ctx* ctx, const gz_particles* p, const void* n, double* dt_i, double* dt_box) {
+    gz_status s = prepare_given<T>(ctx, p, n, true);
+    if (s) return s;
+    Ctx& c = ctx->c;
+    cudaError_t e = run_gradients<T>(c, true);
+    if (e == cudaSuccess && dt_i) e = unpermute_d(c, c.dti, dt_i, 1);
+    if (e == cudaSuccess && dt_box) e = run_dt_out(c, dt_box);
+    return cuda_check(ctx, e, "gz_timestep");
+}
+
+template <typename T>
+gz_status do_fluxes(gz_ctx* ctx, const gz_particles* p, const void* n, const void* grad,
+                    const void* B, double dt, double* dpdt, double* dEdt) {
+    gz_status s = prepare_given<T>(ctx, p, n, true);
+    if (s) return s;
+    Ctx& c = ctx->c;
+    cudaError_t e = run_pack_given<T>(c, (const T*)grad, (const T*)B);
+    if (e == cudaSuccess) e = run_dt_set(c, dt);
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_FLUX);
+        e = run_fluxes<T>(c);
+    }
+    if (e == cudaSuccess) e = unpermute_d(c, c.dpdt, dpdt, 3);
+    if (e == cudaSuccess) e = unpermute_d(c, c.dEdt, dEdt, 1);
+    return cuda_check(ctx, e, "gz_hydro_fluxes");
+}
+
+template <typename T>
+gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev) {
+    Ctx& c = ctx->c;
+    cudaError_t e;
+    {
+        Pass t(c, GZ_PASS_SORT);
+        e = sort_and_bin<T>(c, *p, nullptr);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_DENSITY);
+        e = run_density<T>(c);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_REVERSE);
+        e = run_reverse<T>(c);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_PRIM);
+        e = run_prim<T>(c);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_GRAD);
+        e = run_gradients<T>(c, !(dt_fixed > 0.0));
+        if (e == cudaSuccess) e = run_dt_finalize(c, dt_fixed, dt_used_dev);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_FLUX);
+        e = run_fluxes<T>(c);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_UPDATE);
+        e = run_update<T>(c, *p);
+    }
+    c.nbr_valid = 1;
+    return cuda_check(ctx, e, "gz_step");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gz_version(void) { return kVersion; }
+
+gz_status gz_default_params(gz_params* out) {
+    if (!out) return GZ_E_INVAL;
+    memset(out, 0, sizeof(*out));
+    out->gamma = 5.0 / 3.0;
+    out->ngb = 32.0;
+    out->tol = 1e-6;
+    out->cfl = 0.2;
+    out->kappa_max = 100.0;
+    out->beta = 1.0;
+    out->u_floor_frac = 1e-10;
+    out->h_lim = 0.5;
+    out->cell_factor = 1.0;
+    out->precision = GZ_MIXED32;
+    out->hancock = 1;
+    out->max_iter = 64;
+    out->max_ngb = 128;
+    return GZ_OK;
+}
+
+gz_status gz_create(const gz_params* params, int32_t nboxes, const int64_t* counts,
+                    void* cuda_stream, gz_ctx** out) {
+    if (!out || !params || !counts || nboxes < 1) return GZ_E_INVAL;
+    *out = nullptr;
+    std::string why;
+    if (!params_ok(params, why)) return GZ_E_INVAL;
+    long long N = 0;
+    for (int b = 0; b < nboxes; ++b) {
+        if (counts[b] < 1) return GZ_E_INVAL;
+        N += counts[b];
+    }
+    if (N >= (1ll << 31) - 1) return GZ_E_INVAL;
+    gz_ctx* ctx = new (std::nothrow) gz_ctx();
+    if (!ctx) return GZ_E_NOMEM;
+    Ctx& c = ctx->c;
+    c.params = *params;
+    c.precision = params->precision;
+    c.N = (int)N;
+    c.nboxes = nboxes;
+    c.counts.assign(counts, counts + nboxes);
+    c.stream = (cudaStream_t)cuda_stream;
+    c.cap = params->max_ngb;
+    c.launches = 0;
+    c.prof = 0;
+    for (int k = 0; k < GZ_NPASSES; ++k) {
+        c.prof_ms[k] = 0.0;
+        c.prof_calls[k] = 0;
+    }
+    c.rcap = std::max(8, params->max_ngb / 2);
+    // per-box cell grids: cell length ~ cell_factor * H0 of the box
+    int maxnc = 1;
+    long long cells = 0;
+    int first = 0;
+    c.hboxes.resize(nboxes);
+    for (int b = 0; b < nboxes; ++b) {
+        const double H0 = cbrt(3.0 * params->ngb / (4.0 * M_PI * (double)counts[b]));
+        double f = floor(1.0 / (params->cell_factor * H0));
+        int nc = f < 1.0 ? 1 : (f > 512.0 ? 512 : (int)f);
+        c.hboxes[b].nc = nc;
+        c.hboxes[b].cell_off = (int)cells;
+        c.hboxes[b].first = first;
+        c.hboxes[b].count = (int)counts[b];
+        first += (int)counts[b];
+        cells += (long long)nc * nc * nc;
+        maxnc = std::max(maxnc, nc);
+    }
+    if (cells >= (1ll << 30)) {
+        delete ctx;
+        return GZ_E_INVAL;
+    }
+    c.total_cells = (int)cells;
+    c.cbits = ceil_log2(maxnc);
+    c.box_bits = ceil_log2(nboxes);
+    if (3 * c.cbits + c.box_bits > 32) {
+        delete ctx;
+        return GZ_E_INVAL;
+    }
+    // one arena for all scratch
+    const size_t Nz = (size_t)N;
+    const size_t sz = params->precision == GZ_FP64 ? 8 : 4;
+    const int nblk = (int)((N + 4095) / 4096);
+    c.hist_len = 256 * nblk;
+    struct Item {
+        void** ptr;
+        size_t bytes;
+    };
+    std::vector<Item> items = {
+        {(void**)&c.keys, 4 * Nz},        {(void**)&c.keys_alt, 4 * Nz},
+        {(void**)&c.vals, 4 * Nz},        {(void**)&c.vals_alt, 4 * Nz},
+        {(void**)&c.hist, 4 * (size_t)c.hist_len},
+        {(void**)&c.box_of, 4 * Nz},      {(void**)&c.boxes, sizeof(BoxInfo) * (size_t)nboxes},
+        {(void**)&c.cells, sizeof(int2) * (size_t)cells},
+        {(void**)&c.sx, sz * Nz},         {(void**)&c.sy, sz * Nz},
+        {(void**)&c.sz, sz * Nz},         {(void**)&c.svx, sz * Nz},
+        {(void**)&c.svy, sz * Nz},        {(void**)&c.svz, sz * Nz},
+        {(void**)&c.sm, sz * Nz},         {(void**)&c.su, sz * Nz},
+        {(void**)&c.sh, sz * Nz},         {(void**)&c.sn, sz * Nz},
+        {(void**)&c.srho, sz * Nz},       {(void**)&c.sP, sz * Nz},
+        {(void**)&c.sc, sz * Nz},         {(void**)&c.sid, 8 * Nz},
+        {(void**)&c.sbox, 4 * Nz},        {(void**)&c.iters, 4 * Nz},
+        {(void**)&c.ncount, 4 * Nz},      {(void**)&c.nbr, 4 * Nz * (size_t)c.cap},
+        {(void**)&c.rcount, 4 * Nz},      {(void**)&c.rnbr, 4 * Nz * (size_t)c.rcap},
+        {(void**)&c.rec, sz * Nz * kRecord},
+        {(void**)&c.dpdt, 8 * 3 * Nz},    {(void**)&c.dEdt, 8 * Nz},
+        {(void**)&c.dti, 8 * Nz},         {(void**)&c.dt_box, 8 * (size_t)nboxes},
+        {(void**)&c.dt_use, 8 * (size_t)nboxes},
+        {(void**)&c.box_hits, 4 * (size_t)nboxes},
+        {(void**)&c.status, sizeof(DevStatus)},
+        {(void**)&c.pairs_dev, sizeof(long long)},
+    };
+    size_t total = 0;
+    for (auto& it : items) total += (it.bytes + 255) & ~(size_t)255;
+    c.arena_bytes = total;
+    if (cudaMalloc(&c.arena, total) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return GZ_E_NOMEM;
+    }
+    char* base = (char*)c.arena;
+    for (auto& it : items) {
+        *it.ptr = base;
+        base += (it.bytes + 255) & ~(size_t)255;
+    }
+    std::vector<int> box_of(Nz);
+    for (int b = 0; b < nboxes; ++b)
+        for (int k = 0; k < c.hboxes[b].count; ++k) box_of[c.hboxes[b].first + k] = b;
+    cudaError_t e = cudaMemcpyAsync(c.box_of, box_of.data(), 4 * Nz, cudaMemcpyHostToDevice, c.stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c.boxes, c.hboxes.data(), sizeof(BoxInfo) * nboxes, cudaMemcpyHostToDevice,
+                            c.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c.status, 0, sizeof(DevStatus), c.stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(&c.status->first_bad_id, 0xFF, sizeof(unsigned long long), c.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c.ncount, 0, 4 * Nz, c.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c.rcount, 0, 4 * Nz, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);  // host vectors go out of scope
+    if (e != cudaSuccess) {
+        cudaFree(c.arena);
+        delete ctx;
+        return GZ_E_CUDA;
+    }
+    *out = ctx;
+    return GZ_OK;
+}
+
+gz_status gz_destroy(gz_ctx* ctx) {
+    if (!ctx) return GZ_E_INVAL;
+    cudaStreamSynchronize(ctx->c.stream);
+    for (auto& pe : ctx->c.pending) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    for (auto ev : ctx->c.ev_pool) cudaEventDestroy(ev);
+    cudaFree(ctx->c.arena);
+    delete ctx;
+    return GZ_OK;
+}
+
+#define GZ_DISPATCH(call_f, call_d) \
+    (ctx->c.precision == GZ_FP64 ? (call_d) : (call_f))
+
+gz_status gz_density(gz_ctx* ctx, gz_particles* p, void* n_out, int32_t* iters_out) {
+    if (!ctx) return GZ_E_INVAL;
+    if (gz_status s = check_particles(ctx, p, false)) return s;
+    return GZ_DISPATCH(do_density<float>(ctx, p, n_out, iters_out),
+                       do_density<double>(ctx, p, n_out, iters_out));
+}
+
+gz_status gz_gradients(gz_ctx* ctx, const gz_particles* p, const void* n, void* grad_out, void* B_out) {
+    if (!ctx) return GZ_E_INVAL;
+    if (gz_status s = check_particles(ctx, p, true)) return s;
+    if (!n) return fail(ctx, GZ_E_INVAL, "null n");
+    return GZ_DISPATCH(do_gradients<float>(ctx, p, n, grad_out, B_out),
+                       do_gradients<double>(ctx, p, n, grad_out, B_out));
+}
+
+gz_status gz_timestep(gz_ctx* ctx, const gz_particles* p, const void* n, double* dt_i_out,
+                      double* dt_box_out) {
+    if (!ctx) return GZ_E_INVAL;
+    if (gz_status s = check_particles(ctx, p, true)) return s;
+    if (!n) return fail(ctx, GZ_E_INVAL, "null n");
+    return GZ_DISPATCH(do_timestep<float>(ctx, p, n, dt_i_out, dt_box_out),
+                       do_timestep<double>(ctx, p, n, dt_i_out, dt_box_out));
+}
+
+gz_status gz_hydro_fluxes(gz_ctx* ctx, const gz_particles* p, const void* n, const void* grad,
+                          const void* B, double dt, double* dpdt, double* dEdt) {
+    if (!ctx) return GZ_E_INVAL;
+    if (gz_status s = check_particles(ctx, p, true)) return s;
+    if (!n || !grad || !B || !dpdt || !dEdt) return fail(ctx, GZ_E_INVAL, "null input/output");
+    if (!(dt >= 0.0) || !isfinite(dt)) return fail(ctx, GZ_E_INVAL, "dt must be finite and >= 0");
+    return GZ_DISPATCH(do_fluxes<float>(ctx, p, n, grad, B, dt, dpdt, dEdt),
+                       do_fluxes<double>(ctx, p, n, grad, B, dt, dpdt, dEdt));
+}
+
+gz_status gz_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev) {
+    if (!ctx) return GZ_E_INVAL;
+    if (gz_status s = check_particles(ctx, p, true)) return s;
+    if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
+    return GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev),
+                       do_step<double>(ctx, p, dt_fixed, dt_used_dev));
+}
+
+gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt,
+                           const gz_particles* gbar_end, gz_particles* gbar_start) {
+    if (!ctx) return GZ_E_INVAL;
+    (void)p_start;
+    (void)dt;
+    (void)gbar_end;
+    (void)gbar_start;
+    return fail(ctx, GZ_E_INVAL, "gz_step_backward: not available in this build");
+}
+
+gz_status gz_get_neighbours(gz_ctx* ctx, int32_t* count_out, int64_t* ids_out, int32_t cap) {
+    if (!ctx || !count_out || cap < 0) return GZ_E_INVAL;
+    if (!ctx->c.nbr_valid) return fail(ctx, GZ_E_INVAL, "no neighbour lists yet");
+    return cuda_check(ctx, run_get_neighbours(ctx->c, count_out, ids_out, cap), "gz_get_neighbours");
+}
+
+gz_status gz_get_status(gz_ctx* ctx, uint32_t* bits, int64_t* first_bad_id, int64_t* counters,
+                        int32_t reset) {
+    if (!ctx) return GZ_E_INVAL;
+    Ctx& c = ctx->c;
+    DevStatus h;
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&h, c.status, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(ctx, GZ_E_CUDA, std::string("gz_get_status: ") + cudaGetErrorString(e));
+    if (bits) *bits = h.bits;
+    if (first_bad_id) *first_bad_id = h.first_bad_id == ~0ull ? -1 : (int64_t)h.first_bad_id;
+    if (counters)
+        for (int k = 0; k < GZ_NCOUNTERS; ++k) counters[k] = (int64_t)h.counters[k];
+    if (reset) {
+        e = cudaMemsetAsync(c.status, 0, sizeof(DevStatus), c.stream);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(&c.status->first_bad_id, 0xFF, sizeof(unsigned long long), c.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+        if (e != cudaSuccess) return fail(ctx, GZ_E_CUDA, "gz_get_status reset failed");
+    }
+    return (h.bits & GZ_S_ERROR_MASK) ? GZ_E_DEVICE : GZ_OK;
+}
+
+const char* gz_last_error(gz_ctx* ctx) { return ctx ? ctx->c.err.c_str() : ""; }
+
+gz_status gz_get_info(gz_ctx* ctx, int64_t* info, int32_t n) {
+    if (!ctx || !info || n < 0 || n > 6) return GZ_E_INVAL;
+    const Ctx& c = ctx->c;
+    const int64_t v[6] = {c.launches, c.N, c.nboxes, c.total_cells, c.cap, c.rcap};
+    for (int k = 0; k < n; ++k) info[k] = v[k];
+    return GZ_OK;
+}
+
+gz_status gz_pair_count(gz_ctx* ctx, int64_t* ordered_pairs) {
+    if (!ctx || !ordered_pairs) return GZ_E_INVAL;
+    Ctx& c = ctx->c;
+    if (!c.nbr_valid) return fail(ctx, GZ_E_INVAL, "no pair lists yet");
+    long long h = 0;
+    cudaError_t e = run_pair_count(c, c.pairs_dev);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, c.pairs_dev, sizeof(h), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return fail(ctx, GZ_E_CUDA, std::string("gz_pair_count: ") + cudaGetErrorString(e));
+    *ordered_pairs = h;
+    return GZ_OK;
+}
+
+gz_status gz_profile_enable(gz_ctx* ctx, int32_t enable) {
+    if (!ctx) return GZ_E_INVAL;
+    ctx->c.prof = enable ? 1 : 0;
+    return GZ_OK;
+}
+
+gz_status gz_profile_read(gz_ctx* ctx, double* ms, int64_t* calls, int32_t reset) {
+    if (!ctx) return GZ_E_INVAL;
+    Ctx& c = ctx->c;
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return fail(ctx, GZ_E_CUDA, std::string("gz_profile_read: ") + cudaGetErrorString(e));
+    for (auto& pe : c.pending) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, pe.a, pe.b) == cudaSuccess) {
+            c.prof_ms[pe.pass] += t;
+            c.prof_calls[pe.pass] += 1;
+        }
+        c.ev_pool.push_back(pe.a);
+        c.ev_pool.push_back(pe.b);
+    }
+    c.pending.clear();
+    for (int k = 0; k < GZ_NPASSES; ++k) {
+        if (ms) ms[k] = c.prof_ms[k];
+        if (calls) calls[k] = c.prof_calls[k];
+        if (reset) {
+            c.prof_ms[k] = 0.0;
+            c.prof_calls[k] = 0;
+        }
+    }
+    return GZ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,966 @@
+// Hydro passes of the MFM step in sorted particle order (steps S2-S6).
+// One thread per particle; neighbour lists are slot-major ([slot][N]) so a
+// warp's accesses to slot k are coalesced.  Every pair quantity that mixes
+// both particles of a pair is either symmetric in its operands or evaluated
+// after ordering the pair by id, so both particles get bitwise-opposite
+// contributions (no atomics on rates).
+#include <type_traits>
+
+#include "gz_launch.cuh"
+
+namespace gz {
+
+namespace {
+
+inline int blocks(int n, int t) { return (n + t - 1) / t; }
+
+// Kahan-compensated sum for FP32 neighbour sums; plain sum in FP64.
+template <typename T>
+struct Acc {
+    T s = T(0);
+    __device__ __forceinline__ void add(T v) { s += v; }
+    __device__ __forceinline__ double value() const { return (double)s; }
+};
+template <>
+struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        float y = __fsub_rn(v, c);
+        float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
+// --------------------------------------------------------------- O4 / O5
+// Bracketed Newton iteration on f(H) = (4 pi/3) H^3 n(H) - N_ngb, written as
+// (32/3)(1 + sum_j w(q_j)) - N_ngb with f' = (32/3) sum_j (-w'(q_j)) q_j / H.
+// The neighbour list of each evaluation is written as it is found; the last
+// evaluation's list (that of the returned H) is the one that remains.
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_density(int N, Sorted<T> s, Grid g, KParams p, unsigned* __restrict__ nbr,
+              int* __restrict__ ncount, int* __restrict__ iters, DevStatus* st) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const BoxInfo bx = g.boxes[s.box[i]];
+    const T xi = s.x[i], yi = s.y[i], zi = s.z[i];
+    double H = (double)s.h[i];
+    if (!(H > 0.0) || !(H < p.h_lim)) {
+        set_status(st, GZ_S_NONFINITE, GZ_C_NONFINITE, s.id[i]);
+        H = cbrt(3.0 * p.ngb / (4.0 * kPi * (double)bx.count));
+        if (!(H < p.h_lim)) H = 0.5 * p.h_lim;
+    }
+    const double C = 32.0 / 3.0;
+    double lo = 0.0, hi = 0.0, S = 0.0, Hev = H;
+    bool has_lo = false, has_hi = false, conv = false, clamped = false;
+    int it, cnt = 0;
+    for (it = 1; it <= p.max_iter; ++it) {
+        const T Ht = (T)H;
+        const T H2 = Ht * Ht;
+        const T iH = T(1) / Ht;
+        Acc<T> sw;
+        T sd = T(0);
+        int c = 0;
+        for_candidates<T>(g, bx, s.x, s.y, s.z, i, xi, yi, zi, Ht,
+                          [&](int j, T, T, T, T r2) {
+                              if (r2 < H2) {
+                                  const T q = sqrt(r2) * iH;
+                                  sw.add(kern_w(q));
+                                  sd += -kern_dw(q) * q;
+                                  if (c < p.cap) nbr[(size_t)c * N + i] = (unsigned)j;
+                                  ++c;
+                              }
+                          });
+        cnt = c;
+        S = sw.value();
+        Hev = (double)Ht;
+        const double f = C * (1.0 + S) - p.ngb;
+        const double fp = C * (double)sd / Hev;
+        if (fabs(f) <= p.tol * p.ngb) {
+            conv = true;
+            break;
+        }
+        if (it == p.max_iter) break;
+        if (f < 0.0) {
+            lo = Hev;
+            has_lo = true;
+        } else {
+            hi = Hev;
+            has_hi = true;
+        }
+        const double lo_eff = has_lo ? lo : 0.5 * Hev;
+        const double hi_eff = has_hi ? hi : 2.0 * Hev;
+        double Hn = 0.0;
+        bool ok = false;
+        if (fp > 0.0) {
+            Hn = Hev - f / fp;
+            ok = (Hn > lo_eff) && (Hn < hi_eff);
+        }
+        if (!ok) Hn = (has_lo && has_hi) ? 0.5 * (lo + hi) : (f < 0.0 ? 2.0 * Hev : 0.5 * Hev);
+        if (Hn >= p.h_lim) {
+            Hn = 0.5 * (Hev + p.h_lim);
+            clamped = true;
+        }
+        H = Hn;
+    }
+    if (it > p.max_iter) it = p.max_iter;
+    s.h[i] = (T)Hev;
+    s.n[i] = (T)(8.0 * (1.0 + S) / (kPi * Hev * Hev * Hev));
+    iters[i] = it;
+    ncount[i] = cnt;
+    if (!conv) {
+        set_status(st, GZ_S_HCONV, GZ_C_HCONV, s.id[i]);
+        if (clamped) atomicOr(&st->bits, GZ_S_HLIM);
+    }
+    if (cnt > p.cap) set_status(st, GZ_S_NBR_OVERFLOW, GZ_C_NBR_OVERFLOW, s.id[i]);
+}
+
+// Neighbour lists N_i = {j : r_ij < H_i} for given H (O3).
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_lists(int N, Sorted<T> s, Grid g, KParams p, unsigned* __restrict__ nbr,
+            int* __restrict__ ncount, DevStatus* st) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const BoxInfo bx = g.boxes[s.box[i]];
+    const T Hi = s.h[i];
+    const T H2 = Hi * Hi;
+    int c = 0;
+    for_candidates<T>(g, bx, s.x, s.y, s.z, i, s.x[i], s.y[i], s.z[i], Hi,
+                      [&](int j, T, T, T, T r2) {
+                          if (r2 < H2) {
+                              if (c < p.cap) nbr[(size_t)c * N + i] = (unsigned)j;
+                              ++c;
+                          }
+                      });
+    ncount[i] = c;
+    if (c > p.cap) set_status(st, GZ_S_NBR_OVERFLOW, GZ_C_NBR_OVERFLOW, s.id[i]);
+}
+
+// Reverse pairs (O10): j in N_i with r_ij >= H_j is appended to j's list.
+template <typename T>
+__global__ void k_reverse(int N, Sorted<T> s, KParams p, const unsigned* __restrict__ nbr,
+                          const int* __restrict__ ncount, int* __restrict__ rcount,
+                          unsigned* __restrict__ rnbr, DevStatus* st) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const T xi = s.x[i], yi = s.y[i], zi = s.z[i];
+    const T xim1 = xi - T(1), yim1 = yi - T(1), zim1 = zi - T(1);
+    const int cnt = min(ncount[i], p.cap);
+    for (int k = 0; k < cnt; ++k) {
+        const int j = (int)nbr[(size_t)k * N + i];
+        const T Hj = s.h[j];
+        const T dx = mi_diff(s.x[j], xi, xim1), dy = mi_diff(s.y[j], yi, yim1),
+                dz = mi_diff(s.z[j], zi, zim1);
+        const T r2 = sep2(dx, dy, dz);
+        if (!(r2 < Hj * Hj)) {
+            const int slot = atomicAdd(&rcount[j], 1);
+            if (slot < p.rcap)
+                rnbr[(size_t)slot * N + j] = (unsigned)i;
+            else
+                set_status(st, GZ_S_NBR_OVERFLOW, GZ_C_NBR_OVERFLOW, s.id[j]);
+        }
+    }
+}
+
+// Orders each reverse list by sorted index so the flux sums are deterministic.
+__global__ void k_sort_rev(int N, const int* __restrict__ rcount, unsigned* __restrict__ rnbr,
+                           int rcap) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int n = min(rcount[i], rcap);
+    for (int a = 1; a < n; ++a) {
+        const unsigned v = rnbr[(size_t)a * N + i];
+        int b = a - 1;
+        while (b >= 0 && rnbr[(size_t)b * N + i] > v) {
+            rnbr[(size_t)(b + 1) * N + i] = rnbr[(size_t)b * N + i];
+            --b;
+        }
+        rnbr[(size_t)(b + 1) * N + i] = v;
+    }
+}
+
+// O5 primitives: rho = m n, P = (gamma - 1) rho u, c = sqrt(gamma P / rho).
+template <typename T>
+__global__ void k_prim(int N, Sorted<T> s, KParams p, DevStatus* st) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const T g = (T)p.gamma;
+    const T rho = s.m[i] * s.n[i];
+    const T P = (g - T(1)) * rho * s.u[i];
+    const T c = sqrt(g * P / rho);
+    s.rho[i] = rho;
+    s.P[i] = P;
+    s.c[i] = c;
+    if (!(rho > T(0)) || !(P > T(0)) || !finite_(c) || !finite_(s.vx[i]) || !finite_(s.vy[i]) ||
+        !finite_(s.vz[i]))
+        set_status(st, GZ_S_NONFINITE, GZ_C_NONFINITE, s.id[i]);
+}
+
+// Symmetric 3x3 inverse by adjugate; kappa = |E|_F |B|_F / 3.
+template <typename A>
+__device__ __forceinline__ void invert_sym(const A E[6], A B[6], A& det, A& kap) {
+    const A a = E[0], b = E[1], c = E[2], d = E[3], e = E[4], f = E[5];
+    const A Cxx = d * f - e * e, Cxy = c * e - b * f, Cxz = b * e - c * d;
+    const A Cyy = a * f - c * c, Cyz = b * c - a * e, Czz = a * d - b * b;
+    det = a * Cxx + b * Cxy + c * Cxz;
+    const A id = A(1) / det;
+    B[0] = Cxx * id;
+    B[1] = Cxy * id;
+    B[2] = Cxz * id;
+    B[3] = Cyy * id;
+    B[4] = Cyz * id;
+    B[5] = Czz * id;
+    const A nE = sqrt(a * a + d * d + f * f + A(2) * (b * b + c * c + e * e));
+    const A nB = sqrt(B[0] * B[0] + B[3] * B[3] + B[5] * B[5] +
+                      A(2) * (B[1] * B[1] + B[2] * B[2] + B[4] * B[4]));
+    kap = nE * nB / A(3);
+}
+
+// ---------------------------------------------------------- O6-O9, O13
+// Gradients, limiter and packed flux record; optionally the per-particle
+// signal-speed step (over N_i and the reverse list) and its per-box minimum.
+// Record (32 values): x y z H | 1/H knorm rho P | vx vy vz g0 | g1..g14 | B0..B5
+// with knorm = 8/(pi H^3 n^2) so that V_i psi_j(x_i) = knorm * w(r/H).
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_gradients(int N, Sorted<T> s, const unsigned* __restrict__ nbr, const int* __restrict__ ncount,
+                const unsigned* __restrict__ rnbr, const int* __restrict__ rcount, KParams p,
+                T* __restrict__ rec, double* __restrict__ dti, unsigned long long* __restrict__ dtmin,
+                DevStatus* st, int want_dt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = i < N;
+    double dt_i = INFINITY;
+    int mybox = 0;
+    if (active) {
+        mybox = s.box[i];
+        const T xi = s.x[i], yi = s.y[i], zi = s.z[i];
+        const T xim1 = xi - T(1), yim1 = yi - T(1), zim1 = zi - T(1);
+        const T Hi = s.h[i], ni = s.n[i];
+        const T Wi[5] = {s.rho[i], s.vx[i], s.vy[i], s.vz[i], s.P[i]};
+        const T ci = s.c[i];
+        const T iH = T(1) / Hi;
+        const T norm = T(8.0 / kPi) * iH * iH * iH / ni;
+        T E[6] = {0, 0, 0, 0, 0, 0};
+        T Sg[15];
+        T fmax[5], fmin[5];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+            fmax[f] = fmin[f] = Wi[f];
+            Sg[3 * f] = Sg[3 * f + 1] = Sg[3 * f + 2] = T(0);
+        }
+        T vmax = T(0);
+        bool any = false;
+        const int cnt = min(ncount[i], p.cap);
+        for (int k = 0; k < cnt; ++k) {
+            const int j = (int)nbr[(size_t)k * N + i];
+            const T dx = mi_diff(s.x[j], xi, xim1), dy = mi_diff(s.y[j], yi, yim1),
+                    dz = mi_diff(s.z[j], zi, zim1);
+            const T r2 = sep2(dx, dy, dz);
+            const T r = sqrt(r2);
+            const T psi = norm * kern_w(r * iH);
+            const T pdx = psi * dx, pdy = psi * dy, pdz = psi * dz;
+            E[0] += pdx * dx;
+            E[1] += pdx * dy;
+            E[2] += pdx * dz;
+            E[3] += pdy * dy;
+            E[4] += pdy * dz;
+            E[5] += pdz * dz;
+            const T Wj[5] = {s.rho[j], s.vx[j], s.vy[j], s.vz[j], s.P[j]};
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                const T df = Wj[f] - Wi[f];
+                Sg[3 * f] += df * pdx;
+                Sg[3 * f + 1] += df * pdy;
+                Sg[3 * f + 2] += df * pdz;
+                fmax[f] = max(fmax[f], Wj[f]);
+                fmin[f] = min(fmin[f], Wj[f]);
+            }
+            if (want_dt) {
+                const T vd = ((Wj[1] - Wi[1]) * dx + (Wj[2] - Wi[2]) * dy) + (Wj[3] - Wi[3]) * dz;
+                const T w = vd / r;
+                const T vs = ci + s.c[j] - min(w, T(0));
+                vmax = any ? max(vmax, vs) : vs;
+                any = true;
+            }
+        }
+        // O7: B = E^-1; FP64 re-do of E and its inverse when kappa > kappa_max
+        T B[6], det, kap;
+        invert_sym<T>(E, B, det, kap);
+        double g[15];
+        bool singular;
+        if (std::is_same<T, float>::value && !(kap <= (T)p.kappa_max)) {
+            double E64[6] = {0, 0, 0, 0, 0, 0};
+            const double xd = (double)xi, yd = (double)yi, zd = (double)zi;
+            const double iHd = 1.0 / (double)Hi;
+            const double normd = 8.0 / kPi * iHd * iHd * iHd / (double)ni;
+            for (int k = 0; k < cnt; ++k) {
+                const int j = (int)nbr[(size_t)k * N + i];
+                const double dx = mi_diff((double)s.x[j], xd, 0.0),
+                             dy = mi_diff((double)s.y[j], yd, 0.0),
+                             dz = mi_diff((double)s.z[j], zd, 0.0);
+                const double r = sqrt(sep2(dx, dy, dz));
+                const double psi = normd * kern_w(r * iHd);
+                E64[0] += psi * dx * dx;
+                E64[1] += psi * dx * dy;
+                E64[2] += psi * dx * dz;
+                E64[3] += psi * dy * dy;
+                E64[4] += psi * dy * dz;
+                E64[5] += psi * dz * dz;
+            }
+            double B64[6], det64, kap64;
+            invert_sym<double>(E64, B64, det64, kap64);
+            atomicOr(&st->bits, GZ_S_KAPPA_FP64);
+            atomicAdd(&st->counters[GZ_C_KAPPA_FP64], 1ull);
+            singular = !(det64 > 0.0) || !(kap64 <= 1e8);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) B[q] = (T)B64[q];
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                const double s0 = Sg[3 * f], s1 = Sg[3 * f + 1], s2 = Sg[3 * f + 2];
+                g[3 * f] = B64[0] * s0 + B64[1] * s1 + B64[2] * s2;
+                g[3 * f + 1] = B64[1] * s0 + B64[3] * s1 + B64[4] * s2;
+                g[3 * f + 2] = B64[2] * s0 + B64[4] * s1 + B64[5] * s2;
+            }
+        } else {
+            singular = !(det > T(0)) || !(kap <= T(1e8));
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                const T s0 = Sg[3 * f], s1 = Sg[3 * f + 1], s2 = Sg[3 * f + 2];
+                g[3 * f] = B[0] * s0 + B[1] * s1 + B[2] * s2;
+                g[3 * f + 1] = B[1] * s0 + B[3] * s1 + B[4] * s2;
+                g[3 * f + 2] = B[2] * s0 + B[4] * s1 + B[5] * s2;
+            }
+        }
+        if (singular) {
+            set_status(st, GZ_S_SINGULAR, GZ_C_SINGULAR, s.id[i]);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) B[q] = T(0);
+#pragma unroll
+            for (int q = 0; q < 15; ++q) g[q] = 0.0;
+        }
+        T gt[15];
+#pragma unroll
+        for (int q = 0; q < 15; ++q) gt[q] = (T)g[q];
+        // O9 limiter: alpha_f = min_j min(1, beta (f_ext - f_i) / (g . s_ij d))
+        T al[5] = {T(1), T(1), T(1), T(1), T(1)};
+        const T beta = (T)p.beta;
+        for (int k = 0; k < cnt; ++k) {
+            const int j = (int)nbr[(size_t)k * N + i];
+            const T dx = mi_diff(s.x[j], xi, xim1), dy = mi_diff(s.y[j], yi, yim1),
+                    dz = mi_diff(s.z[j], zi, zim1);
+            const T sij = Hi / (Hi + s.h[j]);
+            const T ox = sij * dx, oy = sij * dy, oz = sij * dz;
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                const T D = (gt[3 * f] * ox + gt[3 * f + 1] * oy) + gt[3 * f + 2] * oz;
+                T a = T(1);
+                if (D > T(0))
+                    a = min(T(1), beta * (fmax[f] - Wi[f]) / D);
+                else if (D < T(0))
+                    a = min(T(1), beta * (fmin[f] - Wi[f]) / D);
+                al[f] = min(al[f], a);
+            }
+        }
+        if (want_dt) {
+            const int rc = min(rcount[i], p.rcap);
+            for (int k = 0; k < rc; ++k) {
+                const int j = (int)rnbr[(size_t)k * N + i];
+                const T dx = mi_diff(s.x[j], xi, xim1), dy = mi_diff(s.y[j], yi, yim1),
+                        dz = mi_diff(s.z[j], zi, zim1);
+                const T r = sqrt(sep2(dx, dy, dz));
+                const T vd = ((s.vx[j] - Wi[1]) * dx + (s.vy[j] - Wi[2]) * dy) + (s.vz[j] - Wi[3]) * dz;
+                const T w = vd / r;
+                const T vs = ci + s.c[j] - min(w, T(0));
+                vmax = any ? max(vmax, vs) : vs;
+                any = true;
+            }
+            dt_i = (any && vmax > T(0)) ? 2.0 * cbrt(1.0 / (double)ni) / (double)vmax : INFINITY;
+            dti[i] = dt_i;
+        }
+        T* R = rec + (size_t)i * kRecord;
+        R[0] = xi;
+        R[1] = yi;
+        R[2] = zi;
+        R[3] = Hi;
+        R[4] = iH;
+        R[5] = norm / ni;
+        R[6] = Wi[0];
+        R[7] = Wi[4];
+        R[8] = Wi[1];
+        R[9] = Wi[2];
+        R[10] = Wi[3];
+#pragma unroll
+        for (int q = 0; q < 15; ++q) R[11 + q] = al[q / 3] * gt[q];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) R[26 + q] = B[q];
+    }
+    if (want_dt) {
+        // warp-level minimum per box, one atomic per warp when the warp is in one box
+        const unsigned full = 0xffffffffu;
+        unsigned long long v = active ? dbits(dt_i) : dbits(INFINITY);
+        const int b0 = __shfl_sync(full, mybox, 0);
+        const bool same = __all_sync(full, !active || mybox == b0);
+        if (same) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                unsigned long long w = __shfl_xor_sync(full, v, o);
+                v = w < v ? w : v;
+            }
+            if ((threadIdx.x & 31) == 0) atomicMin(&dtmin[b0], v);
+        } else if (active) {
+            atomicMin(&dtmin[mybox], v);
+        }
+    }
+}
+
+// Builds flux records from caller-supplied gradients and B (caller order).
+template <typename T>
+__global__ void k_pack_given(int N, Sorted<T> s, const T* __restrict__ grad, const T* __restrict__ B,
+                             T* __restrict__ rec) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const unsigned o = s.orig[i];
+    const T Hi = s.h[i], ni = s.n[i];
+    const T iH = T(1) / Hi;
+    T* R = rec + (size_t)i * kRecord;
+    R[0] = s.x[i];
+    R[1] = s.y[i];
+    R[2] = s.z[i];
+    R[3] = Hi;
+    R[4] = iH;
+    R[5] = T(8.0 / kPi) * iH * iH * iH / ni / ni;
+    R[6] = s.rho[i];
+    R[7] = s.P[i];
+    R[8] = s.vx[i];
+    R[9] = s.vy[i];
+    R[10] = s.vz[i];
+    for (int q = 0; q < 15; ++q) R[11 + q] = grad[(size_t)q * N + o];
+    for (int q = 0; q < 6; ++q) R[26 + q] = B[(size_t)q * N + o];
+}
+
+template <typename T>
+__global__ void k_grad_out(int N, const unsigned* __restrict__ orig, const T* __restrict__ rec,
+                           T* __restrict__ grad, T* __restrict__ B) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const unsigned o = orig[i];
+    const T* R = rec + (size_t)i * kRecord;
+    if (grad)
+        for (int q = 0; q < 15; ++q) grad[(size_t)q * N + o] = R[11 + q];
+    if (B)
+        for (int q = 0; q < 6; ++q) B[(size_t)q * N + o] = R[26 + q];
+}
+
+// ---------------------------------------------------------- O10-O12
+__device__ __forceinline__ void load_rec(const float* __restrict__ p, float (&v)[kRecord]) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int k = 0; k < kRecord / 4; ++k) {
+        const float4 t = __ldg(q + k);
+        v[4 * k] = t.x;
+        v[4 * k + 1] = t.y;
+        v[4 * k + 2] = t.z;
+        v[4 * k + 3] = t.w;
+    }
+}
+__device__ __forceinline__ void load_rec(const double* __restrict__ p, double (&v)[kRecord]) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int k = 0; k < kRecord / 2; ++k) {
+        const double2 t = __ldg(q + k);
+        v[2 * k] = t.x;
+        v[2 * k + 1] = t.y;
+    }
+}
+
+// Face state of particle a toward the face at a + s o (o = offset to the
+// partner): linear reconstruction with a's limited gradients plus the Hancock
+// half step (dt/2) (-rho div v, -grad P / rho, -gamma P div v).
+template <typename T>
+__device__ __forceinline__ void face_state(const T (&a)[kRecord], T s, T dx, T dy, T dz, T hdt,
+                                           T gam, bool hancock, T (&F)[5]) {
+    const T ox = s * dx, oy = s * dy, oz = s * dz;
+    const T W[5] = {a[6], a[8], a[9], a[10], a[7]};
+#pragma unroll
+    for (int f = 0; f < 5; ++f)
+        F[f] = W[f] + ((a[11 + 3 * f] * ox + a[12 + 3 * f] * oy) + a[13 + 3 * f] * oz);
+    if (hancock) {
+        const T div = (a[11 + 3] + a[11 + 7]) + a[11 + 11];
+        const T ir = T(1) / a[6];
+        F[0] += hdt * (-a[6] * div);
+        F[1] += hdt * (-a[11 + 12] * ir);
+        F[2] += hdt * (-a[11 + 13] * ir);
+        F[3] += hdt * (-a[11 + 14] * ir);
+        F[4] += hdt * (-gam * a[7] * div);
+    }
+}
+
+// Contribution of the pair (a, b) to particle a's rates: dp (3) and dE.
+// Returns false when the face area vanishes.  flags: 1 fallback, 2 P* < 0.
+template <typename T>
+__device__ __forceinline__ bool pair_rates(const T (&a)[kRecord], const T (&b)[kRecord], bool aL,
+                                           T hdt, T gam, bool hancock, T (&dp)[3], T& dE, int& fl) {
+    const T dx = mi_diff(b[0], a[0], a[0] - T(1));
+    const T dy = mi_diff(b[1], a[1], a[1] - T(1));
+    const T dz = mi_diff(b[2], a[2], a[2] - T(1));
+    const T r2 = sep2(dx, dy, dz);
+    const T r = sqrt(r2);
+    const T ca = r2 < a[3] * a[3] ? a[5] * kern_w(r * a[4]) : T(0);
+    const T cb = r2 < b[3] * b[3] ? b[5] * kern_w(r * b[4]) : T(0);
+    const T Bax = (a[26] * dx + a[27] * dy) + a[28] * dz;
+    const T Bay = (a[27] * dx + a[29] * dy) + a[30] * dz;
+    const T Baz = (a[28] * dx + a[30] * dy) + a[31] * dz;
+    const T Bbx = (b[26] * dx + b[27] * dy) + b[28] * dz;
+    const T Bby = (b[27] * dx + b[29] * dy) + b[30] * dz;
+    const T Bbz = (b[28] * dx + b[30] * dy) + b[31] * dz;
+    const T A0 = add_rn(mul_rn(ca, Bax), mul_rn(cb, Bbx));
+    const T A1 = add_rn(mul_rn(ca, Bay), mul_rn(cb, Bby));
+    const T A2 = add_rn(mul_rn(ca, Baz), mul_rn(cb, Bbz));
+    const T Aq = sep2(A0, A1, A2);
+    if (!(Aq > T(0))) return false;
+    const T Am = sqrt(Aq);
+    const T iA = T(1) / Am;
+    const T n0 = A0 * iA, n1 = A1 * iA, n2 = A2 * iA;
+    const T Hs = a[3] + b[3];
+    const T sa = a[3] / Hs, sb = b[3] / Hs;
+    T Fa[5], Fb[5];
+    face_state(a, sa, dx, dy, dz, hdt, gam, hancock, Fa);
+    face_state(b, sb, -dx, -dy, -dz, hdt, gam, hancock, Fb);
+    const T Wa[5] = {a[6], a[8], a[9], a[10], a[7]};
+    const T Wb[5] = {b[6], b[8], b[9], b[10], b[7]};
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+        const T lo = min(Wa[f], Wb[f]), hi = max(Wa[f], Wb[f]);
+        Fa[f] = min(max(Fa[f], lo), hi);
+        Fb[f] = min(max(Fb[f], lo), hi);
+    }
+    if (!(Fa[0] > T(0) && Fa[4] > T(0) && Fb[0] > T(0) && Fb[4] > T(0))) {
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+            Fa[f] = Wa[f];
+            Fb[f] = Wb[f];
+        }
+        fl |= 1;
+    }
+    // canonical order: L = lower id
+    T FL[5], FR[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+        FL[f] = aL ? Fa[f] : Fb[f];
+        FR[f] = aL ? Fb[f] : Fa[f];
+    }
+    const T vLx = aL ? Wa[1] : Wb[1], vLy = aL ? Wa[2] : Wb[2], vLz = aL ? Wa[3] : Wb[3];
+    const T vRx = aL ? Wb[1] : Wa[1], vRy = aL ? Wb[2] : Wa[2], vRz = aL ? Wb[3] : Wa[3];
+    const T sL = aL ? sa : sb;
+    const T nx = aL ? n0 : -n0, ny = aL ? n1 : -n1, nz = aL ? n2 : -n2;
+    const T vfx = vLx + sL * (vRx - vLx), vfy = vLy + sL * (vRy - vLy), vfz = vLz + sL * (vRz - vLz);
+    const T vfn = (vfx * nx + vfy * ny) + vfz * nz;
+    const T uL = ((FL[1] - vfx) * nx + (FL[2] - vfy) * ny) + (FL[3] - vfz) * nz;
+    const T uR = ((FR[1] - vfx) * nx + (FR[2] - vfy) * ny) + (FR[3] - vfz) * nz;
+    // O12 HLLC with Davis wave speeds
+    const T rL = FL[0], PL = FL[4], rR = FR[0], PR = FR[4];
+    const T cL = sqrt(gam * PL / rL), cR = sqrt(gam * PR / rR);
+    const T SL = min(uL - cL, uR - cR), SR = max(uL + cL, uR + cR);
+    const T num = ((PR - PL) + rL * uL * (SL - uL)) - rR * uR * (SR - uR);
+    const T den = rL * (SL - uL) - rR * (SR - uR);
+    const T ss = num / den;
+    T ps = PL + rL * (SL - uL) * (ss - uL);
+    if (ps < T(0)) {
+        ps = T(0);
+        fl |= 2;
+    }
+    dp[0] = -mul_rn(ps, A0);
+    dp[1] = -mul_rn(ps, A1);
+    dp[2] = -mul_rn(ps, A2);
+    const T ef = ps * (ss + vfn) * Am;
+    dE = aL ? -ef : ef;
+    return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_fluxes(int N, const T* __restrict__ rec, const long long* __restrict__ sid,
+             const int* __restrict__ sbox, const unsigned* __restrict__ nbr,
+             const int* __restrict__ ncount, const unsigned* __restrict__ rnbr,
+             const int* __restrict__ rcount, KParams p, const double* __restrict__ dt_use,
+             double* __restrict__ dpdt, double* __restrict__ dEdt, DevStatus* st) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    T a[kRecord];
+    load_rec(rec + (size_t)i * kRecord, a);
+    const long long idi = sid[i];
+    const T hdt = (T)(0.5 * dt_use[sbox[i]]);
+    const T gam = (T)p.gamma;
+    const bool hancock = p.hancock != 0;
+    T part[4] = {T(0), T(0), T(0), T(0)};
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int np = 0, fl = 0, nfall = 0, nneg = 0;
+    const int cnt = min(ncount[i], p.cap);
+    const int rc = min(rcount[i], p.rcap);
+    for (int k = 0; k < cnt + rc; ++k) {
+        const int j = k < cnt ? (int)nbr[(size_t)k * N + i] : (int)rnbr[(size_t)(k - cnt) * N + i];
+        T b[kRecord];
+        load_rec(rec + (size_t)j * kRecord, b);
+        T dp[3], dE;
+        fl = 0;
+        if (pair_rates(a, b, idi < sid[j], hdt, gam, hancock, dp, dE, fl)) {
+            part[0] += dp[0];
+            part[1] += dp[1];
+            part[2] += dp[2];
+            part[3] += dE;
+        }
+        nfall += fl & 1;
+        nneg += (fl >> 1) & 1;
+        if (++np == 8) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                acc[q] += (double)part[q];
+                part[q] = T(0);
+            }
+            np = 0;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] += (double)part[q];
+    dpdt[i] = acc[0];
+    dpdt[(size_t)N + i] = acc[1];
+    dpdt[2 * (size_t)N + i] = acc[2];
+    dEdt[i] = acc[3];
+    if (nfall) {
+        atomicOr(&st->bits, GZ_S_FALLBACK);
+        atomicAdd(&st->counters[GZ_C_FALLBACK], (unsigned long long)nfall);
+    }
+    if (nneg) {
+        atomicOr(&st->bits, GZ_S_PSTAR_NEG);
+        atomicAdd(&st->counters[GZ_C_PSTAR_NEG], (unsigned long long)nneg);
+    }
+}
+
+// ----------------------------------------------------------------- O14
+__device__ __forceinline__ double wrap1(double v) {
+    if (v < 0.0) v += 1.0;
+    if (v >= 1.0) v -= 1.0;
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T to_box(double v) {
+    T t = (T)v;
+    if (t >= T(1)) t -= T(1);
+    return t;
+}
+
+template <typename T>
+__global__ void k_update(int N, Sorted<T> s, const double* __restrict__ dpdt,
+                         const double* __restrict__ dEdt, const double* __restrict__ dt_use,
+                         gz_particles out, int* __restrict__ box_hits, DevStatus* st) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const unsigned o = s.orig[i];
+    const int b = s.box[i];
+    const double dt = dt_use[b];
+    const double m = (double)s.m[i];
+    const double vx = (double)s.vx[i], vy = (double)s.vy[i], vz = (double)s.vz[i];
+    const double u = (double)s.u[i];
+    const double v2 = (vx * vx + vy * vy) + vz * vz;
+    const double E = m * (u + 0.5 * v2) + dt * dEdt[i];
+    const double px = m * vx + dt * dpdt[i];
+    const double py = m * vy + dt * dpdt[(size_t)N + i];
+    const double pz = m * vz + dt * dpdt[2 * (size_t)N + i];
+    const double nx = px / m, ny = py / m, nz = pz / m;
+    const double x = wrap1((double)s.x[i] + dt * (0.5 * (vx + nx)));
+    const double y = wrap1((double)s.y[i] + dt * (0.5 * (vy + ny)));
+    const double z = wrap1((double)s.z[i] + dt * (0.5 * (vz + nz)));
+    const double un = E / m - 0.5 * ((nx * nx + ny * ny) + nz * nz);
+    ((T*)out.x)[o] = to_box<T>(x);
+    ((T*)out.y)[o] = to_box<T>(y);
+    ((T*)out.z)[o] = to_box<T>(z);
+    ((T*)out.vx)[o] = (T)nx;
+    ((T*)out.vy)[o] = (T)ny;
+    ((T*)out.vz)[o] = (T)nz;
+    ((T*)out.u)[o] = (T)un;
+    ((T*)out.h)[o] = s.h[i];
+    if (!(un > 0.0)) {
+        atomicAdd(&box_hits[b], 1);
+        set_status(st, GZ_S_UFLOOR, GZ_C_UFLOOR, -1);
+    }
+    if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(nx) && isfinite(ny) &&
+          isfinite(nz) && isfinite(un)))
+        set_status(st, GZ_S_NONFINITE, GZ_C_NONFINITE, s.id[i]);
+}
+
+template <typename T>
+struct Bits;
+template <>
+struct Bits<float> {
+    typedef unsigned U;
+    static constexpr int nbits = 32;
+    __device__ static U get(float v) { return __float_as_uint(v); }
+    __device__ static float put(U b) { return __uint_as_float(b); }
+};
+template <>
+struct Bits<double> {
+    typedef unsigned long long U;
+    static constexpr int nbits = 64;
+    __device__ static U get(double v) { return (U)__double_as_longlong(v); }
+    __device__ static double put(U b) { return __longlong_as_double((long long)b); }
+};
+
+// O14 floor: for each box with a hit, the lower median of u at step start
+// (radix select on the bit patterns of positive values), then every
+// non-positive updated u of the box is set to u_floor_frac * median.
+template <typename T>
+__global__ void k_ufloor(Sorted<T> s, const BoxInfo* __restrict__ boxes,
+                         const int* __restrict__ box_hits, gz_particles out, double frac) {
+    typedef typename Bits<T>::U U;
+    const int b = blockIdx.x;
+    if (box_hits[b] == 0) return;
+    const int first = boxes[b].first, count = boxes[b].count;
+    __shared__ unsigned hist[256];
+    __shared__ U prefix_s;
+    __shared__ int k_s;
+    U prefix = 0, mask = 0;
+    int k = (count - 1) / 2;
+    for (int shift = Bits<T>::nbits - 8; shift >= 0; shift -= 8) {
+        for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
+        __syncthreads();
+        for (int e = threadIdx.x; e < count; e += blockDim.x) {
+            const U v = Bits<T>::get(s.u[first + e]);
+            if ((v & mask) == prefix) atomicAdd(&hist[(unsigned)((v >> shift) & 255u)], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int d = 0;
+            for (; d < 255; ++d) {
+                if (k < (int)hist[d]) break;
+                k -= (int)hist[d];
+            }
+            prefix_s = prefix | ((U)d << shift);
+            k_s = k;
+        }
+        __syncthreads();
+        prefix = prefix_s;
+        k = k_s;
+        mask |= ((U)255u << shift);
+        __syncthreads();
+    }
+    const T fl = (T)(frac * (double)Bits<T>::put(prefix));
+    T* u = (T*)out.u;
+    for (int e = threadIdx.x; e < count; e += blockDim.x) {
+        const int o = first + e;  // caller order and sorted order share box ranges
+        if (!(u[o] > T(0))) u[o] = fl;
+    }
+}
+
+__global__ void k_dt_init(int nb, unsigned long long* dtmin) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) dtmin[b] = dbits(INFINITY);
+}
+__global__ void k_dt_final(int nb, const unsigned long long* __restrict__ dtmin, double cfl,
+                           double dt_fixed, double* __restrict__ dt_use, double* __restrict__ out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const double raw = __longlong_as_double((long long)dtmin[b]);
+    const double dt = dt_fixed > 0.0 ? dt_fixed : cfl * raw;
+    dt_use[b] = dt;
+    if (out) out[b] = dt;
+}
+__global__ void k_dt_set(int nb, double dt, double* __restrict__ dt_use) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) dt_use[b] = dt;
+}
+__global__ void k_dt_out(int nb, const unsigned long long* __restrict__ dtmin, double cfl,
+                         double* __restrict__ out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) out[b] = cfl * __longlong_as_double((long long)dtmin[b]);
+}
+
+__global__ void k_get_nbrs(int N, const unsigned* __restrict__ orig, const long long* __restrict__ sid,
+                           const unsigned* __restrict__ nbr, const int* __restrict__ ncount, int cap_in,
+                           int32_t* __restrict__ count_out, int64_t* __restrict__ ids_out, int cap) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const unsigned o = orig[i];
+    const int c = ncount[i];
+    count_out[o] = c;
+    if (!ids_out) return;
+    const int m = min(min(c, cap_in), cap);
+    for (int k = 0; k < cap; ++k)
+        ids_out[(size_t)k * N + o] = k < m ? (int64_t)sid[nbr[(size_t)k * N + i]] : (int64_t)-1;
+}
+
+__global__ void k_pairs(int N, const int* __restrict__ ncount, const int* __restrict__ rcount,
+                        int cap, int rcap, long long* __restrict__ out) {
+    long long v = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+        v += min(ncount[i], cap) + min(rcount[i], rcap);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd((unsigned long long*)out, (unsigned long long)v);
+}
+
+}  // namespace
+
+cudaError_t run_pair_count(Ctx& c, long long* out_dev) {
+    c.launches += 1;
+    cudaMemsetAsync(out_dev, 0, sizeof(long long), c.stream);
+    k_pairs<<<304, 256, 0, c.stream>>>(c.N, c.ncount, c.rcount, c.cap, c.rcap, out_dev);
+    return cudaGetLastError();
+}
+
+KParams kparams(const Ctx& c) {
+    KParams k;
+    k.gamma = c.params.gamma;
+    k.ngb = c.params.ngb;
+    k.tol = c.params.tol;
+    k.cfl = c.params.cfl;
+    k.kappa_max = c.params.kappa_max;
+    k.beta = c.params.beta;
+    k.u_floor_frac = c.params.u_floor_frac;
+    k.h_lim = c.params.h_lim;
+    k.hancock = c.params.hancock;
+    k.max_iter = c.params.max_iter;
+    k.cap = c.cap;
+    k.rcap = c.rcap;
+    return k;
+}
+
+static Grid grid_of(const Ctx& c) {
+    Grid g;
+    g.boxes = c.boxes;
+    g.cells = c.cells;
+    return g;
+}
+
+template <typename T>
+cudaError_t run_density(Ctx& c) {
+    c.launches += 1;
+    k_density<T><<<blocks(c.N, 128), 128, 0, c.stream>>>(c.N, sorted_view<T>(c), grid_of(c), kparams(c),
+                                                          c.nbr, c.ncount, c.iters, c.status);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_build_lists(Ctx& c) {
+    c.launches += 1;
+    k_lists<T><<<blocks(c.N, 128), 128, 0, c.stream>>>(c.N, sorted_view<T>(c), grid_of(c), kparams(c),
+                                                        c.nbr, c.ncount, c.status);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_reverse(Ctx& c) {
+    c.launches += 2;
+    cudaMemsetAsync(c.rcount, 0, sizeof(int) * (size_t)c.N, c.stream);
+    k_reverse<T><<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, sorted_view<T>(c), kparams(c), c.nbr,
+                                                          c.ncount, c.rcount, c.rnbr, c.status);
+    k_sort_rev<<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, c.rcount, c.rnbr, c.rcap);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_prim(Ctx& c) {
+    c.launches += 1;
+    k_prim<T><<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, sorted_view<T>(c), kparams(c), c.status);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_gradients(Ctx& c, bool want_dt) {
+    c.launches += want_dt ? 2 : 1;
+    if (want_dt) k_dt_init<<<blocks(c.nboxes, 256), 256, 0, c.stream>>>(c.nboxes, (unsigned long long*)c.dt_box);
+    k_gradients<T><<<blocks(c.N, 128), 128, 0, c.stream>>>(
+        c.N, sorted_view<T>(c), c.nbr, c.ncount, c.rnbr, c.rcount, kparams(c), (T*)c.rec, c.dti,
+        (unsigned long long*)c.dt_box, c.status, want_dt ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_pack_given(Ctx& c, const T* grad, const T* B) {
+    c.launches += 1;
+    k_pack_given<T><<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, sorted_view<T>(c), grad, B, (T*)c.rec);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_grad_out(Ctx& c, T* grad, T* B) {
+    c.launches += 1;
+    k_grad_out<T><<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, c.vals, (const T*)c.rec, grad, B);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_fluxes(Ctx& c) {
+    c.launches += 1;
+    k_fluxes<T><<<blocks(c.N, 128), 128, 0, c.stream>>>(c.N, (const T*)c.rec, c.sid, c.sbox, c.nbr,
+                                                         c.ncount, c.rnbr, c.rcount, kparams(c),
+                                                         c.dt_use, c.dpdt, c.dEdt, c.status);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_update(Ctx& c, gz_particles& p) {
+    c.launches += 2;
+    int* hits = c.box_hits;
+    cudaMemsetAsync(hits, 0, sizeof(int) * (size_t)c.nboxes, c.stream);
+    k_update<T><<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, sorted_view<T>(c), c.dpdt, c.dEdt,
+                                                         c.dt_use, p, hits, c.status);
+    k_ufloor<T><<<c.nboxes, 1024, 0, c.stream>>>(sorted_view<T>(c), c.boxes, hits, p,
+                                                  c.params.u_floor_frac);
+    return cudaGetLastError();
+}
+
+cudaError_t run_dt_init(Ctx& c) {
+    c.launches += 1;
+    k_dt_init<<<blocks(c.nboxes, 256), 256, 0, c.stream>>>(c.nboxes, (unsigned long long*)c.dt_box);
+    return cudaGetLastError();
+}
+
+cudaError_t run_dt_finalize(Ctx& c, double dt_fixed, double* dt_used_dev) {
+    c.launches += 1;
+    k_dt_final<<<blocks(c.nboxes, 256), 256, 0, c.stream>>>(
+        c.nboxes, (const unsigned long long*)c.dt_box, c.params.cfl, dt_fixed, c.dt_use, dt_used_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t run_dt_set(Ctx& c, double dt) {
+    c.launches += 1;
+    k_dt_set<<<blocks(c.nboxes, 256), 256, 0, c.stream>>>(c.nboxes, dt, c.dt_use);
+    return cudaGetLastError();
+}
+
+cudaError_t run_dt_out(Ctx& c, double* out) {
+    c.launches += 1;
+    k_dt_out<<<blocks(c.nboxes, 256), 256, 0, c.stream>>>(c.nboxes, (const unsigned long long*)c.dt_box,
+                                                          c.params.cfl, out);
+    return cudaGetLastError();
+}
+
+cudaError_t run_get_neighbours(Ctx& c, int32_t* count_out, int64_t* ids_out, int cap) {
+    c.launches += 1;
+    k_get_nbrs<<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, c.vals, c.sid, c.nbr, c.ncount, c.cap,
+                                                       count_out, ids_out, cap);
+    return cudaGetLastError();
+}
+
+#define GZ_INST(T)                                                   \
+    template cudaError_t run_density<T>(Ctx&);                       \
+    template cudaError_t run_build_lists<T>(Ctx&);                   \
+    template cudaError_t run_reverse<T>(Ctx&);                       \
+    template cudaError_t run_prim<T>(Ctx&);                          \
+    template cudaError_t run_gradients<T>(Ctx&, bool);               \
+    template cudaError_t run_pack_given<T>(Ctx&, const T*, const T*); \
+    template cudaError_t run_grad_out<T>(Ctx&, T*, T*);              \
+    template cudaError_t run_fluxes<T>(Ctx&);                        \
+    template cudaError_t run_update<T>(Ctx&, gz_particles&);
+GZ_INST(float)
+GZ_INST(double)
+#undef GZ_INST
+
+}  // namespace gz

@@ -1,0 +1,218 @@
+// Internal declarations of the GB300 MFM library: context layout, device
+// status, kernel-side helpers.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "gz.h"
+
+namespace gz {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kRecord = 32;  // values per packed particle record (flux pass)
+
+// Device status word (one per context).
+struct DevStatus {
+    unsigned int bits;
+    unsigned int pad;
+    unsigned long long first_bad_id;  // smallest id with an error bit (~0 = none)
+    unsigned long long counters[GZ_NCOUNTERS];
+};
+
+// Per-box cell grid description (device table).
+struct BoxInfo {
+    int nc;          // cells per axis
+    int cell_off;    // first cell of this box in the cell array
+    int first;       // first particle (sorted order == caller order per box)
+    int count;       // particles in the box
+};
+
+// Scalar parameters passed by value to kernels.
+struct KParams {
+    double gamma, ngb, tol, cfl, kappa_max, beta, u_floor_frac, h_lim;
+    int hancock, max_iter, cap, rcap;
+};
+
+// Sorted-order views the kernels share.
+template <typename T>
+struct Sorted {
+    T *x, *y, *z, *vx, *vy, *vz, *m, *u, *h;
+    long long* id;      // original ids, sorted order
+    unsigned* orig;     // caller index of sorted particle
+    int* box;           // box of sorted particle
+    T *n, *rho, *P, *c;
+};
+
+struct Grid {
+    const BoxInfo* boxes;  // device
+    const int2* cells;     // (start, end) per cell, all boxes
+};
+
+struct Ctx {
+    gz_params params;
+    int precision;
+    int N;
+    int nboxes;
+    std::vector<int64_t> counts;
+    std::vector<BoxInfo> hboxes;
+    int total_cells;
+    int cbits;     // bits per axis of a cell coordinate
+    int box_bits;  // bits of the box index in a key
+    cudaStream_t stream;
+    std::string err;
+
+    // device buffers
+    void* arena;
+    size_t arena_bytes;
+    BoxInfo* boxes;
+    int2* cells;
+    unsigned *keys, *keys_alt, *vals, *vals_alt;
+    unsigned* hist;
+    int hist_len;
+    int* box_of;  // caller order
+    // sorted state (working precision) and derived per-particle data
+    void *sx, *sy, *sz, *svx, *svy, *svz, *sm, *su, *sh, *sn, *srho, *sP, *sc;
+    long long* sid;
+    int* sbox;
+    int* iters;
+    int* ncount;
+    unsigned* nbr;  // [cap][N]
+    int* rcount;
+    unsigned* rnbr;  // [rcap][N]
+    void* rec;       // [N][kRecord] working precision
+    double* dpdt;    // [3][N] sorted
+    double* dEdt;    // [N] sorted
+    double* dti;     // [N] sorted
+    double* dt_box;  // [nboxes] CFL minimum (before the cfl factor is applied: raw min)
+    double* dt_use;  // [nboxes] step used
+    int* box_hits;   // [nboxes] u-floor hits of the current step
+    DevStatus* status;
+    int cap, rcap;
+    int nbr_valid;  // neighbour lists of the last density pass are current
+    long long launches;  // kernel launches issued
+    // per-pass CUDA-event profile
+    int prof;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending {
+        int pass;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    double prof_ms[GZ_NPASSES];
+    long long prof_calls[GZ_NPASSES];
+    long long* pairs_dev;  // scratch for gz_pair_count
+};
+
+// ------------------------------------------------------------------ status
+__device__ __forceinline__ void set_status(DevStatus* st, unsigned bit, int counter,
+                                           long long id) {
+    atomicOr(&st->bits, bit);
+    atomicAdd(&st->counters[counter], 1ull);
+    if ((bit & GZ_S_ERROR_MASK) && id >= 0)
+        atomicMin(&st->first_bad_id, (unsigned long long)id);
+}
+
+// --------------------------------------------------------- O1 min image
+// FP64: exactly the oracle's expression (difference, then shift by one).
+__device__ __forceinline__ double mi_diff(double xj, double xi, double /*xim1*/) {
+    double d = xj - xi;
+    if (d >= 0.5)
+        d = d - 1.0;
+    else if (d < -0.5)
+        d = d + 1.0;
+    return d;
+}
+// FP32: shift the operand near 1 first (x - 1 is exact for x in [1/2, 1)),
+// so the wrapped offset is correctly rounded like an unwrapped one.
+__device__ __forceinline__ float mi_diff(float xj, float xi, float xim1) {
+    float d = xj - xi;
+    float dl = __fsub_rn(__fsub_rn(xj, 1.0f), xi);
+    float dh = __fsub_rn(xj, xim1);
+    return d >= 0.5f ? dl : (d < -0.5f ? dh : d);
+}
+
+// --------------------------------------------------------- O2 kernel
+template <typename T>
+__device__ __forceinline__ T kern_w(T q) {
+    T t = T(1) - q;
+    T a = T(1) + q * q * (T(-6) + T(6) * q);
+    T b = T(2) * t * t * t;
+    return q <= T(0.5) ? a : (q < T(1) ? b : T(0));
+}
+template <typename T>
+__device__ __forceinline__ T kern_dw(T q) {
+    T t = T(1) - q;
+    T a = q * (T(-12) + T(18) * q);
+    T b = T(-6) * t * t;
+    return q <= T(0.5) ? a : (q < T(1) ? b : T(0));
+}
+
+__device__ __forceinline__ bool finite_(float v) { return isfinite(v); }
+__device__ __forceinline__ bool finite_(double v) { return isfinite(v); }
+
+// r^2 = (dx dx + dy dy) + dz dz.  FP64 rounds after every operation (no FMA
+// contraction), exactly like the oracle, so neighbour decisions agree bitwise.
+__device__ __forceinline__ double sep2(double dx, double dy, double dz) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+__device__ __forceinline__ float sep2(float dx, float dy, float dz) {
+    return (dx * dx + dy * dy) + dz * dz;
+}
+
+// ordered-integer image of a non-negative double (for atomicMin)
+__device__ __forceinline__ unsigned long long dbits(double v) {
+    return (unsigned long long)__double_as_longlong(v);
+}
+
+// Loop over all candidates j != self in the cells that overlap the cube
+// [x - R, x + R] of particle self's box, calling fn(j, dx, dy, dz, r2).
+template <typename T, typename F>
+__device__ __forceinline__ void for_candidates(const Grid& g, const BoxInfo& bx, const T* __restrict__ x,
+                                               const T* __restrict__ y, const T* __restrict__ z,
+                                               int self, T xi, T yi, T zi, T R, F&& fn) {
+    const int nc = bx.nc;
+    const int2* __restrict__ cells = g.cells + bx.cell_off;
+    int lo[3], hi[3];
+    const double pos[3] = {(double)xi, (double)yi, (double)zi};
+    const double Rd = (double)R;
+    // positions outside [0, 1] (flagged by the binning pass) see no candidates
+    if (!(pos[0] >= 0.0 && pos[0] <= 1.0 && pos[1] >= 0.0 && pos[1] <= 1.0 && pos[2] >= 0.0 &&
+          pos[2] <= 1.0 && Rd >= 0.0))
+        return;
+    const bool full = !(Rd < 0.5);  // (also catches non-finite R)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = full ? 0 : (int)floor((pos[a] - Rd) * nc - 1e-3);
+        hi[a] = full ? nc - 1 : (int)floor((pos[a] + Rd) * nc + 1e-3);
+        if (hi[a] - lo[a] + 1 >= nc) {
+            lo[a] = 0;
+            hi[a] = nc - 1;
+        }
+    }
+    const T xim1 = xi - T(1), yim1 = yi - T(1), zim1 = zi - T(1);
+    for (int cz = lo[2]; cz <= hi[2]; ++cz) {
+        const int wz = cz < 0 ? cz + nc : (cz >= nc ? cz - nc : cz);
+        for (int cy = lo[1]; cy <= hi[1]; ++cy) {
+            const int wy = cy < 0 ? cy + nc : (cy >= nc ? cy - nc : cy);
+            const int row = (wz * nc + wy) * nc;
+            for (int cx = lo[0]; cx <= hi[0]; ++cx) {
+                const int wx = cx < 0 ? cx + nc : (cx >= nc ? cx - nc : cx);
+                const int2 se = cells[row + wx];
+                for (int j = se.x; j < se.y; ++j) {
+                    if (j == self) continue;
+                    T dx = mi_diff(x[j], xi, xim1);
+                    T dy = mi_diff(y[j], yi, yim1);
+                    T dz = mi_diff(z[j], zi, zim1);
+                    T r2 = sep2(dx, dy, dz);
+                    fn(j, dx, dy, dz, r2);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace gz

@@ -1,0 +1,55 @@
+// Host-side launchers shared between the translation units of the library.
+#pragma once
+
+#include "gz_internal.cuh"
+
+namespace gz {
+
+template <typename T>
+Sorted<T> sorted_view(Ctx& c);
+
+// Binning + radix sort + permutation into the context's sorted arrays, and
+// cell ranges.  n_in (caller order, may be null) is permuted into the sorted
+// n array as well.  Returns a CUDA error code.
+template <typename T>
+cudaError_t sort_and_bin(Ctx& c, const gz_particles& p, const void* n_in);
+
+// Writes sorted-order arrays back to caller order.
+template <typename T>
+cudaError_t unpermute_T(Ctx& c, const T* src, T* dst, int rows);
+cudaError_t unpermute_d(Ctx& c, const double* src, double* dst, int rows);
+cudaError_t unpermute_i(Ctx& c, const int* src, int* dst);
+
+// Hydro passes (sorted order).
+template <typename T>
+cudaError_t run_density(Ctx& c);
+template <typename T>
+cudaError_t run_build_lists(Ctx& c);
+template <typename T>
+cudaError_t run_reverse(Ctx& c);
+template <typename T>
+cudaError_t run_prim(Ctx& c);
+template <typename T>
+cudaError_t run_gradients(Ctx& c, bool want_dt);
+template <typename T>
+cudaError_t run_timestep_only(Ctx& c);
+template <typename T>
+cudaError_t run_pack_given(Ctx& c, const T* grad, const T* B);
+template <typename T>
+cudaError_t run_fluxes(Ctx& c);
+template <typename T>
+cudaError_t run_update(Ctx& c, gz_particles& p);
+template <typename T>
+cudaError_t run_grad_out(Ctx& c, T* grad_out, T* B_out);
+
+cudaError_t run_dt_init(Ctx& c);
+cudaError_t run_dt_finalize(Ctx& c, double dt_fixed, double* dt_used_dev);
+cudaError_t run_dt_set(Ctx& c, double dt);
+cudaError_t run_dt_out(Ctx& c, double* out);
+cudaError_t run_get_neighbours(Ctx& c, int32_t* count_out, int64_t* ids_out, int cap);
+
+cudaError_t run_pair_count(Ctx& c, long long* out_dev);
+
+KParams kparams(const Ctx& c);
+
+}  // namespace gz
