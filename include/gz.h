@@ -142,7 +142,8 @@ gz_status gz_create(const gz_params* params, int32_t nboxes, const int64_t* coun
 /* Frees the context and its scratch (synchronises its stream). */
 gz_status gz_destroy(gz_ctx* ctx);
 
-/* O3-O5.  Reads x, y, z, h (h = initial guess of H) and id; solves the
+/* O3-O5.  Reads x, y, z, h (h = initial guess of H) and id (vx, vy, vz, m
+ * and u are not read and may be NULL); solves the
  * h-iteration for every particle and writes the converged H back into h,
  * the kernel number density n into n_out, and the number of f evaluations
  * into iters_out (int32).  n_out and iters_out may be NULL.  The neighbour

@@ -86,9 +86,10 @@ struct Pass {
 
 gz_status check_particles(gz_ctx* ctx, const gz_particles* p, bool need_vel) {
     if (!p) return fail(ctx, GZ_E_INVAL, "null particle set");
-    if (!p->x || !p->y || !p->z || !p->h || !p->id || !p->m || !p->u)
+    if (!p->x || !p->y || !p->z || !p->h || !p->id)
         return fail(ctx, GZ_E_INVAL, "null particle array");
-    if (need_vel && (!p->vx || !p->vy || !p->vz)) return fail(ctx, GZ_E_INVAL, "null velocity array");
+    if (need_vel && (!p->vx || !p->vy || !p->vz || !p->m || !p->u))
+        return fail(ctx, GZ_E_INVAL, "null velocity, mass or energy array");
     return GZ_OK;
 }
 

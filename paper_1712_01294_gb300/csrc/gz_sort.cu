@@ -152,11 +152,12 @@ __global__ void k_permute(int N, const unsigned* __restrict__ skeys,
     s.x[i] = ((const T*)p.x)[src];
     s.y[i] = ((const T*)p.y)[src];
     s.z[i] = ((const T*)p.z)[src];
-    s.vx[i] = ((const T*)p.vx)[src];
-    s.vy[i] = ((const T*)p.vy)[src];
-    s.vz[i] = ((const T*)p.vz)[src];
-    s.m[i] = ((const T*)p.m)[src];
-    s.u[i] = ((const T*)p.u)[src];
+    // velocities, mass and energy are optional (the density pass reads none)
+    if (p.vx) s.vx[i] = ((const T*)p.vx)[src];
+    if (p.vy) s.vy[i] = ((const T*)p.vy)[src];
+    if (p.vz) s.vz[i] = ((const T*)p.vz)[src];
+    if (p.m) s.m[i] = ((const T*)p.m)[src];
+    if (p.u) s.u[i] = ((const T*)p.u)[src];
     s.h[i] = ((const T*)p.h)[src];
     s.id[i] = (long long)p.id[src];
     if (n_in) s.n[i] = ((const T*)n_in)[src];

@@ -329,6 +329,21 @@ def test_single_particle_box_flags_nonconvergence_without_fault():
     assert 0.0 < float(d["h"].cpu()[0]) < 0.5
 
 
+def test_density_reads_only_positions_h_and_ids():
+    m = gz()
+    q = cast_state(I.sod(10), m.GZ_MIXED32)
+    d = device(q, m.GZ_MIXED32)
+    ref = {k: v.clone() for k, v in d.items()}
+    ctx = ctx_for(q.N, m.GZ_MIXED32)
+    n1, it1 = ctx.density(ref)
+    for k in ("vx", "vy", "vz", "m", "u"):
+        d[k] = None
+    n2, it2 = ctx.density(d)
+    assert_status_ok(ctx)
+    import torch
+    assert torch.equal(n1, n2) and torch.equal(it1, it2) and torch.equal(ref["h"], d["h"])
+
+
 def test_invalid_positions_are_flagged():
     m = gz()
     q = cast_state(I.sod(8), m.GZ_MIXED32)
