@@ -233,7 +233,7 @@ gz_status gz_profile_read(gz_ctx* ctx, double* ms, int64_t* calls, int32_t reset
  * (device arrays of the working precision; vx, vy, vz, m, u are ignored),
  * writes the converged H back into h, n into n_out and the f-evaluation
  * counts into iters_out (either may be NULL); enqueued on cuda_stream.
- * Scratch: a fixed array inside the library (about 7.1 MB, held on every GPU
+ * Scratch: a fixed array inside the library (about 8.1 MB, held on every GPU
  * that loads the library until exit).  Limits: 1 <= n <= 32768 and a cell
  * grid of at most 32^3 cells (cell_factor * H0 >= 1/32), else GZ_E_INVAL.
  * The first call on a device looks up the array's device address (once per

@@ -124,13 +124,13 @@ gz_status prepare_given(gz_ctx* ctx, const gz_particles* p, const void* n, bool 
         Pass t(c, GZ_PASS_LISTS);
         e = run_build_lists<T>(c);
     }
-    if (e == cudaSuccess && reverse) {
-        Pass t(c, GZ_PASS_REVERSE);
-        e = run_reverse<T>(c);
-    }
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_PRIM);
         e = run_prim<T>(c);
+    }
+    if (e == cudaSuccess && reverse) {
+        Pass t(c, GZ_PASS_REVERSE);
+        e = run_reverse<T>(c);
     }
     c.nbr_valid = 1;
     return cuda_check(ctx, e, "prepare");
@@ -191,12 +191,12 @@ gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
         e = run_density<T>(c);
     }
     if (e == cudaSuccess) {
-        Pass t(c, GZ_PASS_REVERSE);
-        e = run_reverse<T>(c);
+        Pass t(c, GZ_PASS_PRIM);
+        e = run_prim<T>(c);  // also stores the converged H in the packed positions
     }
     if (e == cudaSuccess) {
-        Pass t(c, GZ_PASS_PRIM);
-        e = run_prim<T>(c);
+        Pass t(c, GZ_PASS_REVERSE);
+        e = run_reverse<T>(c);
     }
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_GRAD);
@@ -261,14 +261,16 @@ gz_status gz_create(const gz_params* params, int32_t nboxes, const int64_t* coun
     c.nboxes = nboxes;
     c.counts.assign(counts, counts + nboxes);
     c.stream = (cudaStream_t)cuda_stream;
-    c.cap = params->max_ngb;
+    // lists are read four indices at a time, and the first 32 entries of each
+    // list by the 32 lanes of a warp
+    c.cap = std::max(32, (params->max_ngb + 7) / 8 * 8);
     c.launches = 0;
     c.prof = 0;
     for (int k = 0; k < GZ_NPASSES; ++k) {
         c.prof_ms[k] = 0.0;
         c.prof_calls[k] = 0;
     }
-    c.rcap = std::max(8, params->max_ngb / 2);
+    c.rcap = std::max(32, c.cap / 2 / 4 * 4);
     // per-box cell grids: cell length ~ cell_factor * H0 of the box
     int maxnc = 1;
     long long cells = 0;
@@ -301,7 +303,7 @@ gz_status gz_create(const gz_params* params, int32_t nboxes, const int64_t* coun
     const size_t Nz = (size_t)N;
     const size_t sz = params->precision == GZ_FP64 ? 8 : 4;
     const int nblk = (int)((N + 4095) / 4096);
-    c.hist_len = 256 * nblk;
+    c.hist_len = 256 * nblk + 256;  // per-block digit counts, then the digit totals
     struct Item {
         void** ptr;
         size_t bytes;
@@ -319,6 +321,8 @@ gz_status gz_create(const gz_params* params, int32_t nboxes, const int64_t* coun
         {(void**)&c.sh, sz * Nz},         {(void**)&c.sn, sz * Nz},
         {(void**)&c.srho, sz * Nz},       {(void**)&c.sP, sz * Nz},
         {(void**)&c.sc, sz * Nz},         {(void**)&c.sid, 8 * Nz},
+        {(void**)&c.spos, 4 * sz * Nz},   {(void**)&c.sprim, 4 * sz * Nz},
+        {(void**)&c.sprim2, 2 * sz * Nz},
         {(void**)&c.sbox, 4 * Nz},        {(void**)&c.iters, 4 * Nz},
         {(void**)&c.ncount, 4 * Nz},      {(void**)&c.nbr, 4 * Nz * (size_t)c.cap},
         {(void**)&c.rcount, 4 * Nz},      {(void**)&c.rnbr, 4 * Nz * (size_t)c.rcap},

@@ -4,6 +4,7 @@
 // both particles of a pair is either symmetric in its operands or evaluated
 // after ordering the pair by id, so both particles get bitwise-opposite
 // contributions (no atomics on rates).
+#include <algorithm>
 #include <type_traits>
 
 #include "gz_launch.cuh"
@@ -38,19 +39,37 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 
+// Pair-pass division and square roots: the FP32 path uses the hardware
+// reciprocal / reciprocal square root (about 2 ulp; deterministic, so both
+// particles of a pair still compute identical values); FP64 stays IEEE.
+__device__ __forceinline__ float pdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double pdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float psqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ double psqrt(double x) { return sqrt(x); }
+
 // --------------------------------------------------------------- O4 / O5
 // Bracketed Newton iteration on f(H) = (4 pi/3) H^3 n(H) - N_ngb, written as
 // (32/3)(1 + sum_j w(q_j)) - N_ngb with f' = (32/3) sum_j (-w'(q_j)) q_j / H.
-// The neighbour list of each evaluation is written as it is found; the last
-// evaluation's list (that of the returned H) is the one that remains.
+// The first evaluation scans the cells once with radius Rc = 1.05 H and keeps
+// (r^2, j) of the candidates inside Rc in shared memory; later evaluations
+// read only that cache (rebuilt if H grows past Rc).  A particle with more
+// than kDensCache candidates falls back to scanning the cells at every
+// evaluation.  The neighbour list of the returned H is written at the end.
+constexpr int kDensBlock = 64;
+constexpr int kDensCache = 48;
+
 template <typename T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kDensBlock)
     k_density(int N, Sorted<T> s, Grid g, KParams p, unsigned* __restrict__ nbr,
               int* __restrict__ ncount, int* __restrict__ iters, DevStatus* st) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ T c_r2[kDensCache][kDensBlock];
+    __shared__ unsigned c_j[kDensCache][kDensBlock];
+    const int t = threadIdx.x;
+    const int i = blockIdx.x * kDensBlock + t;
     if (i >= N) return;
     const BoxInfo bx = g.boxes[s.box[i]];
-    const T xi = s.x[i], yi = s.y[i], zi = s.z[i];
+    const P4<T> me = s.pos[i];
+    const T xi = me.x, yi = me.y, zi = me.z;
     double H = (double)s.h[i];
     if (!(H > 0.0) || !(H < p.h_lim)) {
         set_status(st, GZ_S_NONFINITE, GZ_C_NONFINITE, s.id[i]);
@@ -59,25 +78,57 @@ __global__ void __launch_bounds__(128)
     }
     const double C = 32.0 / 3.0;
     double lo = 0.0, hi = 0.0, S = 0.0, Hev = H;
-    bool has_lo = false, has_hi = false, conv = false, clamped = false;
-    int it, cnt = 0;
+    bool has_lo = false, has_hi = false, conv = false, clamped = false, cached = false;
+    T Rc = T(0);
+    int it, cnt = 0, ncache = 0;
     for (it = 1; it <= p.max_iter; ++it) {
         const T Ht = (T)H;
         const T H2 = Ht * Ht;
         const T iH = T(1) / Ht;
+        if (!cached || Ht > Rc) {
+            T R = Ht * T(1.05);
+            if (!(R < (T)p.h_lim)) R = max(Ht, (T)p.h_lim);
+            const T R2 = R * R;
+            int n = 0;
+            for_candidates<T>(g, bx, s.pos, i, xi, yi, zi, R,
+                              [&](int j, T, T, T, T r2) {
+                                  if (r2 < R2) {
+                                      if (n < kDensCache) {
+                                          c_r2[n][t] = r2;
+                                          c_j[n][t] = (unsigned)j;
+                                      }
+                                      ++n;
+                                  }
+                              });
+            Rc = R;
+            ncache = n;
+            cached = n <= kDensCache;
+        }
         Acc<T> sw;
         T sd = T(0);
         int c = 0;
-        for_candidates<T>(g, bx, s.x, s.y, s.z, i, xi, yi, zi, Ht,
-                          [&](int j, T, T, T, T r2) {
-                              if (r2 < H2) {
-                                  const T q = sqrt(r2) * iH;
-                                  sw.add(kern_w(q));
-                                  sd += -kern_dw(q) * q;
-                                  if (c < p.cap) nbr[(size_t)c * N + i] = (unsigned)j;
-                                  ++c;
-                              }
-                          });
+        if (cached) {
+            for (int k = 0; k < ncache; ++k) {
+                const T r2 = c_r2[k][t];
+                if (r2 < H2) {
+                    const T q = sqrt(r2) * iH;
+                    sw.add(kern_w(q));
+                    sd += -kern_dw(q) * q;
+                    ++c;
+                }
+            }
+        } else {
+            for_candidates<T>(g, bx, s.pos, i, xi, yi, zi, Ht,
+                              [&](int j, T, T, T, T r2) {
+                                  if (r2 < H2) {
+                                      const T q = sqrt(r2) * iH;
+                                      sw.add(kern_w(q));
+                                      sd += -kern_dw(q) * q;
+                                      if (c < p.cap) nbr[(size_t)i * p.cap + c] = (unsigned)j;
+                                      ++c;
+                                  }
+                              });
+        }
         cnt = c;
         S = sw.value();
         Hev = (double)Ht;
@@ -111,6 +162,17 @@ __global__ void __launch_bounds__(128)
         H = Hn;
     }
     if (it > p.max_iter) it = p.max_iter;
+    if (cached) {  // list of the returned H, in scan order
+        const T Ht = (T)Hev;
+        const T H2 = Ht * Ht;
+        int c = 0;
+        for (int k = 0; k < ncache; ++k) {
+            if (c_r2[k][t] < H2) {
+                if (c < p.cap) nbr[(size_t)i * p.cap + c] = c_j[k][t];
+                ++c;
+            }
+        }
+    }
     s.h[i] = (T)Hev;
     s.n[i] = (T)(8.0 * (1.0 + S) / (kPi * Hev * Hev * Hev));
     iters[i] = it;
@@ -133,10 +195,11 @@ __global__ void __launch_bounds__(128)
     const T Hi = s.h[i];
     const T H2 = Hi * Hi;
     int c = 0;
-    for_candidates<T>(g, bx, s.x, s.y, s.z, i, s.x[i], s.y[i], s.z[i], Hi,
+    const P4<T> me = s.pos[i];
+    for_candidates<T>(g, bx, s.pos, i, me.x, me.y, me.z, Hi,
                       [&](int j, T, T, T, T r2) {
                           if (r2 < H2) {
-                              if (c < p.cap) nbr[(size_t)c * N + i] = (unsigned)j;
+                              if (c < p.cap) nbr[(size_t)i * p.cap + c] = (unsigned)j;
                               ++c;
                           }
                       });
@@ -145,27 +208,35 @@ __global__ void __launch_bounds__(128)
 }
 
 // Reverse pairs (O10): j in N_i with r_ij >= H_j is appended to j's list.
+// Reads the packed positions, whose w component is the converged H.
 template <typename T>
 __global__ void k_reverse(int N, Sorted<T> s, KParams p, const unsigned* __restrict__ nbr,
                           const int* __restrict__ ncount, int* __restrict__ rcount,
                           unsigned* __restrict__ rnbr, DevStatus* st) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const T xi = s.x[i], yi = s.y[i], zi = s.z[i];
-    const T xim1 = xi - T(1), yim1 = yi - T(1), zim1 = zi - T(1);
+    const P4<T> me = s.pos[i];
+    const T xim1 = me.x - T(1), yim1 = me.y - T(1), zim1 = me.z - T(1);
     const int cnt = min(ncount[i], p.cap);
-    for (int k = 0; k < cnt; ++k) {
-        const int j = (int)nbr[(size_t)k * N + i];
-        const T Hj = s.h[j];
-        const T dx = mi_diff(s.x[j], xi, xim1), dy = mi_diff(s.y[j], yi, yim1),
-                dz = mi_diff(s.z[j], zi, zim1);
-        const T r2 = sep2(dx, dy, dz);
-        if (!(r2 < Hj * Hj)) {
-            const int slot = atomicAdd(&rcount[j], 1);
-            if (slot < p.rcap)
-                rnbr[(size_t)slot * N + j] = (unsigned)i;
-            else
-                set_status(st, GZ_S_NBR_OVERFLOW, GZ_C_NBR_OVERFLOW, s.id[j]);
+    const unsigned* L = nbr + (size_t)i * p.cap;
+    for (int k0 = 0; k0 < cnt; k0 += 4) {
+        const uint4 jj = *reinterpret_cast<const uint4*>(L + k0);
+        const unsigned js[4] = {jj.x, jj.y, jj.z, jj.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (k0 + u >= cnt) break;
+            const int j = (int)js[u];
+            const P4<T> q = s.pos[j];
+            const T dx = mi_diff(q.x, me.x, xim1), dy = mi_diff(q.y, me.y, yim1),
+                    dz = mi_diff(q.z, me.z, zim1);
+            const T r2 = sep2(dx, dy, dz);
+            if (!(r2 < q.w * q.w)) {
+                const int slot = atomicAdd(&rcount[j], 1);
+                if (slot < p.rcap)
+                    rnbr[(size_t)j * p.rcap + slot] = (unsigned)i;
+                else
+                    set_status(st, GZ_S_NBR_OVERFLOW, GZ_C_NBR_OVERFLOW, s.id[j]);
+            }
         }
     }
 }
@@ -176,14 +247,15 @@ __global__ void k_sort_rev(int N, const int* __restrict__ rcount, unsigned* __re
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int n = min(rcount[i], rcap);
+    unsigned* L = rnbr + (size_t)i * rcap;
     for (int a = 1; a < n; ++a) {
-        const unsigned v = rnbr[(size_t)a * N + i];
+        const unsigned v = L[a];
         int b = a - 1;
-        while (b >= 0 && rnbr[(size_t)b * N + i] > v) {
-            rnbr[(size_t)(b + 1) * N + i] = rnbr[(size_t)b * N + i];
+        while (b >= 0 && L[b] > v) {
+            L[b + 1] = L[b];
             --b;
         }
-        rnbr[(size_t)(b + 1) * N + i] = v;
+        L[b + 1] = v;
     }
 }
 
@@ -199,6 +271,9 @@ __global__ void k_prim(int N, Sorted<T> s, KParams p, DevStatus* st) {
     s.rho[i] = rho;
     s.P[i] = P;
     s.c[i] = c;
+    s.pos[i].w = s.h[i];
+    s.prim[i] = P4<T>{rho, s.vx[i], s.vy[i], s.vz[i]};
+    s.prim2[i] = P2<T>{P, c};
     if (!(rho > T(0)) || !(P > T(0)) || !finite_(c) || !finite_(s.vx[i]) || !finite_(s.vy[i]) ||
         !finite_(s.vz[i]))
         set_status(st, GZ_S_NONFINITE, GZ_C_NONFINITE, s.id[i]);
@@ -229,6 +304,8 @@ __device__ __forceinline__ void invert_sym(const A E[6], A B[6], A& det, A& kap)
 // signal-speed step (over N_i and the reverse list) and its per-box minimum.
 // Record (32 values): x y z H | 1/H knorm rho P | vx vy vz g0 | g1..g14 | B0..B5
 // with knorm = 8/(pi H^3 n^2) so that V_i psi_j(x_i) = knorm * w(r/H).
+// Neighbours are read four at a time (one 16-byte load of indices, then the
+// packed records of all four) so their loads are in flight together.
 template <typename T>
 __global__ void __launch_bounds__(128)
     k_gradients(int N, Sorted<T> s, const unsigned* __restrict__ nbr, const int* __restrict__ ncount,
@@ -241,11 +318,14 @@ __global__ void __launch_bounds__(128)
     int mybox = 0;
     if (active) {
         mybox = s.box[i];
-        const T xi = s.x[i], yi = s.y[i], zi = s.z[i];
+        const P4<T> me = s.pos[i];
+        const T xi = me.x, yi = me.y, zi = me.z, Hi = me.w;
         const T xim1 = xi - T(1), yim1 = yi - T(1), zim1 = zi - T(1);
-        const T Hi = s.h[i], ni = s.n[i];
-        const T Wi[5] = {s.rho[i], s.vx[i], s.vy[i], s.vz[i], s.P[i]};
-        const T ci = s.c[i];
+        const T ni = s.n[i];
+        const P4<T> pm = s.prim[i];
+        const P2<T> pm2 = s.prim2[i];
+        const T Wi[5] = {pm.x, pm.y, pm.z, pm.w, pm2.x};
+        const T ci = pm2.y;
         const T iH = T(1) / Hi;
         const T norm = T(8.0 / kPi) * iH * iH * iH / ni;
         T E[6] = {0, 0, 0, 0, 0, 0};
@@ -259,53 +339,67 @@ __global__ void __launch_bounds__(128)
         T vmax = T(0);
         bool any = false;
         const int cnt = min(ncount[i], p.cap);
-        for (int k = 0; k < cnt; ++k) {
-            const int j = (int)nbr[(size_t)k * N + i];
-            const T dx = mi_diff(s.x[j], xi, xim1), dy = mi_diff(s.y[j], yi, yim1),
-                    dz = mi_diff(s.z[j], zi, zim1);
-            const T r2 = sep2(dx, dy, dz);
-            const T r = sqrt(r2);
-            const T psi = norm * kern_w(r * iH);
-            const T pdx = psi * dx, pdy = psi * dy, pdz = psi * dz;
-            E[0] += pdx * dx;
-            E[1] += pdx * dy;
-            E[2] += pdx * dz;
-            E[3] += pdy * dy;
-            E[4] += pdy * dz;
-            E[5] += pdz * dz;
-            const T Wj[5] = {s.rho[j], s.vx[j], s.vy[j], s.vz[j], s.P[j]};
+        const unsigned* L = nbr + (size_t)i * p.cap;
+        for (int k0 = 0; k0 < cnt; k0 += 4) {
+            const uint4 jj = *reinterpret_cast<const uint4*>(L + k0);
+            const unsigned js[4] = {jj.x, jj.y, jj.z, jj.w};
+            P4<T> q[4], w[4];
+            P2<T> w2[4];
 #pragma unroll
-            for (int f = 0; f < 5; ++f) {
-                const T df = Wj[f] - Wi[f];
-                Sg[3 * f] += df * pdx;
-                Sg[3 * f + 1] += df * pdy;
-                Sg[3 * f + 2] += df * pdz;
-                fmax[f] = max(fmax[f], Wj[f]);
-                fmin[f] = min(fmin[f], Wj[f]);
+            for (int u = 0; u < 4; ++u) {
+                if (k0 + u < cnt) {
+                    q[u] = s.pos[js[u]];
+                    w[u] = s.prim[js[u]];
+                    w2[u] = s.prim2[js[u]];
+                }
             }
-            if (want_dt) {
-                const T vd = ((Wj[1] - Wi[1]) * dx + (Wj[2] - Wi[2]) * dy) + (Wj[3] - Wi[3]) * dz;
-                const T w = vd / r;
-                const T vs = ci + s.c[j] - min(w, T(0));
-                vmax = any ? max(vmax, vs) : vs;
-                any = true;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (k0 + u >= cnt) break;
+                const T dx = mi_diff(q[u].x, xi, xim1), dy = mi_diff(q[u].y, yi, yim1),
+                        dz = mi_diff(q[u].z, zi, zim1);
+                const T r2 = sep2(dx, dy, dz);
+                const T r = sqrt(r2);
+                const T psi = norm * kern_w(r * iH);
+                const T pdx = psi * dx, pdy = psi * dy, pdz = psi * dz;
+                E[0] += pdx * dx;
+                E[1] += pdx * dy;
+                E[2] += pdx * dz;
+                E[3] += pdy * dy;
+                E[4] += pdy * dz;
+                E[5] += pdz * dz;
+                const T Wj[5] = {w[u].x, w[u].y, w[u].z, w[u].w, w2[u].x};
+#pragma unroll
+                for (int f = 0; f < 5; ++f) {
+                    const T df = Wj[f] - Wi[f];
+                    Sg[3 * f] += df * pdx;
+                    Sg[3 * f + 1] += df * pdy;
+                    Sg[3 * f + 2] += df * pdz;
+                    fmax[f] = max(fmax[f], Wj[f]);
+                    fmin[f] = min(fmin[f], Wj[f]);
+                }
+                if (want_dt) {
+                    const T vd = ((Wj[1] - Wi[1]) * dx + (Wj[2] - Wi[2]) * dy) + (Wj[3] - Wi[3]) * dz;
+                    const T vs = ci + w2[u].y - min(vd / r, T(0));
+                    vmax = any ? max(vmax, vs) : vs;
+                    any = true;
+                }
             }
         }
         // O7: B = E^-1; FP64 re-do of E and its inverse when kappa > kappa_max
         T B[6], det, kap;
         invert_sym<T>(E, B, det, kap);
-        double g[15];
+        T gt[15];
         bool singular;
-        if (std::is_same<T, float>::value && !(kap <= (T)p.kappa_max)) {
+        if (sizeof(T) == 4 && !(kap <= (T)p.kappa_max)) {
             double E64[6] = {0, 0, 0, 0, 0, 0};
             const double xd = (double)xi, yd = (double)yi, zd = (double)zi;
             const double iHd = 1.0 / (double)Hi;
             const double normd = 8.0 / kPi * iHd * iHd * iHd / (double)ni;
             for (int k = 0; k < cnt; ++k) {
-                const int j = (int)nbr[(size_t)k * N + i];
-                const double dx = mi_diff((double)s.x[j], xd, 0.0),
-                             dy = mi_diff((double)s.y[j], yd, 0.0),
-                             dz = mi_diff((double)s.z[j], zd, 0.0);
+                const P4<T> q = s.pos[L[k]];
+                const double dx = mi_diff((double)q.x, xd, 0.0), dy = mi_diff((double)q.y, yd, 0.0),
+                             dz = mi_diff((double)q.z, zd, 0.0);
                 const double r = sqrt(sep2(dx, dy, dz));
                 const double psi = normd * kern_w(r * iHd);
                 E64[0] += psi * dx * dx;
@@ -325,18 +419,18 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
             for (int f = 0; f < 5; ++f) {
                 const double s0 = Sg[3 * f], s1 = Sg[3 * f + 1], s2 = Sg[3 * f + 2];
-                g[3 * f] = B64[0] * s0 + B64[1] * s1 + B64[2] * s2;
-                g[3 * f + 1] = B64[1] * s0 + B64[3] * s1 + B64[4] * s2;
-                g[3 * f + 2] = B64[2] * s0 + B64[4] * s1 + B64[5] * s2;
+                gt[3 * f] = (T)(B64[0] * s0 + B64[1] * s1 + B64[2] * s2);
+                gt[3 * f + 1] = (T)(B64[1] * s0 + B64[3] * s1 + B64[4] * s2);
+                gt[3 * f + 2] = (T)(B64[2] * s0 + B64[4] * s1 + B64[5] * s2);
             }
         } else {
             singular = !(det > T(0)) || !(kap <= T(1e8));
 #pragma unroll
             for (int f = 0; f < 5; ++f) {
                 const T s0 = Sg[3 * f], s1 = Sg[3 * f + 1], s2 = Sg[3 * f + 2];
-                g[3 * f] = B[0] * s0 + B[1] * s1 + B[2] * s2;
-                g[3 * f + 1] = B[1] * s0 + B[3] * s1 + B[4] * s2;
-                g[3 * f + 2] = B[2] * s0 + B[4] * s1 + B[5] * s2;
+                gt[3 * f] = B[0] * s0 + B[1] * s1 + B[2] * s2;
+                gt[3 * f + 1] = B[1] * s0 + B[3] * s1 + B[4] * s2;
+                gt[3 * f + 2] = B[2] * s0 + B[4] * s1 + B[5] * s2;
             }
         }
         if (singular) {
@@ -344,41 +438,49 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
             for (int q = 0; q < 6; ++q) B[q] = T(0);
 #pragma unroll
-            for (int q = 0; q < 15; ++q) g[q] = 0.0;
+            for (int q = 0; q < 15; ++q) gt[q] = T(0);
         }
-        T gt[15];
-#pragma unroll
-        for (int q = 0; q < 15; ++q) gt[q] = (T)g[q];
         // O9 limiter: alpha_f = min_j min(1, beta (f_ext - f_i) / (g . s_ij d))
         T al[5] = {T(1), T(1), T(1), T(1), T(1)};
         const T beta = (T)p.beta;
-        for (int k = 0; k < cnt; ++k) {
-            const int j = (int)nbr[(size_t)k * N + i];
-            const T dx = mi_diff(s.x[j], xi, xim1), dy = mi_diff(s.y[j], yi, yim1),
-                    dz = mi_diff(s.z[j], zi, zim1);
-            const T sij = Hi / (Hi + s.h[j]);
-            const T ox = sij * dx, oy = sij * dy, oz = sij * dz;
+        for (int k0 = 0; k0 < cnt; k0 += 4) {
+            const uint4 jj = *reinterpret_cast<const uint4*>(L + k0);
+            const unsigned js[4] = {jj.x, jj.y, jj.z, jj.w};
+            P4<T> q[4];
 #pragma unroll
-            for (int f = 0; f < 5; ++f) {
-                const T D = (gt[3 * f] * ox + gt[3 * f + 1] * oy) + gt[3 * f + 2] * oz;
-                T a = T(1);
-                if (D > T(0))
-                    a = min(T(1), beta * (fmax[f] - Wi[f]) / D);
-                else if (D < T(0))
-                    a = min(T(1), beta * (fmin[f] - Wi[f]) / D);
-                al[f] = min(al[f], a);
+            for (int u = 0; u < 4; ++u)
+                if (k0 + u < cnt) q[u] = s.pos[js[u]];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (k0 + u >= cnt) break;
+                const T dx = mi_diff(q[u].x, xi, xim1), dy = mi_diff(q[u].y, yi, yim1),
+                        dz = mi_diff(q[u].z, zi, zim1);
+                const T sij = Hi / (Hi + q[u].w);
+                const T ox = sij * dx, oy = sij * dy, oz = sij * dz;
+#pragma unroll
+                for (int f = 0; f < 5; ++f) {
+                    const T D = (gt[3 * f] * ox + gt[3 * f + 1] * oy) + gt[3 * f + 2] * oz;
+                    T a = T(1);
+                    if (D > T(0))
+                        a = min(T(1), beta * (fmax[f] - Wi[f]) / D);
+                    else if (D < T(0))
+                        a = min(T(1), beta * (fmin[f] - Wi[f]) / D);
+                    al[f] = min(al[f], a);
+                }
             }
         }
         if (want_dt) {
             const int rc = min(rcount[i], p.rcap);
+            const unsigned* RL = rnbr + (size_t)i * p.rcap;
             for (int k = 0; k < rc; ++k) {
-                const int j = (int)rnbr[(size_t)k * N + i];
-                const T dx = mi_diff(s.x[j], xi, xim1), dy = mi_diff(s.y[j], yi, yim1),
-                        dz = mi_diff(s.z[j], zi, zim1);
+                const int j = (int)RL[k];
+                const P4<T> q = s.pos[j];
+                const P4<T> w = s.prim[j];
+                const T dx = mi_diff(q.x, xi, xim1), dy = mi_diff(q.y, yi, yim1),
+                        dz = mi_diff(q.z, zi, zim1);
                 const T r = sqrt(sep2(dx, dy, dz));
-                const T vd = ((s.vx[j] - Wi[1]) * dx + (s.vy[j] - Wi[2]) * dy) + (s.vz[j] - Wi[3]) * dz;
-                const T w = vd / r;
-                const T vs = ci + s.c[j] - min(w, T(0));
+                const T vd = ((w.y - Wi[1]) * dx + (w.z - Wi[2]) * dy) + (w.w - Wi[3]) * dz;
+                const T vs = ci + s.prim2[j].y - min(vd / r, T(0));
                 vmax = any ? max(vmax, vs) : vs;
                 any = true;
             }
@@ -494,7 +596,7 @@ __device__ __forceinline__ void face_state(const T (&a)[kRecord], T s, T dx, T d
         F[f] = W[f] + ((a[11 + 3 * f] * ox + a[12 + 3 * f] * oy) + a[13 + 3 * f] * oz);
     if (hancock) {
         const T div = (a[11 + 3] + a[11 + 7]) + a[11 + 11];
-        const T ir = T(1) / a[6];
+        const T ir = pdiv(T(1), a[6]);
         F[0] += hdt * (-a[6] * div);
         F[1] += hdt * (-a[11 + 12] * ir);
         F[2] += hdt * (-a[11 + 13] * ir);
@@ -512,7 +614,7 @@ __device__ __forceinline__ bool pair_rates(const T (&a)[kRecord], const T (&b)[k
     const T dy = mi_diff(b[1], a[1], a[1] - T(1));
     const T dz = mi_diff(b[2], a[2], a[2] - T(1));
     const T r2 = sep2(dx, dy, dz);
-    const T r = sqrt(r2);
+    const T r = psqrt(r2);
     const T ca = r2 < a[3] * a[3] ? a[5] * kern_w(r * a[4]) : T(0);
     const T cb = r2 < b[3] * b[3] ? b[5] * kern_w(r * b[4]) : T(0);
     const T Bax = (a[26] * dx + a[27] * dy) + a[28] * dz;
@@ -526,11 +628,11 @@ __device__ __forceinline__ bool pair_rates(const T (&a)[kRecord], const T (&b)[k
     const T A2 = add_rn(mul_rn(ca, Baz), mul_rn(cb, Bbz));
     const T Aq = sep2(A0, A1, A2);
     if (!(Aq > T(0))) return false;
-    const T Am = sqrt(Aq);
-    const T iA = T(1) / Am;
+    const T Am = psqrt(Aq);
+    const T iA = pdiv(T(1), Am);
     const T n0 = A0 * iA, n1 = A1 * iA, n2 = A2 * iA;
     const T Hs = a[3] + b[3];
-    const T sa = a[3] / Hs, sb = b[3] / Hs;
+    const T sa = pdiv(a[3], Hs), sb = pdiv(b[3], Hs);
     T Fa[5], Fb[5];
     face_state(a, sa, dx, dy, dz, hdt, gam, hancock, Fa);
     face_state(b, sb, -dx, -dy, -dz, hdt, gam, hancock, Fb);
@@ -567,11 +669,11 @@ __device__ __forceinline__ bool pair_rates(const T (&a)[kRecord], const T (&b)[k
     const T uR = ((FR[1] - vfx) * nx + (FR[2] - vfy) * ny) + (FR[3] - vfz) * nz;
     // O12 HLLC with Davis wave speeds
     const T rL = FL[0], PL = FL[4], rR = FR[0], PR = FR[4];
-    const T cL = sqrt(gam * PL / rL), cR = sqrt(gam * PR / rR);
+    const T cL = psqrt(pdiv(gam * PL, rL)), cR = psqrt(pdiv(gam * PR, rR));
     const T SL = min(uL - cL, uR - cR), SR = max(uL + cL, uR + cR);
     const T num = ((PR - PL) + rL * uL * (SL - uL)) - rR * uR * (SR - uR);
     const T den = rL * (SL - uL) - rR * (SR - uR);
-    const T ss = num / den;
+    const T ss = pdiv(num, den);
     T ps = PL + rL * (SL - uL) * (ss - uL);
     if (ps < T(0)) {
         ps = T(0);
@@ -585,8 +687,14 @@ __device__ __forceinline__ bool pair_rates(const T (&a)[kRecord], const T (&b)[k
     return true;
 }
 
+// One thread per particle over its pairs N_i then R_i (both contiguous
+// lists, read four indices per 16-byte load).  Contributions are summed in
+// the working precision over runs of 8 pairs and each run is added to FP64
+// accumulators.
+constexpr int kFluxBlock = 128;
+
 template <typename T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kFluxBlock)
     k_fluxes(int N, const T* __restrict__ rec, const long long* __restrict__ sid,
              const int* __restrict__ sbox, const unsigned* __restrict__ nbr,
              const int* __restrict__ ncount, const unsigned* __restrict__ rnbr,
@@ -602,30 +710,39 @@ __global__ void __launch_bounds__(128)
     const bool hancock = p.hancock != 0;
     T part[4] = {T(0), T(0), T(0), T(0)};
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    int np = 0, fl = 0, nfall = 0, nneg = 0;
-    const int cnt = min(ncount[i], p.cap);
-    const int rc = min(rcount[i], p.rcap);
-    for (int k = 0; k < cnt + rc; ++k) {
-        const int j = k < cnt ? (int)nbr[(size_t)k * N + i] : (int)rnbr[(size_t)(k - cnt) * N + i];
-        T b[kRecord];
-        load_rec(rec + (size_t)j * kRecord, b);
-        T dp[3], dE;
-        fl = 0;
-        if (pair_rates(a, b, idi < sid[j], hdt, gam, hancock, dp, dE, fl)) {
-            part[0] += dp[0];
-            part[1] += dp[1];
-            part[2] += dp[2];
-            part[3] += dE;
-        }
-        nfall += fl & 1;
-        nneg += (fl >> 1) & 1;
-        if (++np == 8) {
+    int np = 0, nfall = 0, nneg = 0;
+#pragma unroll 1
+    for (int list = 0; list < 2; ++list) {
+        const unsigned* L = list == 0 ? nbr + (size_t)i * p.cap : rnbr + (size_t)i * p.rcap;
+        const int cnt = list == 0 ? min(ncount[i], p.cap) : min(rcount[i], p.rcap);
+        for (int k0 = 0; k0 < cnt; k0 += 4) {
+            const uint4 jj = *reinterpret_cast<const uint4*>(L + k0);
+            const unsigned js[4] = {jj.x, jj.y, jj.z, jj.w};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                acc[q] += (double)part[q];
-                part[q] = T(0);
+            for (int u = 0; u < 4; ++u) {
+                if (k0 + u >= cnt) break;
+                const int j = (int)js[u];
+                T b[kRecord];
+                load_rec(rec + (size_t)j * kRecord, b);
+                T dp[3], dE;
+                int fl = 0;
+                if (pair_rates(a, b, idi < sid[j], hdt, gam, hancock, dp, dE, fl)) {
+                    part[0] += dp[0];
+                    part[1] += dp[1];
+                    part[2] += dp[2];
+                    part[3] += dE;
+                }
+                nfall += fl & 1;
+                nneg += (fl >> 1) & 1;
+                if (++np == 8) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        acc[q] += (double)part[q];
+                        part[q] = T(0);
+                    }
+                    np = 0;
+                }
             }
-            np = 0;
         }
     }
 #pragma unroll
@@ -650,11 +767,44 @@ __device__ __forceinline__ double wrap1(double v) {
     if (v >= 1.0) v -= 1.0;
     return v;
 }
-template <typename T>
-__device__ __forceinline__ T to_box(double v) {
-    T t = (T)v;
-    if (t >= T(1)) t -= T(1);
-    return t;
+
+// FP64 state: the literal conserved update, like the oracle.
+__device__ __forceinline__ void update_one(double m, double& x, double& y, double& z, double& vx,
+                                           double& vy, double& vz, double& u, double dpx, double dpy,
+                                           double dpz, double dE, double dt) {
+    const double v2 = (vx * vx + vy * vy) + vz * vz;
+    const double E = m * (u + 0.5 * v2) + dt * dE;
+    const double nx = (m * vx + dt * dpx) / m, ny = (m * vy + dt * dpy) / m, nz = (m * vz + dt * dpz) / m;
+    x = wrap1(x + dt * (0.5 * (vx + nx)));
+    y = wrap1(y + dt * (0.5 * (vy + ny)));
+    z = wrap1(z + dt * (0.5 * (vz + nz)));
+    u = E / m - 0.5 * ((nx * nx + ny * ny) + nz * nz);
+    vx = nx;
+    vy = ny;
+    vz = nz;
+}
+// FP32 state: the same update written with the increments dv = dt (dp/dt)/m
+// and du = dt (dE/dt)/m - dv . (v + dv/2), which is E/m - v_new^2/2 - u
+// without the cancellation of the literal form.
+__device__ __forceinline__ float wrapf(float v) {
+    if (v < 0.f) v += 1.f;
+    if (v >= 1.f) v -= 1.f;
+    return v;
+}
+__device__ __forceinline__ void update_one(float m, float& x, float& y, float& z, float& vx,
+                                           float& vy, float& vz, float& u, double dpx, double dpy,
+                                           double dpz, double dE, double dt) {
+    const float dtf = (float)dt, im = 1.f / m;
+    const float dvx = dtf * (float)dpx * im, dvy = dtf * (float)dpy * im, dvz = dtf * (float)dpz * im;
+    const float hx = vx + 0.5f * dvx, hy = vy + 0.5f * dvy, hz = vz + 0.5f * dvz;
+    const float du = dtf * (float)dE * im - ((dvx * hx + dvy * hy) + dvz * hz);
+    x = wrapf(x + dtf * hx);
+    y = wrapf(y + dtf * hy);
+    z = wrapf(z + dtf * hz);
+    u = u + du;
+    vx += dvx;
+    vy += dvy;
+    vz += dvz;
 }
 
 template <typename T>
@@ -665,34 +815,23 @@ __global__ void k_update(int N, Sorted<T> s, const double* __restrict__ dpdt,
     if (i >= N) return;
     const unsigned o = s.orig[i];
     const int b = s.box[i];
-    const double dt = dt_use[b];
-    const double m = (double)s.m[i];
-    const double vx = (double)s.vx[i], vy = (double)s.vy[i], vz = (double)s.vz[i];
-    const double u = (double)s.u[i];
-    const double v2 = (vx * vx + vy * vy) + vz * vz;
-    const double E = m * (u + 0.5 * v2) + dt * dEdt[i];
-    const double px = m * vx + dt * dpdt[i];
-    const double py = m * vy + dt * dpdt[(size_t)N + i];
-    const double pz = m * vz + dt * dpdt[2 * (size_t)N + i];
-    const double nx = px / m, ny = py / m, nz = pz / m;
-    const double x = wrap1((double)s.x[i] + dt * (0.5 * (vx + nx)));
-    const double y = wrap1((double)s.y[i] + dt * (0.5 * (vy + ny)));
-    const double z = wrap1((double)s.z[i] + dt * (0.5 * (vz + nz)));
-    const double un = E / m - 0.5 * ((nx * nx + ny * ny) + nz * nz);
-    ((T*)out.x)[o] = to_box<T>(x);
-    ((T*)out.y)[o] = to_box<T>(y);
-    ((T*)out.z)[o] = to_box<T>(z);
-    ((T*)out.vx)[o] = (T)nx;
-    ((T*)out.vy)[o] = (T)ny;
-    ((T*)out.vz)[o] = (T)nz;
-    ((T*)out.u)[o] = (T)un;
+    T x = s.x[i], y = s.y[i], z = s.z[i], vx = s.vx[i], vy = s.vy[i], vz = s.vz[i], u = s.u[i];
+    update_one(s.m[i], x, y, z, vx, vy, vz, u, dpdt[i], dpdt[(size_t)N + i],
+               dpdt[2 * (size_t)N + i], dEdt[i], dt_use[b]);
+    ((T*)out.x)[o] = x;
+    ((T*)out.y)[o] = y;
+    ((T*)out.z)[o] = z;
+    ((T*)out.vx)[o] = vx;
+    ((T*)out.vy)[o] = vy;
+    ((T*)out.vz)[o] = vz;
+    ((T*)out.u)[o] = u;
     ((T*)out.h)[o] = s.h[i];
-    if (!(un > 0.0)) {
+    if (!(u > T(0))) {
         atomicAdd(&box_hits[b], 1);
         set_status(st, GZ_S_UFLOOR, GZ_C_UFLOOR, -1);
     }
-    if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(nx) && isfinite(ny) &&
-          isfinite(nz) && isfinite(un)))
+    if (!(finite_(x) && finite_(y) && finite_(z) && finite_(vx) && finite_(vy) && finite_(vz) &&
+          finite_(u)))
         set_status(st, GZ_S_NONFINITE, GZ_C_NONFINITE, s.id[i]);
 }
 
@@ -793,7 +932,7 @@ __global__ void k_get_nbrs(int N, const unsigned* __restrict__ orig, const long 
     if (!ids_out) return;
     const int m = min(min(c, cap_in), cap);
     for (int k = 0; k < cap; ++k)
-        ids_out[(size_t)k * N + o] = k < m ? (int64_t)sid[nbr[(size_t)k * N + i]] : (int64_t)-1;
+        ids_out[(size_t)k * N + o] = k < m ? (int64_t)sid[nbr[(size_t)i * cap_in + k]] : (int64_t)-1;
 }
 
 __global__ void k_pairs(int N, const int* __restrict__ ncount, const int* __restrict__ rcount,
@@ -841,8 +980,8 @@ static Grid grid_of(const Ctx& c) {
 template <typename T>
 cudaError_t run_density(Ctx& c) {
     c.launches += 1;
-    k_density<T><<<blocks(c.N, 128), 128, 0, c.stream>>>(c.N, sorted_view<T>(c), grid_of(c), kparams(c),
-                                                          c.nbr, c.ncount, c.iters, c.status);
+    k_density<T><<<blocks(c.N, kDensBlock), kDensBlock, 0, c.stream>>>(
+        c.N, sorted_view<T>(c), grid_of(c), kparams(c), c.nbr, c.ncount, c.iters, c.status);
     return cudaGetLastError();
 }
 
@@ -898,9 +1037,9 @@ cudaError_t run_grad_out(Ctx& c, T* grad, T* B) {
 template <typename T>
 cudaError_t run_fluxes(Ctx& c) {
     c.launches += 1;
-    k_fluxes<T><<<blocks(c.N, 128), 128, 0, c.stream>>>(c.N, (const T*)c.rec, c.sid, c.sbox, c.nbr,
-                                                         c.ncount, c.rnbr, c.rcount, kparams(c),
-                                                         c.dt_use, c.dpdt, c.dEdt, c.status);
+    k_fluxes<T><<<blocks(c.N, kFluxBlock), kFluxBlock, 0, c.stream>>>(
+        c.N, (const T*)c.rec, c.sid, c.sbox, c.nbr, c.ncount, c.rnbr, c.rcount, kparams(c), c.dt_use,
+        c.dpdt, c.dEdt, c.status);
     return cudaGetLastError();
 }
 

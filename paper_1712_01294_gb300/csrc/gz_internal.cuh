@@ -37,6 +37,16 @@ struct KParams {
     int hancock, max_iter, cap, rcap;
 };
 
+// Packed per-particle records (one 16-byte-aligned vector load each).
+template <typename T>
+struct alignas(16) P4 {
+    T x, y, z, w;
+};
+template <typename T>
+struct alignas(2 * sizeof(T)) P2 {
+    T x, y;
+};
+
 // Sorted-order views the kernels share.
 template <typename T>
 struct Sorted {
@@ -45,6 +55,9 @@ struct Sorted {
     unsigned* orig;     // caller index of sorted particle
     int* box;           // box of sorted particle
     T *n, *rho, *P, *c;
+    P4<T>* pos;         // (x, y, z, H)
+    P4<T>* prim;        // (rho, vx, vy, vz)
+    P2<T>* prim2;       // (P, c)
 };
 
 struct Grid {
@@ -76,13 +89,14 @@ struct Ctx {
     int* box_of;  // caller order
     // sorted state (working precision) and derived per-particle data
     void *sx, *sy, *sz, *svx, *svy, *svz, *sm, *su, *sh, *sn, *srho, *sP, *sc;
+    void *spos, *sprim, *sprim2;  // packed records P4 (x y z H), P4 (rho v), P2 (P c)
     long long* sid;
     int* sbox;
     int* iters;
     int* ncount;
-    unsigned* nbr;  // [cap][N]
+    unsigned* nbr;  // [N][cap], particle i's list contiguous
     int* rcount;
-    unsigned* rnbr;  // [rcap][N]
+    unsigned* rnbr;  // [N][rcap]
     void* rec;       // [N][kRecord] working precision
     double* dpdt;    // [3][N] sorted
     double* dEdt;    // [N] sorted
@@ -170,45 +184,66 @@ __device__ __forceinline__ unsigned long long dbits(double v) {
 
 // Loop over all candidates j != self in the cells that overlap the cube
 // [x - R, x + R] of particle self's box, calling fn(j, dx, dy, dz, r2).
+// FP32 with a range well inside half the box: the periodic shift is chosen
+// per cell row instead of per candidate, d = (x_j + a) - b with
+// (a, b) = (0, x_i), (-1, x_i) for cells wrapped below 0 (x_j - 1 is exact
+// there) or (0, x_i - 1) for cells wrapped above 1 (x_i - 1 is exact): the
+// same correctly rounded offsets mi_diff gives, at a third of the cost.
 template <typename T, typename F>
-__device__ __forceinline__ void for_candidates(const Grid& g, const BoxInfo& bx, const T* __restrict__ x,
-                                               const T* __restrict__ y, const T* __restrict__ z,
-                                               int self, T xi, T yi, T zi, T R, F&& fn) {
+__device__ __forceinline__ void for_candidates(const Grid& g, const BoxInfo& bx,
+                                               const P4<T>* __restrict__ pos, int self, T xi, T yi,
+                                               T zi, T R, F&& fn) {
     const int nc = bx.nc;
     const int2* __restrict__ cells = g.cells + bx.cell_off;
-    int lo[3], hi[3];
-    const double pos[3] = {(double)xi, (double)yi, (double)zi};
-    const double Rd = (double)R;
     // positions outside [0, 1] (flagged by the binning pass) see no candidates
-    if (!(pos[0] >= 0.0 && pos[0] <= 1.0 && pos[1] >= 0.0 && pos[1] <= 1.0 && pos[2] >= 0.0 &&
-          pos[2] <= 1.0 && Rd >= 0.0))
+    if (!(xi >= T(0) && xi <= T(1) && yi >= T(0) && yi <= T(1) && zi >= T(0) && zi <= T(1) &&
+          R >= T(0)))
         return;
-    const bool full = !(Rd < 0.5);  // (also catches non-finite R)
+    const bool full = !(R < T(0.5));  // (also catches non-finite R)
+    const T c3[3] = {xi, yi, zi};
+    int lo[3], hi[3];
+    bool wraps_all = full;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        lo[a] = full ? 0 : (int)floor((pos[a] - Rd) * nc - 1e-3);
-        hi[a] = full ? nc - 1 : (int)floor((pos[a] + Rd) * nc + 1e-3);
+        lo[a] = full ? 0 : (int)floor((c3[a] - R) * (T)nc - T(1e-3));
+        hi[a] = full ? nc - 1 : (int)floor((c3[a] + R) * (T)nc + T(1e-3));
         if (hi[a] - lo[a] + 1 >= nc) {
             lo[a] = 0;
             hi[a] = nc - 1;
+            wraps_all = true;
         }
     }
     const T xim1 = xi - T(1), yim1 = yi - T(1), zim1 = zi - T(1);
+    const bool percell = sizeof(T) == 4 && !wraps_all && (T(2) * R + T(2) / (T)nc < T(0.5));
     for (int cz = lo[2]; cz <= hi[2]; ++cz) {
         const int wz = cz < 0 ? cz + nc : (cz >= nc ? cz - nc : cz);
+        const T az = cz < 0 ? T(-1) : T(0), bz = cz >= nc ? zim1 : zi;
         for (int cy = lo[1]; cy <= hi[1]; ++cy) {
             const int wy = cy < 0 ? cy + nc : (cy >= nc ? cy - nc : cy);
+            const T ay = cy < 0 ? T(-1) : T(0), by = cy >= nc ? yim1 : yi;
             const int row = (wz * nc + wy) * nc;
             for (int cx = lo[0]; cx <= hi[0]; ++cx) {
                 const int wx = cx < 0 ? cx + nc : (cx >= nc ? cx - nc : cx);
+                const T ax = cx < 0 ? T(-1) : T(0), bxx = cx >= nc ? xim1 : xi;
                 const int2 se = cells[row + wx];
-                for (int j = se.x; j < se.y; ++j) {
-                    if (j == self) continue;
-                    T dx = mi_diff(x[j], xi, xim1);
-                    T dy = mi_diff(y[j], yi, yim1);
-                    T dz = mi_diff(z[j], zi, zim1);
-                    T r2 = sep2(dx, dy, dz);
-                    fn(j, dx, dy, dz, r2);
+                if (percell) {
+                    for (int j = se.x; j < se.y; ++j) {
+                        if (j == self) continue;
+                        const P4<T> q = pos[j];
+                        const T dx = (q.x + ax) - bxx;
+                        const T dy = (q.y + ay) - by;
+                        const T dz = (q.z + az) - bz;
+                        fn(j, dx, dy, dz, sep2(dx, dy, dz));
+                    }
+                } else {
+                    for (int j = se.x; j < se.y; ++j) {
+                        if (j == self) continue;
+                        const P4<T> q = pos[j];
+                        const T dx = mi_diff(q.x, xi, xim1);
+                        const T dy = mi_diff(q.y, yi, yim1);
+                        const T dz = mi_diff(q.z, zi, zim1);
+                        fn(j, dx, dy, dz, sep2(dx, dy, dz));
+                    }
                 }
             }
         }

@@ -24,7 +24,7 @@ constexpr int kCap = 32;          // neighbour-list slots (lists are not returne
 constexpr int kMaxDevices = 64;
 
 constexpr size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
-constexpr size_t kHistLen = 256 * ((kMaxN + 4095) / 4096);
+constexpr size_t kHistLen = 256 * ((kMaxN + 4095) / 4096) + 256;  // counts + digit totals
 // Worst case (FP64) of every slice the density pass touches.
 constexpr size_t kScratchBytes =
     4 * al(4 * (size_t)kMaxN)                          // keys, keys_alt, vals, vals_alt
@@ -33,13 +33,14 @@ constexpr size_t kScratchBytes =
     + al(sizeof(BoxInfo))                              // box table
     + al(sizeof(int2) * (size_t)kMaxCells)             // cell ranges
     + 5 * al(8 * (size_t)kMaxN)                        // sorted x, y, z, h, n
+    + al(32 * (size_t)kMaxN)                           // packed positions (x, y, z, H)
     + al(8 * (size_t)kMaxN)                            // sorted ids
     + 3 * al(4 * (size_t)kMaxN)                        // sorted box, iterations, counts
     + al(4 * (size_t)kMaxN * kCap)                     // neighbour lists
     + al(sizeof(DevStatus));
 
 // The scratch itself: every GPU that loads the library holds these bytes
-// (7,086,592 B, about 7.1 MB) until the process exits.  All calls share it.
+// (8,136,192 B, about 8.1 MB) until the process exits.  All calls share it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mu;
@@ -114,6 +115,7 @@ gz_status run(const gz_params* prm, int N, gz_particles* p, void* n_out, int32_t
     c.sz = take(8 * Nz);
     c.sh = take(8 * Nz);
     c.sn = take(8 * Nz);
+    c.spos = take(32 * Nz);
     c.sid = (long long*)take(8 * Nz);
     c.sbox = (int*)take(4 * Nz);
     c.iters = (int*)take(4 * Nz);
@@ -122,6 +124,7 @@ gz_status run(const gz_params* prm, int N, gz_particles* p, void* n_out, int32_t
     c.status = (DevStatus*)take(sizeof(DevStatus));
     // the density pass never touches these
     c.svx = c.svy = c.svz = c.sm = c.su = c.srho = c.sP = c.sc = nullptr;
+    c.sprim = c.sprim2 = nullptr;
     c.rcount = nullptr;
     c.rnbr = nullptr;
     c.rec = nullptr;

@@ -33,9 +33,9 @@ __device__ __forceinline__ unsigned compact3(unsigned v) {
 
 template <typename T>
 __device__ __forceinline__ int cell_coord(T v, int nc) {
-    double s = floor((double)v * nc);
-    if (!(s >= 0.0)) return 0;  // also NaN
-    if (s > (double)(nc - 1)) return nc - 1;
+    T s = floor(v * (T)nc);
+    if (!(s >= T(0))) return 0;  // also NaN
+    if (s > (T)(nc - 1)) return nc - 1;
     return (int)s;
 }
 
@@ -71,39 +71,59 @@ __global__ void k_rs_hist(const unsigned* __restrict__ keys, int N, int shift,
     for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t * nblk + blockIdx.x] = h[t];
 }
 
-// Exclusive prefix sum of n values by one block of 1024 threads.
-__global__ void k_rs_scan(unsigned* __restrict__ data, int n) {
-    __shared__ unsigned part[1024];
-    const int t = threadIdx.x;
-    const int per = (n + 1023) / 1024;
-    const int b = t * per;
-    const int e = min(b + per, n);
-    unsigned s = 0;
-    for (int k = b; k < e; ++k) s += data[k];
-    part[t] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        unsigned v = t >= off ? part[t - off] : 0u;
+// Exclusive scan of one digit's row hist[d][0..nblk) (block d), and the row
+// total into totals[d].
+__global__ void k_rs_rows(unsigned* __restrict__ hist, int nblk, unsigned* __restrict__ totals) {
+    __shared__ unsigned wsum[kSortWarps];
+    __shared__ unsigned base_s;
+    unsigned* row = hist + (size_t)blockIdx.x * nblk;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    unsigned running = 0;
+    for (int b0 = 0; b0 < nblk; b0 += kSortThreads) {
+        const int b = b0 + t;
+        const unsigned v = b < nblk ? row[b] : 0u;
+        unsigned x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
         __syncthreads();
-        part[t] += v;
+        if (t == 0) {
+            unsigned acc = 0;
+            for (int w = 0; w < kSortWarps; ++w) {
+                const unsigned ws = wsum[w];
+                wsum[w] = acc;
+                acc += ws;
+            }
+            base_s = acc;
+        }
+        __syncthreads();
+        if (b < nblk) row[b] = running + wsum[warp] + x - v;
+        running += base_s;
         __syncthreads();
     }
-    unsigned run = part[t] - s;  // exclusive
-    for (int k = b; k < e; ++k) {
-        unsigned v = data[k];
-        data[k] = run;
-        run += v;
-    }
+    if (t == 0) totals[blockIdx.x] = running;
 }
 
 // Stable scatter: each warp owns a contiguous sub-tile and walks it in order;
 // lanes with equal digits are ranked with __match_any_sync.
 __global__ void k_rs_scatter(const unsigned* __restrict__ kin, const unsigned* __restrict__ vin,
                              int N, int shift, const unsigned* __restrict__ hist, int nblk,
-                             unsigned* __restrict__ kout, unsigned* __restrict__ vout) {
+                             const unsigned* __restrict__ totals, unsigned* __restrict__ kout,
+                             unsigned* __restrict__ vout) {
     __shared__ unsigned cnt[kSortWarps][256];
+    __shared__ unsigned dbase[256];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int t = threadIdx.x; t < kSortWarps * 256; t += blockDim.x) (&cnt[0][0])[t] = 0;
+    if (threadIdx.x == 0) {  // exclusive scan of the 256 digit totals
+        unsigned acc = 0;
+        for (int d = 0; d < 256; ++d) {
+            dbase[d] = acc;
+            acc += totals[d];
+        }
+    }
     __syncthreads();
     const int wbase = blockIdx.x * kSortTile + warp * kSortPerWarp;
     for (int c = 0; c < kSortPerWarp; c += 32) {
@@ -112,7 +132,7 @@ __global__ void k_rs_scatter(const unsigned* __restrict__ kin, const unsigned* _
     }
     __syncthreads();
     for (int d = threadIdx.x; d < 256; d += blockDim.x) {
-        unsigned run = hist[d * nblk + blockIdx.x];
+        unsigned run = dbase[d] + hist[d * nblk + blockIdx.x];
         for (int w = 0; w < kSortWarps; ++w) {
             unsigned v = cnt[w][d];
             cnt[w][d] = run;
@@ -159,6 +179,7 @@ __global__ void k_permute(int N, const unsigned* __restrict__ skeys,
     if (p.m) s.m[i] = ((const T*)p.m)[src];
     if (p.u) s.u[i] = ((const T*)p.u)[src];
     s.h[i] = ((const T*)p.h)[src];
+    s.pos[i] = P4<T>{s.x[i], s.y[i], s.z[i], s.h[i]};
     s.id[i] = (long long)p.id[src];
     if (n_in) s.n[i] = ((const T*)n_in)[src];
     s.orig[i] = src;
@@ -205,6 +226,9 @@ Sorted<T> sorted_view(Ctx& c) {
     s.rho = (T*)c.srho;
     s.P = (T*)c.sP;
     s.c = (T*)c.sc;
+    s.pos = (P4<T>*)c.spos;
+    s.prim = (P4<T>*)c.sprim;
+    s.prim2 = (P2<T>*)c.sprim2;
     return s;
 }
 template Sorted<float> sorted_view<float>(Ctx&);
@@ -222,9 +246,10 @@ cudaError_t sort_and_bin(Ctx& c, const gz_particles& p, const void* n_in) {
     c.launches += 2 + 3 * ((total_bits + 7) / 8);
     unsigned *ki = c.keys, *vi = c.vals, *ko = c.keys_alt, *vo = c.vals_alt;
     for (int shift = 0; shift < total_bits; shift += 8) {
+        unsigned* totals = c.hist + 256 * (size_t)nblk;
         k_rs_hist<<<nblk, kSortThreads, 0, st>>>(ki, N, shift, c.hist, nblk);
-        k_rs_scan<<<1, 1024, 0, st>>>(c.hist, 256 * nblk);
-        k_rs_scatter<<<nblk, kSortThreads, 0, st>>>(ki, vi, N, shift, c.hist, nblk, ko, vo);
+        k_rs_rows<<<256, kSortThreads, 0, st>>>(c.hist, nblk, totals);
+        k_rs_scatter<<<nblk, kSortThreads, 0, st>>>(ki, vi, N, shift, c.hist, nblk, totals, ko, vo);
         unsigned* t = ki;
         ki = ko;
         ko = t;
