@@ -195,20 +195,42 @@ def turbulence(n: int = 128, seed: int = 1714, gamma: float = GAMMA, mach: float
 
 
 def kh(n: int = 64, seed: int = 1715, gamma: float = GAMMA, amp: float = 0.01,
-       jitter: float = 0.1) -> Particles:
+       jitter: float = 0.1, smooth: float = 0.0) -> Particles:
+    """Kelvin-Helmholtz layer.  smooth > 0 gives the differentiable variant:
+    tanh interfaces of that width, and 1 % smooth modulations of P and vz so
+    that no field is exactly uniform (a uniform field is a kink of the slope
+    limiter, where the step has no derivative)."""
     rng = np.random.default_rng(seed)
     x, y, z, _ = lattice(n, rng, jitter)
     N = x.size
     phi = float(rng.uniform(0.0, 1.0))
-    inside = np.abs(y - 0.5) < 0.25
-    rho = np.where(inside, 2.0, 1.0)
-    vx = np.where(inside, 0.5, -0.5)
+    if smooth > 0.0:
+        inside = 0.5 * (np.tanh((y - 0.25) / smooth) - np.tanh((y - 0.75) / smooth))
+    else:
+        inside = (np.abs(y - 0.5) < 0.25).astype(np.float64)
+    rho = 1.0 + inside
+    vx = -0.5 + inside
     vy = amp * np.sin(4.0 * math.pi * (x + phi))
-    P = 2.5
+    vz = np.zeros(N)
+    P = np.full(N, 2.5)
+    if smooth > 0.0:
+        P = P * (1.0 + 0.01 * np.sin(2 * math.pi * (x + 2 * z)) * np.cos(2 * math.pi * y))
+        vz = 0.01 * np.sin(2 * math.pi * (y - z + phi))
     m = rho / N
     u = P / ((gamma - 1.0) * rho)
-    return _finish(x, y, z, vx, vy, np.zeros(N), m, u,
-                   meta=dict(kind="kh", n=n, seed=seed, phi=phi, gamma=gamma))
+    return _finish(x, y, z, vx, vy, vz, m, u,
+                   meta=dict(kind="kh", n=n, seed=seed, phi=phi, gamma=gamma, smooth=smooth))
+
+
+def smooth_turbulence(n: int = 16, seed: int = 1717, gamma: float = GAMMA) -> Particles:
+    """Turbulent box whose pressure carries a smooth 10 % modulation, so every
+    field varies smoothly (no limiter kink from an exactly uniform field)."""
+    p = turbulence(n, seed=seed, gamma=gamma)
+    mod = 1.0 + 0.1 * np.sin(2 * math.pi * p.x) * np.cos(2 * math.pi * p.y + 0.3) + \
+        0.05 * np.sin(2 * math.pi * (p.z + p.x))
+    p.u = p.u * mod
+    p.meta["kind"] = "smooth_turbulence"
+    return p
 
 
 def ensemble(nboxes: int = 256, seed: int = 1716, nmin: int = 8, nmax: int = 24,
@@ -245,5 +267,6 @@ WORKLOADS = {
     "sedov64": lambda: sedov(64, seed=1713),
     "turb128": lambda: turbulence(128, seed=1714),
     "kh64": lambda: kh(64, seed=1715),
+    "kh64_smooth": lambda: kh(64, seed=1715, smooth=0.05),
     "ensemble256": lambda: ensemble(256, seed=1716),
 }
