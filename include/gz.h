@@ -169,6 +169,18 @@ gz_status gz_timestep(gz_ctx* ctx, const gz_particles* p, const void* n, double*
 gz_status gz_hydro_fluxes(gz_ctx* ctx, const gz_particles* p, const void* n, const void* grad,
                           const void* B, double dt, double* dpdt, double* dEdt);
 
+/* Adjoint of gz_hydro_fluxes with the same frozen inputs (H, n, grad, B,
+ * dt; neighbour and pair sets of those H): given dpdt_bar ([3][N]) and
+ * dEdt_bar ([N]) = dL/d(rates), writes dL/d(inputs) as double arrays:
+ * x_bar [3][N] (positions), h_bar [N], n_bar [N], W_bar [5][N] (rho, vx,
+ * vy, vz, P), grad_bar [15][N], B_bar [6][N].  Any output may be NULL.
+ * min/max/clamp pass the adjoint to the branch the forward took. */
+gz_status gz_hydro_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const void* n,
+                                   const void* grad, const void* B, double dt,
+                                   const double* dpdt_bar, const double* dEdt_bar, double* x_bar,
+                                   double* h_bar, double* n_bar, double* W_bar, double* grad_bar,
+                                   double* B_bar);
+
 /* One full step O4-O14 in place on p (x, y, z, vx, vy, vz, u, h updated;
  * m and id read only).  dt_fixed > 0 uses that step for every box;
  * otherwise each box takes its CFL step.  dt_used_dev (device, nboxes

@@ -13,7 +13,9 @@ Differentiation conventions (the same for the CUDA adjoint):
   with the converged H* held constant, whose derivative is the implicit one,
   -(df/dx) / f';
 * the u floor value (a multiple of a median) is a constant;
-* min/max/clamp pass the derivative of the branch they select.
+* min/max/clamp pass the derivative of the branch they select; at an exact
+  tie (a limited face value equal to its clamp bound, which happens wherever
+  the limiter zeroes a gradient) the clamp passes it to the unclamped value.
 """
 from __future__ import annotations
 
@@ -143,7 +145,37 @@ def step(state, fr: Frozen, gamma=5.0 / 3.0, ngb=32.0, beta=1.0, hancock=True,
         alpha = torch.minimum(torch.ones_like(fld), aij.min(1).values)
         gl.append([alpha * g[q][k] for k in range(3)])
     # O10-O12 over unordered pairs in canonical order
-    L, R = fr.pL, fr.pR
+    dp, dE = flux_stage(x, y, z, prim, H, n, gl, B, fr.pL, fr.pR, fr.dt, gamma, hancock)
+    # O14
+    dt = fr.dt
+    px = m * vx + dt * dp[0]
+    py = m * vy + dt * dp[1]
+    pz = m * vz + dt * dp[2]
+    v2 = (vx * vx + vy * vy) + vz * vz
+    En = m * (u + 0.5 * v2) + dt * dE
+    nx, ny, nz = px / m, py / m, pz / m
+
+    def wrap(v):
+        v = torch.where(v < 0, v + 1.0, v)
+        return torch.where(v >= 1.0, v - 1.0, v)
+    out = {"x": wrap(x + dt * (0.5 * (vx + nx))), "y": wrap(y + dt * (0.5 * (vy + ny))),
+           "z": wrap(z + dt * (0.5 * (vz + nz))), "vx": nx, "vy": ny, "vz": nz}
+    un = En / m - 0.5 * ((nx * nx + ny * ny) + nz * nz)
+    if u_floor is not None:
+        un = torch.where(un > 0, un, torch.full_like(un, float(u_floor)))
+    out["u"] = un
+    if return_all:
+        out.update({"H": H, "n": n, "dpdt": torch.stack(dp), "dEdt": dE,
+                    "grad": torch.stack([gl[q][k] for q in range(5) for k in range(3)]),
+                    "B": torch.stack(B)})
+    return out
+
+
+def flux_stage(x, y, z, prim, H, n, gl, B, L, R, dt, gamma=5.0 / 3.0, hancock=True):
+    """O10-O12: rates dp/dt (list of 3) and dE/dt over the unordered canonical
+    pairs (L, R), given primitives prim = [rho, vx, vy, vz, P], support radii
+    H, densities n, limited gradients gl[field][axis] and B (6 components)."""
+    N = x.shape[0]
     pdx, pdy, pdz = offsets(x, y, z, L, R)
     pr2 = (pdx * pdx + pdy * pdy) + pdz * pdz
     pr = torch.sqrt(pr2)
@@ -172,7 +204,7 @@ def step(state, fr: Frozen, gamma=5.0 / 3.0, ngb=32.0, beta=1.0, hancock=True,
         FL.append(prim[q][L] + ((gl[q][0][L] * sdL[0] + gl[q][1][L] * sdL[1]) + gl[q][2][L] * sdL[2]))
         FR.append(prim[q][R] + ((gl[q][0][R] * sdR[0] + gl[q][1][R] * sdR[1]) + gl[q][2][R] * sdR[2]))
     if hancock:
-        h = 0.5 * fr.dt
+        h = 0.5 * dt
         divL = (gl[1][0][L] + gl[2][1][L]) + gl[3][2][L]
         divR = (gl[1][0][R] + gl[2][1][R]) + gl[3][2][R]
         FL[0] = FL[0] + h * (-prim[0][L] * divL)
@@ -183,10 +215,12 @@ def step(state, fr: Frozen, gamma=5.0 / 3.0, ngb=32.0, beta=1.0, hancock=True,
         FL[4] = FL[4] + h * (-gamma * prim[4][L] * divL)
         FR[4] = FR[4] + h * (-gamma * prim[4][R] * divR)
     for q in range(5):
-        lo = torch.minimum(prim[q][L], prim[q][R])
-        hi = torch.maximum(prim[q][L], prim[q][R])
-        FL[q] = torch.minimum(torch.maximum(FL[q], lo), hi)
-        FR[q] = torch.minimum(torch.maximum(FR[q], lo), hi)
+        # clamp as v < lo ? lo : (v > hi ? hi : v): at a tie the derivative
+        # follows v (min/max of torch would split it between the branches)
+        lo = torch.where(prim[q][L] <= prim[q][R], prim[q][L], prim[q][R])
+        hi = torch.where(prim[q][L] >= prim[q][R], prim[q][L], prim[q][R])
+        FL[q] = torch.where(FL[q] < lo, lo, torch.where(FL[q] > hi, hi, FL[q]))
+        FR[q] = torch.where(FR[q] < lo, lo, torch.where(FR[q] > hi, hi, FR[q]))
     bad = (FL[0] <= 0) | (FL[4] <= 0) | (FR[0] <= 0) | (FR[4] <= 0)
     for q in range(5):
         FL[q] = torch.where(bad, prim[q][L], FL[q])
@@ -197,8 +231,8 @@ def step(state, fr: Frozen, gamma=5.0 / 3.0, ngb=32.0, beta=1.0, hancock=True,
     rL, PL, rR, PR = FL[0], FL[4], FR[0], FR[4]
     cL = torch.sqrt(gamma * PL / rL)
     cR = torch.sqrt(gamma * PR / rR)
-    SL = torch.minimum(uL - cL, uR - cR)
-    SR = torch.maximum(uL + cL, uR + cR)
+    SL = torch.where(uL - cL <= uR - cR, uL - cL, uR - cR)
+    SR = torch.where(uL + cL >= uR + cR, uL + cL, uR + cR)
     num = PR - PL + rL * uL * (SL - uL) - rR * uR * (SR - uR)
     den = rL * (SL - uL) - rR * (SR - uR)
     ss = num / den
@@ -209,29 +243,7 @@ def step(state, fr: Frozen, gamma=5.0 / 3.0, ngb=32.0, beta=1.0, hancock=True,
     dp = [torch.zeros(N, dtype=torch.float64).index_add(0, L, Fp[k]).index_add(0, R, -Fp[k])
           for k in range(3)]
     dE = torch.zeros(N, dtype=torch.float64).index_add(0, L, FE).index_add(0, R, -FE)
-    # O14
-    dt = fr.dt
-    px = m * vx + dt * dp[0]
-    py = m * vy + dt * dp[1]
-    pz = m * vz + dt * dp[2]
-    v2 = (vx * vx + vy * vy) + vz * vz
-    En = m * (u + 0.5 * v2) + dt * dE
-    nx, ny, nz = px / m, py / m, pz / m
-
-    def wrap(v):
-        v = torch.where(v < 0, v + 1.0, v)
-        return torch.where(v >= 1.0, v - 1.0, v)
-    out = {"x": wrap(x + dt * (0.5 * (vx + nx))), "y": wrap(y + dt * (0.5 * (vy + ny))),
-           "z": wrap(z + dt * (0.5 * (vz + nz))), "vx": nx, "vy": ny, "vz": nz}
-    un = En / m - 0.5 * ((nx * nx + ny * ny) + nz * nz)
-    if u_floor is not None:
-        un = torch.where(un > 0, un, torch.full_like(un, float(u_floor)))
-    out["u"] = un
-    if return_all:
-        out.update({"H": H, "n": n, "dpdt": torch.stack(dp), "dEdt": dE,
-                    "grad": torch.stack([gl[q][k] for q in range(5) for k in range(3)]),
-                    "B": torch.stack(B)})
-    return out
+    return dp, dE
 
 
 def freeze(state_np, params, use_cells=1):

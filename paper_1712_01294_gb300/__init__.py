@@ -81,6 +81,7 @@ def load_library(build_if_missing: bool = True):
             "gz_timestep": (st, [vp, P, vp, vp, vp]),
             "gz_hydro_fluxes": (st, [vp, P, vp, vp, vp, d, vp, vp]),
             "gz_step": (st, [vp, P, d, vp]),
+            "gz_hydro_fluxes_backward": (st, [vp, P, vp, vp, vp, d, vp, vp, vp, vp, vp, vp, vp, vp]),
             "gz_step_backward": (st, [vp, P, d, P, P]),
             "gz_get_neighbours": (st, [vp, vp, vp, i32]),
             "gz_get_status": (st, [vp, vp, vp, vp, i32]),
@@ -214,6 +215,20 @@ class Context:
         self._check(self.lib.gz_hydro_fluxes(self.h, C.byref(s), _ptr(n), _ptr(grad), _ptr(B),
                                              float(dt), _ptr(dpdt), _ptr(dEdt)), "gz_hydro_fluxes")
         return dpdt, dEdt
+
+    def hydro_fluxes_backward(self, p, n, grad, B, dt, dpdt_bar, dEdt_bar):
+        """gz_hydro_fluxes_backward: dict of float64 adjoints x [3,N], h, n, W [5,N],
+        grad [15,N], B [6,N]."""
+        f64 = self.torch.float64
+        out = {"x": self.empty(3, self.N, dtype=f64), "h": self.empty(self.N, dtype=f64),
+               "n": self.empty(self.N, dtype=f64), "W": self.empty(5, self.N, dtype=f64),
+               "grad": self.empty(15, self.N, dtype=f64), "B": self.empty(6, self.N, dtype=f64)}
+        s = self._parts(p)
+        self._check(self.lib.gz_hydro_fluxes_backward(
+            self.h, C.byref(s), _ptr(n), _ptr(grad), _ptr(B), float(dt), _ptr(dpdt_bar),
+            _ptr(dEdt_bar), _ptr(out["x"]), _ptr(out["h"]), _ptr(out["n"]), _ptr(out["W"]),
+            _ptr(out["grad"]), _ptr(out["B"])), "gz_hydro_fluxes_backward")
+        return out
 
     def step(self, p, dt_fixed: float = 0.0, dt_used=None):
         """gz_step in place on p; dt_used (device float64 [nboxes]) receives the steps."""

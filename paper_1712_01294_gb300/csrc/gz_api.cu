@@ -179,6 +179,22 @@ gz_status do_fluxes(gz_ctx* ctx, const gz_particles* p, const void* n, const voi
 }
 
 template <typename T>
+gz_status do_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const void* n, const void* grad,
+                             const void* B, double dt, const double* dpbar, const double* dEbar,
+                             double* xbar, double* hbar, double* nbar, double* Wbar, double* gbar,
+                             double* Bbar) {
+    gz_status s = prepare_given<T>(ctx, p, n, true);
+    if (s) return s;
+    Ctx& c = ctx->c;
+    cudaError_t e = ensure_adjoint_scratch(c);
+    if (e == cudaSuccess) e = run_pack_given<T>(c, (const T*)grad, (const T*)B);
+    if (e == cudaSuccess) e = run_dt_set(c, dt);
+    if (e == cudaSuccess) e = run_flux_adjoint<T>(c, dpbar, dEbar);
+    if (e == cudaSuccess) e = run_adj_out_flux(c, xbar, hbar, nbar, Wbar, gbar, Bbar);
+    return cuda_check(ctx, e, "gz_hydro_fluxes_backward");
+}
+
+template <typename T>
 gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev) {
     Ctx& c = ctx->c;
     cudaError_t e;
@@ -378,6 +394,7 @@ gz_status gz_destroy(gz_ctx* ctx) {
     }
     for (auto ev : ctx->c.ev_pool) cudaEventDestroy(ev);
     cudaFree(ctx->c.arena);
+    if (ctx->c.adj_arena) cudaFree(ctx->c.adj_arena);
     delete ctx;
     return GZ_OK;
 }
@@ -417,6 +434,21 @@ gz_status gz_hydro_fluxes(gz_ctx* ctx, const gz_particles* p, const void* n, con
     if (!(dt >= 0.0) || !isfinite(dt)) return fail(ctx, GZ_E_INVAL, "dt must be finite and >= 0");
     return GZ_DISPATCH(do_fluxes<float>(ctx, p, n, grad, B, dt, dpdt, dEdt),
                        do_fluxes<double>(ctx, p, n, grad, B, dt, dpdt, dEdt));
+}
+
+gz_status gz_hydro_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const void* n,
+                                   const void* grad, const void* B, double dt,
+                                   const double* dpdt_bar, const double* dEdt_bar, double* x_bar,
+                                   double* h_bar, double* n_bar, double* W_bar, double* grad_bar,
+                                   double* B_bar) {
+    if (!ctx) return GZ_E_INVAL;
+    if (gz_status s = check_particles(ctx, p, true)) return s;
+    if (!n || !grad || !B || !dpdt_bar || !dEdt_bar) return fail(ctx, GZ_E_INVAL, "null input");
+    if (!(dt >= 0.0) || !isfinite(dt)) return fail(ctx, GZ_E_INVAL, "dt must be finite and >= 0");
+    return GZ_DISPATCH(do_fluxes_backward<float>(ctx, p, n, grad, B, dt, dpdt_bar, dEdt_bar, x_bar, h_bar,
+                                                 n_bar, W_bar, grad_bar, B_bar),
+                       do_fluxes_backward<double>(ctx, p, n, grad, B, dt, dpdt_bar, dEdt_bar, x_bar,
+                                                  h_bar, n_bar, W_bar, grad_bar, B_bar));
 }
 
 gz_status gz_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev) {

@@ -1,0 +1,232 @@
+// Device functions shared by the forward passes and their adjoints.
+#pragma once
+
+#include "gz_internal.cuh"
+
+namespace gz {
+
+// Kahan-compensated sum for FP32 neighbour sums; plain sum in FP64.
+template <typename T>
+struct Acc {
+    T s = T(0);
+    __device__ __forceinline__ void add(T v) { s += v; }
+    __device__ __forceinline__ double value() const { return (double)s; }
+};
+template <>
+struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        float y = __fsub_rn(v, c);
+        float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
+// Pair-pass division and square roots: the FP32 path uses the hardware
+// reciprocal / reciprocal square root (about 2 ulp; deterministic, so both
+// particles of a pair still compute identical values); FP64 stays IEEE.
+__device__ __forceinline__ float pdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double pdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float psqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ double psqrt(double x) { return sqrt(x); }
+
+// Symmetric 3x3 inverse by adjugate; kappa = |E|_F |B|_F / 3.
+template <typename A>
+__device__ __forceinline__ void invert_sym(const A E[6], A B[6], A& det, A& kap) {
+    const A a = E[0], b = E[1], c = E[2], d = E[3], e = E[4], f = E[5];
+    const A Cxx = d * f - e * e, Cxy = c * e - b * f, Cxz = b * e - c * d;
+    const A Cyy = a * f - c * c, Cyz = b * c - a * e, Czz = a * d - b * b;
+    det = a * Cxx + b * Cxy + c * Cxz;
+    const A id = A(1) / det;
+    B[0] = Cxx * id;
+    B[1] = Cxy * id;
+    B[2] = Cxz * id;
+    B[3] = Cyy * id;
+    B[4] = Cyz * id;
+    B[5] = Czz * id;
+    const A nE = sqrt(a * a + d * d + f * f + A(2) * (b * b + c * c + e * e));
+    const A nB = sqrt(B[0] * B[0] + B[3] * B[3] + B[5] * B[5] +
+                      A(2) * (B[1] * B[1] + B[2] * B[2] + B[4] * B[4]));
+    kap = nE * nB / A(3);
+}
+
+// ---------------------------------------------------------- O10-O12
+__device__ __forceinline__ void load_rec(const float* __restrict__ p, float (&v)[kRecord]) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int k = 0; k < kRecord / 4; ++k) {
+        const float4 t = __ldg(q + k);
+        v[4 * k] = t.x;
+        v[4 * k + 1] = t.y;
+        v[4 * k + 2] = t.z;
+        v[4 * k + 3] = t.w;
+    }
+}
+__device__ __forceinline__ void load_rec(const double* __restrict__ p, double (&v)[kRecord]) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int k = 0; k < kRecord / 2; ++k) {
+        const double2 t = __ldg(q + k);
+        v[2 * k] = t.x;
+        v[2 * k + 1] = t.y;
+    }
+}
+
+// Face state of particle a toward the face at a + s o (o = offset to the
+// partner): linear reconstruction with a's limited gradients plus the Hancock
+// half step (dt/2) (-rho div v, -grad P / rho, -gamma P div v).
+template <typename T>
+__device__ __forceinline__ void face_state(const T (&a)[kRecord], T s, T dx, T dy, T dz, T hdt,
+                                           T gam, bool hancock, T (&F)[5]) {
+    const T ox = s * dx, oy = s * dy, oz = s * dz;
+    const T W[5] = {a[6], a[8], a[9], a[10], a[7]};
+#pragma unroll
+    for (int f = 0; f < 5; ++f)
+        F[f] = W[f] + ((a[11 + 3 * f] * ox + a[12 + 3 * f] * oy) + a[13 + 3 * f] * oz);
+    if (hancock) {
+        const T div = (a[11 + 3] + a[11 + 7]) + a[11 + 11];
+        const T ir = pdiv(T(1), a[6]);
+        F[0] += hdt * (-a[6] * div);
+        F[1] += hdt * (-a[11 + 12] * ir);
+        F[2] += hdt * (-a[11 + 13] * ir);
+        F[3] += hdt * (-a[11 + 14] * ir);
+        F[4] += hdt * (-gam * a[7] * div);
+    }
+}
+
+// Contribution of the pair (a, b) to particle a's rates: dp (3) and dE.
+// Returns false when the face area vanishes.  flags: 1 fallback, 2 P* < 0.
+template <typename T>
+__device__ __forceinline__ bool pair_rates(const T (&a)[kRecord], const T (&b)[kRecord], bool aL,
+                                           T hdt, T gam, bool hancock, T (&dp)[3], T& dE, int& fl) {
+    const T dx = mi_diff(b[0], a[0], a[0] - T(1));
+    const T dy = mi_diff(b[1], a[1], a[1] - T(1));
+    const T dz = mi_diff(b[2], a[2], a[2] - T(1));
+    const T r2 = sep2(dx, dy, dz);
+    const T r = psqrt(r2);
+    const T ca = r2 < a[3] * a[3] ? a[5] * kern_w(r * a[4]) : T(0);
+    const T cb = r2 < b[3] * b[3] ? b[5] * kern_w(r * b[4]) : T(0);
+    const T Bax = (a[26] * dx + a[27] * dy) + a[28] * dz;
+    const T Bay = (a[27] * dx + a[29] * dy) + a[30] * dz;
+    const T Baz = (a[28] * dx + a[30] * dy) + a[31] * dz;
+    const T Bbx = (b[26] * dx + b[27] * dy) + b[28] * dz;
+    const T Bby = (b[27] * dx + b[29] * dy) + b[30] * dz;
+    const T Bbz = (b[28] * dx + b[30] * dy) + b[31] * dz;
+    const T A0 = add_rn(mul_rn(ca, Bax), mul_rn(cb, Bbx));
+    const T A1 = add_rn(mul_rn(ca, Bay), mul_rn(cb, Bby));
+    const T A2 = add_rn(mul_rn(ca, Baz), mul_rn(cb, Bbz));
+    const T Aq = sep2(A0, A1, A2);
+    if (!(Aq > T(0))) return false;
+    const T Am = psqrt(Aq);
+    const T iA = pdiv(T(1), Am);
+    const T n0 = A0 * iA, n1 = A1 * iA, n2 = A2 * iA;
+    const T Hs = a[3] + b[3];
+    const T sa = pdiv(a[3], Hs), sb = pdiv(b[3], Hs);
+    T Fa[5], Fb[5];
+    face_state(a, sa, dx, dy, dz, hdt, gam, hancock, Fa);
+    face_state(b, sb, -dx, -dy, -dz, hdt, gam, hancock, Fb);
+    const T Wa[5] = {a[6], a[8], a[9], a[10], a[7]};
+    const T Wb[5] = {b[6], b[8], b[9], b[10], b[7]};
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+        const T lo = min(Wa[f], Wb[f]), hi = max(Wa[f], Wb[f]);
+        Fa[f] = min(max(Fa[f], lo), hi);
+        Fb[f] = min(max(Fb[f], lo), hi);
+    }
+    if (!(Fa[0] > T(0) && Fa[4] > T(0) && Fb[0] > T(0) && Fb[4] > T(0))) {
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+            Fa[f] = Wa[f];
+            Fb[f] = Wb[f];
+        }
+        fl |= 1;
+    }
+    // canonical order: L = lower id
+    T FL[5], FR[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+        FL[f] = aL ? Fa[f] : Fb[f];
+        FR[f] = aL ? Fb[f] : Fa[f];
+    }
+    const T vLx = aL ? Wa[1] : Wb[1], vLy = aL ? Wa[2] : Wb[2], vLz = aL ? Wa[3] : Wb[3];
+    const T vRx = aL ? Wb[1] : Wa[1], vRy = aL ? Wb[2] : Wa[2], vRz = aL ? Wb[3] : Wa[3];
+    const T sL = aL ? sa : sb;
+    const T nx = aL ? n0 : -n0, ny = aL ? n1 : -n1, nz = aL ? n2 : -n2;
+    const T vfx = vLx + sL * (vRx - vLx), vfy = vLy + sL * (vRy - vLy), vfz = vLz + sL * (vRz - vLz);
+    const T vfn = (vfx * nx + vfy * ny) + vfz * nz;
+    const T uL = ((FL[1] - vfx) * nx + (FL[2] - vfy) * ny) + (FL[3] - vfz) * nz;
+    const T uR = ((FR[1] - vfx) * nx + (FR[2] - vfy) * ny) + (FR[3] - vfz) * nz;
+    // O12 HLLC with Davis wave speeds
+    const T rL = FL[0], PL = FL[4], rR = FR[0], PR = FR[4];
+    const T cL = psqrt(pdiv(gam * PL, rL)), cR = psqrt(pdiv(gam * PR, rR));
+    const T SL = min(uL - cL, uR - cR), SR = max(uL + cL, uR + cR);
+    const T num = ((PR - PL) + rL * uL * (SL - uL)) - rR * uR * (SR - uR);
+    const T den = rL * (SL - uL) - rR * (SR - uR);
+    const T ss = pdiv(num, den);
+    T ps = PL + rL * (SL - uL) * (ss - uL);
+    if (ps < T(0)) {
+        ps = T(0);
+        fl |= 2;
+    }
+    dp[0] = -mul_rn(ps, A0);
+    dp[1] = -mul_rn(ps, A1);
+    dp[2] = -mul_rn(ps, A2);
+    const T ef = ps * (ss + vfn) * Am;
+    dE = aL ? -ef : ef;
+    return true;
+}
+
+// ----------------------------------------------------------------- O14
+__device__ __forceinline__ double wrap1(double v) {
+    if (v < 0.0) v += 1.0;
+    if (v >= 1.0) v -= 1.0;
+    return v;
+}
+
+// FP64 state: the literal conserved update, like the oracle.
+__device__ __forceinline__ void update_one(double m, double& x, double& y, double& z, double& vx,
+                                           double& vy, double& vz, double& u, double dpx, double dpy,
+                                           double dpz, double dE, double dt) {
+    const double v2 = (vx * vx + vy * vy) + vz * vz;
+    const double E = m * (u + 0.5 * v2) + dt * dE;
+    const double nx = (m * vx + dt * dpx) / m, ny = (m * vy + dt * dpy) / m, nz = (m * vz + dt * dpz) / m;
+    x = wrap1(x + dt * (0.5 * (vx + nx)));
+    y = wrap1(y + dt * (0.5 * (vy + ny)));
+    z = wrap1(z + dt * (0.5 * (vz + nz)));
+    u = E / m - 0.5 * ((nx * nx + ny * ny) + nz * nz);
+    vx = nx;
+    vy = ny;
+    vz = nz;
+}
+// FP32 state: the same update written with the increments dv = dt (dp/dt)/m
+// and du = dt (dE/dt)/m - dv . (v + dv/2), which is E/m - v_new^2/2 - u
+// without the cancellation of the literal form.
+__device__ __forceinline__ float wrapf(float v) {
+    if (v < 0.f) v += 1.f;
+    if (v >= 1.f) v -= 1.f;
+    return v;
+}
+__device__ __forceinline__ void update_one(float m, float& x, float& y, float& z, float& vx,
+                                           float& vy, float& vz, float& u, double dpx, double dpy,
+                                           double dpz, double dE, double dt) {
+    const float dtf = (float)dt, im = 1.f / m;
+    const float dvx = dtf * (float)dpx * im, dvy = dtf * (float)dpy * im, dvz = dtf * (float)dpz * im;
+    const float hx = vx + 0.5f * dvx, hy = vy + 0.5f * dvy, hz = vz + 0.5f * dvz;
+    const float du = dtf * (float)dE * im - ((dvx * hx + dvy * hy) + dvz * hz);
+    x = wrapf(x + dtf * hx);
+    y = wrapf(y + dtf * hy);
+    z = wrapf(z + dtf * hz);
+    u = u + du;
+    vx += dvx;
+    vy += dvy;
+    vz += dvz;
+}
+
+}  // namespace gz

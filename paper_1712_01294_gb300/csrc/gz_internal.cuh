@@ -14,6 +14,9 @@ namespace gz {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kRecord = 32;  // values per packed particle record (flux pass)
+constexpr int kAdj = 33;     // adjoint values per particle (see gz_adjoint.cu)
+constexpr int kSeed = 44;    // gradient-pass adjoint seeds per particle
+constexpr int kGInfo = 25;   // raw gradients, limiter factors, active limiter offsets
 
 // Device status word (one per context).
 struct DevStatus {
@@ -119,6 +122,13 @@ struct Ctx {
     double prof_ms[GZ_NPASSES];
     long long prof_calls[GZ_NPASSES];
     long long* pairs_dev;  // scratch for gz_pair_count
+    // adjoint scratch, allocated on the first backward call
+    void* adj_arena = nullptr;
+    double* adj = nullptr;    // [N][kAdj]
+    double* wgt = nullptr;    // [N][4] rate adjoints
+    double* seeds = nullptr;  // [N][kSeed]
+    int* lim = nullptr;       // [N][10] limiter: active neighbour, extreme particle per field
+    void* ginfo = nullptr;    // [N][kGInfo] working precision
 };
 
 // ------------------------------------------------------------------ status

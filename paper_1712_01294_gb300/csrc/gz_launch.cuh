@@ -50,6 +50,13 @@ cudaError_t run_get_neighbours(Ctx& c, int32_t* count_out, int64_t* ids_out, int
 
 cudaError_t run_pair_count(Ctx& c, long long* out_dev);
 
+// Adjoint passes.
+cudaError_t ensure_adjoint_scratch(Ctx& c);
+template <typename T>
+cudaError_t run_flux_adjoint(Ctx& c, const double* dpbar, const double* dEbar);
+cudaError_t run_adj_out_flux(Ctx& c, double* xbar, double* hbar, double* nbar, double* Wbar, double* gbar,
+                             double* Bbar);
+
 KParams kparams(const Ctx& c);
 
 }  // namespace gz
