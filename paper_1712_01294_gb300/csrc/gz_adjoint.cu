@@ -404,7 +404,423 @@ __global__ void k_adj_out_flux(int N, const unsigned* __restrict__ orig, const d
         for (int q = 0; q < 6; ++q) Bbar[(size_t)q * N + o] = a[AB + q];
 }
 
+// ------------------------------------------------------------- update
+// O14 reversed.  v' = v + dt dp/m, x' = x + dt (v + v')/2,
+// u' = u + |v|^2/2 + dt dE/m - |v'|^2/2 (a floored u' is a constant).
+template <typename T>
+__global__ void k_update_adj(int N, Sorted<T> s, const double* __restrict__ dpdt,
+                             const double* __restrict__ dEdt, const double* __restrict__ dt_use,
+                             gz_particles gend, double* __restrict__ adj, double* __restrict__ wgt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const unsigned o = s.orig[i];
+    const double dt = dt_use[s.box[i]];
+    const double m = s.m[i], u = s.u[i];
+    const double v[3] = {s.vx[i], s.vy[i], s.vz[i]};
+    const double dp[3] = {dpdt[i], dpdt[(size_t)N + i], dpdt[2 * (size_t)N + i]};
+    const double dE = dEdt[i];
+    // forward update in the working precision, for the floor decision
+    T X = s.x[i], Y = s.y[i], Z = s.z[i], VX = s.vx[i], VY = s.vy[i], VZ = s.vz[i], U = s.u[i];
+    update_one(s.m[i], X, Y, Z, VX, VY, VZ, U, dp[0], dp[1], dp[2], dE, dt);
+    const bool floored = !(U > T(0));
+    double vn[3];
+    for (int k = 0; k < 3; ++k) vn[k] = v[k] + dt * dp[k] / m;
+    const double xb[3] = {gend.x ? (double)((const T*)gend.x)[o] : 0.0,
+                          gend.y ? (double)((const T*)gend.y)[o] : 0.0,
+                          gend.z ? (double)((const T*)gend.z)[o] : 0.0};
+    const double vb[3] = {gend.vx ? (double)((const T*)gend.vx)[o] : 0.0,
+                          gend.vy ? (double)((const T*)gend.vy)[o] : 0.0,
+                          gend.vz ? (double)((const T*)gend.vz)[o] : 0.0};
+    const double ub = (gend.u && !floored) ? (double)((const T*)gend.u)[o] : 0.0;
+    double* a = adj + (size_t)i * kAdj;
+    double mb = -ub * dt * dE / (m * m);
+    for (int k = 0; k < 3; ++k) {
+        a[AX + k] += xb[k];
+        a[AV + k] += vb[k] + dt * xb[k] + ub * (v[k] - vn[k]);
+        const double w = vb[k] + 0.5 * dt * xb[k];
+        wgt[4 * (size_t)i + k] = dt / m * (w - ub * vn[k]);
+        mb += -(vn[k] - v[k]) / m * w + ub * vn[k] * (vn[k] - v[k]) / m;
+    }
+    wgt[4 * (size_t)i + 3] = ub * dt / m;
+    a[AU] += ub;
+    a[AM] += mb;
+    (void)u;
+}
+
+// ---------------------------------------------------------- gradients
+// Seeds of particle i's gradient pass: from the adjoints of its limited
+// gradients and of B, through the limiter (active constraint only), g = B S
+// and B = E^-1.  Adds i's own terms; stores what i's neighbours gather.
+// seeds: [0,15) Sbar, [15,21) Ebar (xx xy xz yy yz zz), then per field f
+// at 21 + 5 f: xbar (3) and Hbar of the active neighbour, fbar of the
+// extreme particle.
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_grad_seeds(int N, Sorted<T> s, const T* __restrict__ rec, const T* __restrict__ ginfo,
+                 const int* __restrict__ lim, const unsigned* __restrict__ nbr,
+                 const int* __restrict__ ncount, KParams p, double* __restrict__ adj,
+                 double* __restrict__ seeds) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double* a = adj + (size_t)i * kAdj;
+    double* sd = seeds + (size_t)i * kSeed;
+    const T* G = ginfo + (size_t)i * kGInfo;
+    const T* R = rec + (size_t)i * kRecord;
+    const P4<T> me = s.pos[i];
+    const T xi = me.x, yi = me.y, zi = me.z, Hi = me.w;
+    const T xim1 = xi - T(1), yim1 = yi - T(1), zim1 = zi - T(1);
+    const P4<T> pm = s.prim[i];
+    const T Wi[5] = {pm.x, pm.y, pm.z, pm.w, s.prim2[i].x};
+    const double Bs[6] = {R[26], R[27], R[28], R[29], R[30], R[31]};
+    double fbi[5] = {0, 0, 0, 0, 0};
+    double xbi[3] = {0, 0, 0};
+    double Hbi = 0.0, nbi = 0.0;
+    double gb[15];
+    double Bb[6];
+    for (int q = 0; q < 6; ++q) Bb[q] = a[AB + q];
+    for (int q = 0; q < kSeed; ++q) sd[q] = 0.0;
+    const double beta = p.beta;
+    for (int f = 0; f < 5; ++f) {
+        const double al = G[30 + f];
+        const double g[3] = {G[3 * f], G[3 * f + 1], G[3 * f + 2]};
+        const double ghb[3] = {a[AG + 3 * f], a[AG + 3 * f + 1], a[AG + 3 * f + 2]};
+        for (int k = 0; k < 3; ++k) gb[3 * f + k] = al * ghb[k];
+        const double alb = (ghb[0] * g[0] + ghb[1] * g[1]) + ghb[2] * g[2];
+        const int j = lim[(size_t)i * 10 + f];
+        if (j >= 0 && alb != 0.0) {
+            const int k = lim[(size_t)i * 10 + 5 + f];
+            const double D = G[35 + f];
+            const double c1 = alb * beta / D;
+            if (k == i)
+                fbi[f] += c1;
+            else
+                sd[21 + 5 * f + 4] = c1;
+            fbi[f] -= c1;
+            const double Db = -alb * al / D;
+            const P4<T> qj = s.pos[j];
+            const double dx = mi_diff(qj.x, xi, xim1), dy = mi_diff(qj.y, yi, yim1),
+                         dz = mi_diff(qj.z, zi, zim1);
+            const double Hj = qj.w, Hs = (double)Hi + Hj;
+            const double sij = (double)Hi / Hs;
+            const double o[3] = {sij * dx, sij * dy, sij * dz};
+            for (int kk = 0; kk < 3; ++kk) gb[3 * f + kk] += Db * o[kk];
+            const double ob[3] = {Db * g[0], Db * g[1], Db * g[2]};
+            const double sb = (ob[0] * dx + ob[1] * dy) + ob[2] * dz;
+            Hbi += sb * Hj / (Hs * Hs);
+            sd[21 + 5 * f + 3] = -sb * (double)Hi / (Hs * Hs);
+            for (int kk = 0; kk < 3; ++kk) {
+                sd[21 + 5 * f + kk] = ob[kk] * sij;
+                xbi[kk] -= ob[kk] * sij;
+            }
+        }
+    }
+    // g = B S
+    const bool singular = Bs[0] == 0.0 && Bs[1] == 0.0 && Bs[2] == 0.0 && Bs[3] == 0.0 &&
+                          Bs[4] == 0.0 && Bs[5] == 0.0;
+    double Sb[15];
+    for (int f = 0; f < 5; ++f) {
+        const double S0 = G[15 + 3 * f], S1 = G[16 + 3 * f], S2 = G[17 + 3 * f];
+        const double g0 = gb[3 * f], g1 = gb[3 * f + 1], g2 = gb[3 * f + 2];
+        Bb[0] += g0 * S0;
+        Bb[1] += g0 * S1 + g1 * S0;
+        Bb[2] += g0 * S2 + g2 * S0;
+        Bb[3] += g1 * S1;
+        Bb[4] += g1 * S2 + g2 * S1;
+        Bb[5] += g2 * S2;
+        Sb[3 * f] = Bs[0] * g0 + Bs[1] * g1 + Bs[2] * g2;
+        Sb[3 * f + 1] = Bs[1] * g0 + Bs[3] * g1 + Bs[4] * g2;
+        Sb[3 * f + 2] = Bs[2] * g0 + Bs[4] * g1 + Bs[5] * g2;
+    }
+    // B = E^-1: Ebar = -B Bbar B (full symmetric matrices)
+    const double Bm[3][3] = {{Bs[0], Bs[1], Bs[2]}, {Bs[1], Bs[3], Bs[4]}, {Bs[2], Bs[4], Bs[5]}};
+    const double Pm[3][3] = {{Bb[0], 0.5 * Bb[1], 0.5 * Bb[2]},
+                             {0.5 * Bb[1], Bb[3], 0.5 * Bb[4]},
+                             {0.5 * Bb[2], 0.5 * Bb[4], Bb[5]}};
+    double T1[3][3], Em[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) T1[r][c] = (Pm[r][0] * Bm[0][c] + Pm[r][1] * Bm[1][c]) + Pm[r][2] * Bm[2][c];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) Em[r][c] = -((Bm[r][0] * T1[0][c] + Bm[r][1] * T1[1][c]) + Bm[r][2] * T1[2][c]);
+    double Eb[6] = {Em[0][0], Em[0][1] + Em[1][0], Em[0][2] + Em[2][0], Em[1][1], Em[1][2] + Em[2][1], Em[2][2]};
+    if (singular) {
+        for (int q = 0; q < 6; ++q) Eb[q] = 0.0;
+        for (int q = 0; q < 15; ++q) Sb[q] = 0.0;
+    }
+    for (int q = 0; q < 15; ++q) sd[q] = Sb[q];
+    for (int q = 0; q < 6; ++q) sd[15 + q] = Eb[q];
+    // own terms of E = sum psi d d^T and S_f = sum (f_j - f_i) psi d
+    const T ni = s.n[i];
+    const T iH = T(1) / Hi;
+    const T norm = T(8.0 / kPi) * iH * iH * iH / ni;
+    double normb = 0.0;
+    const int cnt = min(ncount[i], p.cap);
+    const unsigned* L = nbr + (size_t)i * p.cap;
+    for (int kk = 0; kk < cnt; ++kk) {
+        const int j = (int)L[kk];
+        const P4<T> qj = s.pos[j];
+        const T dxT = mi_diff(qj.x, xi, xim1), dyT = mi_diff(qj.y, yi, yim1), dzT = mi_diff(qj.z, zi, zim1);
+        const T r2 = sep2(dxT, dyT, dzT);
+        const T r = sqrt(r2);
+        const T q = r * iH;
+        const double w = kern_w(q), dw = kern_dw(q);
+        const double psi = (double)(norm * kern_w(q));
+        const double dx = dxT, dy = dyT, dz = dzT;
+        const P4<T> pj = s.prim[j];
+        const double Wj[5] = {pj.x, pj.y, pj.z, pj.w, s.prim2[j].x};
+        double psib = ((Eb[0] * dx * dx + Eb[1] * dx * dy) + (Eb[2] * dx * dz + Eb[3] * dy * dy)) +
+                      (Eb[4] * dy * dz + Eb[5] * dz * dz);
+        double db[3] = {psi * (2.0 * Eb[0] * dx + Eb[1] * dy + Eb[2] * dz),
+                        psi * (Eb[1] * dx + 2.0 * Eb[3] * dy + Eb[4] * dz),
+                        psi * (Eb[2] * dx + Eb[4] * dy + 2.0 * Eb[5] * dz)};
+        for (int f = 0; f < 5; ++f) {
+            const double df = Wj[f] - (double)Wi[f];
+            const double t = (Sb[3 * f] * dx + Sb[3 * f + 1] * dy) + Sb[3 * f + 2] * dz;
+            fbi[f] -= psi * t;
+            psib += df * t;
+            db[0] += df * psi * Sb[3 * f];
+            db[1] += df * psi * Sb[3 * f + 1];
+            db[2] += df * psi * Sb[3 * f + 2];
+        }
+        normb += psib * w;
+        const double qb = psib * (double)norm * dw;
+        Hbi -= qb * (double)q / (double)Hi;
+        if (r > T(0)) {
+            const double rb = qb / (double)Hi;
+            db[0] += rb * dx / (double)r;
+            db[1] += rb * dy / (double)r;
+            db[2] += rb * dz / (double)r;
+        }
+        xbi[0] -= db[0];
+        xbi[1] -= db[1];
+        xbi[2] -= db[2];
+    }
+    Hbi += normb * (-3.0 * (double)norm / (double)Hi);
+    nbi += normb * (-(double)norm / (double)ni);
+    a[AX] += xbi[0];
+    a[AX + 1] += xbi[1];
+    a[AX + 2] += xbi[2];
+    a[AH] += Hbi;
+    a[AN] += nbi;
+    a[ARHO] += fbi[0];
+    a[AV] += fbi[1];
+    a[AV + 1] += fbi[2];
+    a[AV + 2] += fbi[3];
+    a[AP] += fbi[4];
+}
+
+// Gradient-pass terms of particle j in the sums of every i with j in N_i
+// (all such i are in j's pair lists).
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_grad_gather(int N, Sorted<T> s, const int* __restrict__ lim, const unsigned* __restrict__ nbr,
+                  const int* __restrict__ ncount, const unsigned* __restrict__ rnbr,
+                  const int* __restrict__ rcount, KParams p, const double* __restrict__ seeds,
+                  double* __restrict__ adj) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const P4<T> mj = s.pos[j];
+    const P4<T> pj = s.prim[j];
+    const double Wj[5] = {pj.x, pj.y, pj.z, pj.w, s.prim2[j].x};
+    double fb[5] = {0, 0, 0, 0, 0}, xb[3] = {0, 0, 0}, Hb = 0.0;
+    for (int list = 0; list < 2; ++list) {
+        const unsigned* Lj = list == 0 ? nbr + (size_t)j * p.cap : rnbr + (size_t)j * p.rcap;
+        const int cnt = list == 0 ? min(ncount[j], p.cap) : min(rcount[j], p.rcap);
+        for (int kk = 0; kk < cnt; ++kk) {
+            const int i = (int)Lj[kk];
+            const P4<T> mi = s.pos[i];
+            const T Hi = mi.w;
+            // offset as seen by i (x_j - x_i), exactly as i's gradient pass computed it
+            const T dxT = mi_diff(mj.x, mi.x, mi.x - T(1)), dyT = mi_diff(mj.y, mi.y, mi.y - T(1)),
+                    dzT = mi_diff(mj.z, mi.z, mi.z - T(1));
+            const T r2 = sep2(dxT, dyT, dzT);
+            if (!(r2 < Hi * Hi)) continue;  // j is not in N_i
+            const double* sd = seeds + (size_t)i * kSeed;
+            const T r = sqrt(r2);
+            const T iH = T(1) / Hi;
+            const T q = r * iH;
+            const T norm = T(8.0 / kPi) * iH * iH * iH / s.n[i];
+            const double psi = (double)(norm * kern_w(q));
+            const double dw = kern_dw(q);
+            const double dx = dxT, dy = dyT, dz = dzT;
+            const P4<T> pi_ = s.prim[i];
+            const double Wi[5] = {pi_.x, pi_.y, pi_.z, pi_.w, s.prim2[i].x};
+            const double* Eb = sd + 15;
+            double psib = ((Eb[0] * dx * dx + Eb[1] * dx * dy) + (Eb[2] * dx * dz + Eb[3] * dy * dy)) +
+                          (Eb[4] * dy * dz + Eb[5] * dz * dz);
+            double db[3] = {psi * (2.0 * Eb[0] * dx + Eb[1] * dy + Eb[2] * dz),
+                            psi * (Eb[1] * dx + 2.0 * Eb[3] * dy + Eb[4] * dz),
+                            psi * (Eb[2] * dx + Eb[4] * dy + 2.0 * Eb[5] * dz)};
+            for (int f = 0; f < 5; ++f) {
+                const double df = Wj[f] - Wi[f];
+                const double t = (sd[3 * f] * dx + sd[3 * f + 1] * dy) + sd[3 * f + 2] * dz;
+                fb[f] += psi * t;
+                psib += df * t;
+                db[0] += df * psi * sd[3 * f];
+                db[1] += df * psi * sd[3 * f + 1];
+                db[2] += df * psi * sd[3 * f + 2];
+            }
+            if (r > T(0)) {
+                const double rb = psib * (double)norm * dw / (double)Hi;
+                db[0] += rb * dx / (double)r;
+                db[1] += rb * dy / (double)r;
+                db[2] += rb * dz / (double)r;
+            }
+            xb[0] += db[0];
+            xb[1] += db[1];
+            xb[2] += db[2];
+            // limiter terms where j is i's active neighbour or extreme particle
+            for (int f = 0; f < 5; ++f) {
+                if (lim[(size_t)i * 10 + f] == j) {
+                    xb[0] += sd[21 + 5 * f];
+                    xb[1] += sd[21 + 5 * f + 1];
+                    xb[2] += sd[21 + 5 * f + 2];
+                    Hb += sd[21 + 5 * f + 3];
+                }
+                if (lim[(size_t)i * 10 + f] >= 0 && lim[(size_t)i * 10 + 5 + f] == j) fb[f] += sd[21 + 5 * f + 4];
+            }
+        }
+    }
+    double* a = adj + (size_t)j * kAdj;
+    a[AX] += xb[0];
+    a[AX + 1] += xb[1];
+    a[AX + 2] += xb[2];
+    a[AH] += Hb;
+    a[ARHO] += fb[0];
+    a[AV] += fb[1];
+    a[AV + 1] += fb[2];
+    a[AV + 2] += fb[3];
+    a[AP] += fb[4];
+}
+
+// ------------------------------------------------------------ density
+// rho = m n, P = (gamma - 1) m n u; n = 8 (1 + sum w) / (pi H^3) with H the
+// root of f = (32/3)(1 + sum w) - N_ngb: Hbar_tot = Hbar + nbar dn/dH,
+// lambda = -Hbar_tot / f_H, and every r_ij in N_i receives
+// (w'(q)/H)(nbar 8/(pi H^3) + lambda 32/3) = kappa_i w'(q_ij).
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_dens_seeds(int N, Sorted<T> s, const unsigned* __restrict__ nbr, const int* __restrict__ ncount,
+                 KParams p, double* __restrict__ adj, double* __restrict__ kap) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double* a = adj + (size_t)i * kAdj;
+    const double m = s.m[i], n = s.n[i], u = s.u[i], g1 = p.gamma - 1.0;
+    const double rhob = a[ARHO], Pb = a[AP];
+    const double nb = a[AN] + rhob * m + Pb * g1 * m * u;
+    a[AM] += rhob * n + Pb * g1 * n * u;
+    a[AU] += Pb * g1 * m * n;
+    const P4<T> me = s.pos[i];
+    const T xi = me.x, yi = me.y, zi = me.z, Hi = me.w;
+    const T xim1 = xi - T(1), yim1 = yi - T(1), zim1 = zi - T(1);
+    const T iH = T(1) / Hi;
+    const int cnt = min(ncount[i], p.cap);
+    const unsigned* L = nbr + (size_t)i * p.cap;
+    double dsum = 0.0;
+    for (int kk = 0; kk < cnt; ++kk) {
+        const P4<T> qj = s.pos[L[kk]];
+        const T r = sqrt(sep2(mi_diff(qj.x, xi, xim1), mi_diff(qj.y, yi, yim1), mi_diff(qj.z, zi, zim1)));
+        const T q = r * iH;
+        dsum += (double)kern_dw(q) * (double)q;
+    }
+    const double H = Hi;
+    const double c8 = 8.0 / (kPi * H * H * H);
+    const double dndH = -3.0 * n / H - c8 * dsum / H;
+    const double fH = -(32.0 / 3.0) * dsum / H;
+    const double Hbt = a[AH] + nb * dndH;
+    const double lam = fH != 0.0 ? -Hbt / fH : 0.0;
+    const double kappa = (nb * c8 + lam * 32.0 / 3.0) / H;
+    kap[i] = kappa;
+    double xb[3] = {0, 0, 0};
+    for (int kk = 0; kk < cnt; ++kk) {
+        const P4<T> qj = s.pos[L[kk]];
+        const T dx = mi_diff(qj.x, xi, xim1), dy = mi_diff(qj.y, yi, yim1), dz = mi_diff(qj.z, zi, zim1);
+        const T r = sqrt(sep2(dx, dy, dz));
+        if (!(r > T(0))) continue;
+        const double c = kappa * (double)kern_dw(r * iH) / (double)r;
+        xb[0] -= c * dx;
+        xb[1] -= c * dy;
+        xb[2] -= c * dz;
+    }
+    a[AX] += xb[0];
+    a[AX + 1] += xb[1];
+    a[AX + 2] += xb[2];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_dens_gather(int N, Sorted<T> s, const unsigned* __restrict__ nbr, const int* __restrict__ ncount,
+                  const unsigned* __restrict__ rnbr, const int* __restrict__ rcount, KParams p,
+                  const double* __restrict__ kap, double* __restrict__ adj) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const P4<T> mj = s.pos[j];
+    double xb[3] = {0, 0, 0};
+    for (int list = 0; list < 2; ++list) {
+        const unsigned* Lj = list == 0 ? nbr + (size_t)j * p.cap : rnbr + (size_t)j * p.rcap;
+        const int cnt = list == 0 ? min(ncount[j], p.cap) : min(rcount[j], p.rcap);
+        for (int kk = 0; kk < cnt; ++kk) {
+            const int i = (int)Lj[kk];
+            const P4<T> mi = s.pos[i];
+            const T dx = mi_diff(mj.x, mi.x, mi.x - T(1)), dy = mi_diff(mj.y, mi.y, mi.y - T(1)),
+                    dz = mi_diff(mj.z, mi.z, mi.z - T(1));
+            const T r2 = sep2(dx, dy, dz);
+            if (!(r2 < mi.w * mi.w)) continue;
+            const T r = sqrt(r2);
+            if (!(r > T(0))) continue;
+            const double c = kap[i] * (double)kern_dw(r * (T(1) / mi.w)) / (double)r;
+            xb[0] += c * dx;
+            xb[1] += c * dy;
+            xb[2] += c * dz;
+        }
+    }
+    double* a = adj + (size_t)j * kAdj;
+    a[AX] += xb[0];
+    a[AX + 1] += xb[1];
+    a[AX + 2] += xb[2];
+}
+
+template <typename T>
+__global__ void k_adj_out_step(int N, const unsigned* __restrict__ orig, const double* __restrict__ adj,
+                               gz_particles gs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const unsigned o = orig[i];
+    const double* a = adj + (size_t)i * kAdj;
+    if (gs.x) ((T*)gs.x)[o] = (T)a[AX];
+    if (gs.y) ((T*)gs.y)[o] = (T)a[AX + 1];
+    if (gs.z) ((T*)gs.z)[o] = (T)a[AX + 2];
+    if (gs.vx) ((T*)gs.vx)[o] = (T)a[AV];
+    if (gs.vy) ((T*)gs.vy)[o] = (T)a[AV + 1];
+    if (gs.vz) ((T*)gs.vz)[o] = (T)a[AV + 2];
+    if (gs.u) ((T*)gs.u)[o] = (T)a[AU];
+    if (gs.m) ((T*)gs.m)[o] = (T)a[AM];
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t run_step_adjoint(Ctx& c, const gz_particles& gend, gz_particles& gstart) {
+    const int N = c.N;
+    const KParams kp = kparams(c);
+    Sorted<T> s = sorted_view<T>(c);
+    c.launches += 8;
+    cudaMemsetAsync(c.adj, 0, sizeof(double) * (size_t)N * kAdj, c.stream);
+    k_update_adj<T><<<blocks(N, 256), 256, 0, c.stream>>>(N, s, c.dpdt, c.dEdt, c.dt_use, gend, c.adj, c.wgt);
+    k_flux_adj<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, (const T*)c.rec, (const T*)c.sn, c.sid, c.sbox,
+                                                         c.nbr, c.ncount, c.rnbr, c.rcount, kp, c.dt_use,
+                                                         c.wgt, c.adj);
+    k_grad_seeds<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, (const T*)c.rec, (const T*)c.ginfo, c.lim,
+                                                           c.nbr, c.ncount, kp, c.adj, c.seeds);
+    k_grad_gather<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, c.lim, c.nbr, c.ncount, c.rnbr, c.rcount,
+                                                            kp, c.seeds, c.adj);
+    k_dens_seeds<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, c.nbr, c.ncount, kp, c.adj, c.wgt);
+    k_dens_gather<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, c.nbr, c.ncount, c.rnbr, c.rcount, kp,
+                                                            c.wgt, c.adj);
+    k_adj_out_step<T><<<blocks(N, 256), 256, 0, c.stream>>>(N, c.vals, c.adj, gstart);
+    return cudaGetLastError();
+}
+template cudaError_t run_step_adjoint<float>(Ctx&, const gz_particles&, gz_particles&);
+template cudaError_t run_step_adjoint<double>(Ctx&, const gz_particles&, gz_particles&);
 
 cudaError_t ensure_adjoint_scratch(Ctx& c) {
     if (c.adj) return cudaSuccess;

@@ -194,6 +194,41 @@ gz_status do_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const void* n, 
     return cuda_check(ctx, e, "gz_hydro_fluxes_backward");
 }
 
+// Adjoint of gz_step: the forward passes are re-run from the start state
+// (neighbour sets, H, gradients, records and rates recomputed, not stored),
+// then the adjoint passes run in reverse order.
+template <typename T>
+gz_status do_step_backward(gz_ctx* ctx, const gz_particles* p, double dt, const gz_particles* gend,
+                           gz_particles* gstart) {
+    Ctx& c = ctx->c;
+    cudaError_t e = ensure_adjoint_scratch(c);
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_SORT);
+        e = sort_and_bin<T>(c, *p, nullptr);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_DENSITY);
+        e = run_density<T>(c);
+    }
+    if (e == cudaSuccess) e = run_prim<T>(c);
+    if (e == cudaSuccess) e = run_reverse<T>(c);
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_GRAD);
+        e = run_gradients<T>(c, false, true);
+    }
+    if (e == cudaSuccess) e = run_dt_set(c, dt);
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_FLUX);
+        e = run_fluxes<T>(c);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_UPDATE);
+        e = run_step_adjoint<T>(c, *gend, *gstart);
+    }
+    c.nbr_valid = 1;
+    return cuda_check(ctx, e, "gz_step_backward");
+}
+
 template <typename T>
 gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev) {
     Ctx& c = ctx->c;
@@ -462,11 +497,11 @@ gz_status gz_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
 gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt,
                            const gz_particles* gbar_end, gz_particles* gbar_start) {
     if (!ctx) return GZ_E_INVAL;
-    (void)p_start;
-    (void)dt;
-    (void)gbar_end;
-    (void)gbar_start;
-    return fail(ctx, GZ_E_INVAL, "gz_step_backward: not available in this build");
+    if (gz_status s = check_particles(ctx, p_start, true)) return s;
+    if (!gbar_end || !gbar_start) return fail(ctx, GZ_E_INVAL, "null adjoint set");
+    if (!(dt > 0.0) || !isfinite(dt)) return fail(ctx, GZ_E_INVAL, "dt must be finite and > 0");
+    return GZ_DISPATCH(do_step_backward<float>(ctx, p_start, dt, gbar_end, gbar_start),
+                       do_step_backward<double>(ctx, p_start, dt, gbar_end, gbar_start));
 }
 
 gz_status gz_get_neighbours(gz_ctx* ctx, int32_t* count_out, int64_t* ids_out, int32_t cap) {

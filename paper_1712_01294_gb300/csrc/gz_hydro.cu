@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(128)
     k_gradients(int N, Sorted<T> s, const unsigned* __restrict__ nbr, const int* __restrict__ ncount,
                 const unsigned* __restrict__ rnbr, const int* __restrict__ rcount, KParams p,
                 T* __restrict__ rec, double* __restrict__ dti, unsigned long long* __restrict__ dtmin,
-                DevStatus* st, int want_dt) {
+                DevStatus* st, int want_dt, T* __restrict__ ginfo, int* __restrict__ lim) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = i < N;
     double dt_i = INFINITY;
@@ -280,9 +280,11 @@ __global__ void __launch_bounds__(128)
         T E[6] = {0, 0, 0, 0, 0, 0};
         T Sg[15];
         T fmax[5], fmin[5];
+        int kmax[5], kmin[5];  // particles holding the extremes (for the adjoint)
 #pragma unroll
         for (int f = 0; f < 5; ++f) {
             fmax[f] = fmin[f] = Wi[f];
+            kmax[f] = kmin[f] = i;
             Sg[3 * f] = Sg[3 * f + 1] = Sg[3 * f + 2] = T(0);
         }
         T vmax = T(0);
@@ -324,8 +326,14 @@ __global__ void __launch_bounds__(128)
                     Sg[3 * f] += df * pdx;
                     Sg[3 * f + 1] += df * pdy;
                     Sg[3 * f + 2] += df * pdz;
-                    fmax[f] = max(fmax[f], Wj[f]);
-                    fmin[f] = min(fmin[f], Wj[f]);
+                    if (Wj[f] > fmax[f]) {
+                        fmax[f] = Wj[f];
+                        kmax[f] = (int)js[u];
+                    }
+                    if (Wj[f] < fmin[f]) {
+                        fmin[f] = Wj[f];
+                        kmin[f] = (int)js[u];
+                    }
                 }
                 if (want_dt) {
                     const T vd = ((Wj[1] - Wi[1]) * dx + (Wj[2] - Wi[2]) * dy) + (Wj[3] - Wi[3]) * dz;
@@ -391,6 +399,8 @@ __global__ void __launch_bounds__(128)
         }
         // O9 limiter: alpha_f = min_j min(1, beta (f_ext - f_i) / (g . s_ij d))
         T al[5] = {T(1), T(1), T(1), T(1), T(1)};
+        int jact[5] = {-1, -1, -1, -1, -1}, kact[5] = {i, i, i, i, i};
+        T Dact[5] = {T(0), T(0), T(0), T(0), T(0)};
         const T beta = (T)p.beta;
         for (int k0 = 0; k0 < cnt; k0 += 4) {
             const uint4 jj = *reinterpret_cast<const uint4*>(L + k0);
@@ -414,7 +424,12 @@ __global__ void __launch_bounds__(128)
                         a = min(T(1), beta * (fmax[f] - Wi[f]) / D);
                     else if (D < T(0))
                         a = min(T(1), beta * (fmin[f] - Wi[f]) / D);
-                    al[f] = min(al[f], a);
+                    if (a < al[f]) {
+                        al[f] = a;
+                        jact[f] = (int)js[u];
+                        kact[f] = D > T(0) ? kmax[f] : kmin[f];
+                        Dact[f] = D;
+                    }
                 }
             }
         }
@@ -435,6 +450,21 @@ __global__ void __launch_bounds__(128)
             }
             dt_i = (any && vmax > T(0)) ? 2.0 * cbrt(1.0 / (double)ni) / (double)vmax : INFINITY;
             dti[i] = dt_i;
+        }
+        if (ginfo) {  // what the adjoint of this pass needs
+            T* G = ginfo + (size_t)i * kGInfo;
+#pragma unroll
+            for (int q = 0; q < 15; ++q) {
+                G[q] = gt[q];
+                G[15 + q] = Sg[q];
+            }
+#pragma unroll
+            for (int f = 0; f < 5; ++f) {
+                G[30 + f] = al[f];
+                G[35 + f] = Dact[f];
+                lim[(size_t)i * 10 + f] = jact[f];
+                lim[(size_t)i * 10 + 5 + f] = kact[f];
+            }
         }
         T* R = rec + (size_t)i * kRecord;
         R[0] = xi;
@@ -788,12 +818,13 @@ cudaError_t run_prim(Ctx& c) {
 }
 
 template <typename T>
-cudaError_t run_gradients(Ctx& c, bool want_dt) {
+cudaError_t run_gradients(Ctx& c, bool want_dt, bool with_info) {
     c.launches += want_dt ? 2 : 1;
     if (want_dt) k_dt_init<<<blocks(c.nboxes, 256), 256, 0, c.stream>>>(c.nboxes, (unsigned long long*)c.dt_box);
     k_gradients<T><<<blocks(c.N, 128), 128, 0, c.stream>>>(
         c.N, sorted_view<T>(c), c.nbr, c.ncount, c.rnbr, c.rcount, kparams(c), (T*)c.rec, c.dti,
-        (unsigned long long*)c.dt_box, c.status, want_dt ? 1 : 0);
+        (unsigned long long*)c.dt_box, c.status, want_dt ? 1 : 0, with_info ? (T*)c.ginfo : nullptr,
+        with_info ? c.lim : nullptr);
     return cudaGetLastError();
 }
 
@@ -870,7 +901,7 @@ cudaError_t run_get_neighbours(Ctx& c, int32_t* count_out, int64_t* ids_out, int
     template cudaError_t run_build_lists<T>(Ctx&);                   \
     template cudaError_t run_reverse<T>(Ctx&);                       \
     template cudaError_t run_prim<T>(Ctx&);                          \
-    template cudaError_t run_gradients<T>(Ctx&, bool);               \
+    template cudaError_t run_gradients<T>(Ctx&, bool, bool);         \
     template cudaError_t run_pack_given<T>(Ctx&, const T*, const T*); \
     template cudaError_t run_grad_out<T>(Ctx&, T*, T*);              \
     template cudaError_t run_fluxes<T>(Ctx&);                        \

@@ -15,8 +15,8 @@ namespace gz {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kRecord = 32;  // values per packed particle record (flux pass)
 constexpr int kAdj = 33;     // adjoint values per particle (see gz_adjoint.cu)
-constexpr int kSeed = 44;    // gradient-pass adjoint seeds per particle
-constexpr int kGInfo = 25;   // raw gradients, limiter factors, active limiter offsets
+constexpr int kSeed = 46;    // gradient-pass adjoint seeds per particle
+constexpr int kGInfo = 40;   // raw gradients, S sums, limiter factors, active limiter Delta
 
 // Device status word (one per context).
 struct DevStatus {

@@ -30,7 +30,7 @@ cudaError_t run_reverse(Ctx& c);
 template <typename T>
 cudaError_t run_prim(Ctx& c);
 template <typename T>
-cudaError_t run_gradients(Ctx& c, bool want_dt);
+cudaError_t run_gradients(Ctx& c, bool want_dt, bool with_info = false);
 template <typename T>
 cudaError_t run_timestep_only(Ctx& c);
 template <typename T>
@@ -54,6 +54,8 @@ cudaError_t run_pair_count(Ctx& c, long long* out_dev);
 cudaError_t ensure_adjoint_scratch(Ctx& c);
 template <typename T>
 cudaError_t run_flux_adjoint(Ctx& c, const double* dpbar, const double* dEbar);
+template <typename T>
+cudaError_t run_step_adjoint(Ctx& c, const gz_particles& gend, gz_particles& gstart);
 cudaError_t run_adj_out_flux(Ctx& c, double* xbar, double* hbar, double* nbar, double* Wbar, double* gbar,
                              double* Bbar);
 

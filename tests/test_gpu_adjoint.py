@@ -112,3 +112,40 @@ def test_flux_adjoint_matches_autograd(prec):
         errs[f"B{q_}"] = check(f"B{q_}", o["B"][q_], ref[25 + q_], prec)
     print("flux adjoint errors", prec, {k: f"{v:.2e}" for k, v in errs.items()})
     assert_all()
+
+
+KEYS = ("x", "y", "z", "vx", "vy", "vz", "m", "u")
+OUTK = ("x", "y", "z", "vx", "vy", "vz", "u")
+
+
+def step_adjoint_case(make, prec, seed=7, tol=None):
+    """(oracle gradient dict, CUDA gradient dict) of J = sum <gbar, state_after>
+    with respect to the state before one step (dt and neighbour sets frozen)."""
+    m = gz()
+    q = cast_state(make(), prec)
+    prm = O.params(tol=1e-12 if prec == 0 else 1e-6)
+    fr, s, Hs, n = TS.freeze(q.__dict__, prm)
+    st = TS.as_tensors(s, requires_grad=True)
+    out = TS.step(st, fr)
+    rng = np.random.default_rng(seed)
+    gbar = {k: rng.normal(size=s.N) for k in OUTK}
+    J = sum((out[k] * torch.tensor(gbar[k])).sum() for k in OUTK)
+    ref = dict(zip(KEYS, (g.numpy() for g in torch.autograd.grad(J, [st[k] for k in KEYS]))))
+    ctx = m.Context([s.N], m.default_params(precision=prec, tol=1e-12 if prec == 0 else 1e-6))
+    d = device(q, prec)
+    T = d["x"].dtype
+    gend = {k: torch.as_tensor(gbar[k], dtype=T).cuda().contiguous() for k in OUTK}
+    gstart = {k: torch.zeros(s.N, dtype=T, device="cuda") for k in KEYS}
+    ctx.step_backward(d, fr.dt, gend, gstart)
+    st_ = ctx.status(reset=True)
+    assert st_["ok"], st_
+    got = {k: v.cpu().numpy().astype(np.float64) for k, v in gstart.items()}
+    return ref, got
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_step_adjoint_matches_autograd(prec):
+    ref, got = step_adjoint_case(lambda: I.smooth_turbulence(12, seed=3), prec)
+    errs = {k: check(k, got[k], ref[k], prec) for k in KEYS}
+    print("step adjoint errors", prec, {k: f"{v:.2e}" for k, v in errs.items()})
+    assert_all()
