@@ -1,0 +1,70 @@
+"""torch.autograd bridge for the MFM step: forward = gz_step, backward =
+gz_step_backward (the hand-written adjoint in the CUDA library).
+
+Per-step checkpointing: each MFMStep node keeps only the state its step
+started from (x, y, z, vx, vy, vz, m, u, h); the backward pass re-runs that
+step's forward passes inside gz_step_backward (neighbour sets, H, gradients
+and pair quantities recomputed, not stored).  The step dt is frozen at the
+value the forward used: a CFL step is read back once per step.
+
+Differentiable inputs: x, y, z, vx, vy, vz, m, u.  The support radius h is
+passed through (a converged H does not depend on its initial guess) and ids
+are integers.
+"""
+from __future__ import annotations
+
+import torch
+
+STATE = ("x", "y", "z", "vx", "vy", "vz", "m", "u", "h")
+GRADS = ("x", "y", "z", "vx", "vy", "vz", "m", "u")
+OUT = ("x", "y", "z", "vx", "vy", "vz", "u", "h")
+
+
+class MFMStep(torch.autograd.Function):
+    """One MFM step of a gz Context with autograd support."""
+
+    @staticmethod
+    def forward(fctx, gz_ctx, dt, ids, x, y, z, vx, vy, vz, m, u, h):
+        cur = {"x": x.clone(), "y": y.clone(), "z": z.clone(), "vx": vx.clone(), "vy": vy.clone(),
+               "vz": vz.clone(), "m": m, "u": u.clone(), "h": h.clone(), "id": ids}
+        dtu = torch.empty(1, dtype=torch.float64, device=x.device)
+        gz_ctx.step(cur, float(dt), dtu)
+        used = float(dt) if dt > 0 else float(dtu.item())
+        fctx.save_for_backward(x, y, z, vx, vy, vz, m, u, h)
+        fctx.gz_ctx, fctx.ids, fctx.dt = gz_ctx, ids, used
+        gz_ctx.last_dt = used
+        fctx.mark_non_differentiable(cur["h"])
+        return tuple(cur[k] for k in OUT)
+
+    @staticmethod
+    def backward(fctx, *gout):
+        x, y, z, vx, vy, vz, m, u, h = fctx.saved_tensors
+        start = {"x": x, "y": y, "z": z, "vx": vx, "vy": vy, "vz": vz, "m": m, "u": u, "h": h,
+                 "id": fctx.ids}
+        gend = {}
+        for k, g in zip(OUT[:-1], gout[:-1]):
+            gend[k] = (g if g is not None else torch.zeros_like(x)).contiguous()
+        gstart = {k: torch.zeros_like(x) for k in GRADS}
+        fctx.gz_ctx.step_backward(start, fctx.dt, gend, gstart)
+        return (None, None, None, gstart["x"], gstart["y"], gstart["z"], gstart["vx"],
+                gstart["vy"], gstart["vz"], gstart["m"], gstart["u"], None)
+
+
+def step(gz_ctx, state: dict, dt: float = 0.0) -> dict:
+    """One differentiable step; state holds x..u, h (tensors) and id."""
+    outs = MFMStep.apply(gz_ctx, float(dt), state["id"], *(state[k] for k in STATE))
+    new = dict(zip(OUT, outs))
+    new["m"] = state["m"]
+    new["id"] = state["id"]
+    return new
+
+
+def rollout(gz_ctx, state: dict, nsteps: int, dts=None):
+    """nsteps differentiable steps (CFL steps unless dts gives them); returns
+    the final state and the list of steps used."""
+    used = []
+    for k in range(nsteps):
+        dt = 0.0 if dts is None else float(dts[k])
+        state = step(gz_ctx, state, dt)
+        used.append(gz_ctx.last_dt)
+    return state, used

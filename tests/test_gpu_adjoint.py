@@ -149,3 +149,94 @@ def test_step_adjoint_matches_autograd(prec):
     errs = {k: check(k, got[k], ref[k], prec) for k in KEYS}
     print("step adjoint errors", prec, {k: f"{v:.2e}" for k, v in errs.items()})
     assert_all()
+
+
+def region_ke(state, mask):
+    v2 = state["vx"] ** 2 + state["vy"] ** 2 + state["vz"] ** 2
+    return (0.5 * state["m"].to(torch.float64) * v2.to(torch.float64) * mask).sum()
+
+
+def kh_rollout_grad(prec, n=20, nsteps=3, smooth=0.08, seed=1715):
+    """Gradient of the KH loss (kinetic energy of the particles that start at
+    y > 0.75) after nsteps, with respect to initial v and u, via MFMStep."""
+    m = gz()
+    from paper_1712_01294_gb300 import autograd as GA
+    q = cast_state(I.kh(n, seed=seed, smooth=smooth), prec)
+    ctx = m.Context([q.N], m.default_params(precision=prec, tol=1e-12 if prec == 0 else 1e-6))
+    d = device(q, prec)
+    for k in ("vx", "vy", "vz", "u"):
+        d[k].requires_grad_(True)
+    mask = torch.as_tensor(q.y > 0.75, dtype=torch.float64).cuda()
+    fin, dts = GA.rollout(ctx, dict(d), nsteps)
+    L = region_ke(fin, mask)
+    L.backward()
+    grads = {k: d[k].grad.detach().cpu().numpy().astype(np.float64) for k in ("vx", "vy", "vz", "u")}
+    st_ = ctx.status(reset=True)
+    assert st_["ok"], st_
+    return q, ctx, mask, dts, float(L), grads
+
+
+def test_rollout_gradient_matches_central_differences():
+    """FP64 path: <dL/d(v0, u0), delta> against central differences of the CUDA
+    forward with the same frozen step sequence (spec bar: 1e-4)."""
+    q, ctx, mask, dts, L0, grads = kh_rollout_grad(0, n=24, smooth=0.1)
+    # along the gradient itself: a random direction nearly cancels, and then
+    # the O(eps) jumps of limiter extrema switching in the shear layer dominate
+    norm = np.sqrt(sum(float(np.sum(g * g)) for g in grads.values()))
+    delta = {k: g / norm for k, g in grads.items()}
+    dd = sum(float(np.sum(grads[k] * delta[k])) for k in grads)
+
+    def loss(eps):
+        d = device(q, 0)
+        for k in delta:
+            d[k] = d[k] + eps * torch.as_tensor(delta[k]).cuda()
+        for dt in dts:
+            ctx.step(d, dt)
+        return float(region_ke(d, mask))
+    fds = []
+    for eps in (1e-4, 1e-5, 1e-6):
+        fds.append((loss(eps) - loss(-eps)) / (2 * eps))
+    rel = min(abs(fd - dd) / abs(fd) for fd in fds)
+    print("rollout FD check", dd, fds, rel)
+    assert rel <= 1e-4, (dd, fds)
+
+
+def test_rollout_fp32_gradient_close_to_fp64():
+    _, _, _, _, L64, g64 = kh_rollout_grad(0)
+    _, _, _, _, L32, g32 = kh_rollout_grad(1)
+    assert abs(L32 - L64) <= 1e-5 * abs(L64)
+    for k in g64:
+        err = rms(g32[k] - g64[k]) / rms(g64[k])
+        print("fp32 vs fp64 rollout gradient", k, err)
+        assert err <= 1e-2, (k, err)
+
+
+def test_rollout_gradient_matches_dual_number_oracle():
+    """Two FP64 steps: directional derivative from the PyTorch oracle's dual
+    numbers (neighbour sets frozen per step at the oracle's own states)."""
+    import torch.autograd.forward_ad as fwAD
+    prec, nsteps = 0, 2
+    q, ctx, mask, dts, L0, grads = kh_rollout_grad(prec, n=12, nsteps=nsteps, smooth=0.12)
+    rng = np.random.default_rng(9)
+    delta = {k: rng.normal(size=q.N) for k in grads}
+    dd = sum(float(np.sum(grads[k] * delta[k])) for k in grads)
+    prm = O.params(tol=1e-12)
+    s = ostate(q)
+    with fwAD.dual_level():
+        st = TS.as_tensors(s)
+        st = {k: (fwAD.make_dual(v, torch.as_tensor(delta[k])) if k in delta else v) for k, v in st.items()}
+        cur_np = s
+        for k_step in range(nsteps):
+            fr, _, _, _ = TS.freeze({**cur_np.__dict__}, prm)
+            fr.dt = dts[k_step]
+            out = TS.step(st, fr)
+            out["m"] = st["m"]
+            st = out
+            vals = {k: fwAD.unpack_dual(v).primal.numpy() for k, v in st.items()}
+            cur_np = O.State(vals["x"], vals["y"], vals["z"], vals["vx"], vals["vy"], vals["vz"],
+                             vals["m"], vals["u"], fr.Hstar.numpy(), s.id)
+        v2 = st["vx"] ** 2 + st["vy"] ** 2 + st["vz"] ** 2
+        Lt = (0.5 * st["m"] * v2 * torch.as_tensor(mask.cpu().numpy())).sum()
+        dual = fwAD.unpack_dual(Lt).tangent.item()
+    print("rollout dual-number check", dd, dual)
+    assert abs(dd - dual) <= 1e-9 * abs(dual), (dd, dual)
