@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cell-factor", type=float, default=None)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64-path, adjoint and ensemble measurements")
     return ap.parse_args()
 
 
@@ -191,13 +193,14 @@ def run_ours(a, world, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_e2e = e0.elapsed_time(e1)
+        extras = {} if a.no_extras else measure_extras(a, ctx, d, dtu, stream, prec, p)
     tmax = ms
     if dist:
         tt = torch.tensor([ms, ms_e2e], dtype=torch.float64, device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         tmax, ms_e2e = float(tt[0]), float(tt[1])
     value = world * N * a.steps / (tmax / 1e3)
-    e2e = world * N * a.e2e_steps / (ms_e2e / 1e3)
+    e2e = world * N * a.e2e_steps / (ms_e2e / 1e3) if a.e2e_steps > 0 else None
     # roofline of the dominant kernel
     pk = peaks()
     clocks = clk.summary()
@@ -226,12 +229,131 @@ def run_ours(a, world, rank, local):
         "roofline": roof,
         "pass_ms_per_step": {k: round(v[0] / max(v[1], 1), 4) for k, v in prof.items() if v[1]},
         "pass_share": shares, "dominant_pass": dom,
-        "e2e": {"value": round(e2e, 1), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": round(e2e, 1) if e2e else None, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    line.update(extras)
+    if "fp64_path" in line:
+        line["fp64_path"]["fp32_over_fp64"] = round(value / world / line["fp64_path"]["value"], 2)
+    if "adjoint" in line:
+        adj = line["adjoint"]
+        adj["forward_ms_per_step"] = round(tmax / a.steps, 4)
+        # (forward that saves the checkpoint + backward) / plain forward
+        adj["total_over_forward"] = round(
+            (adj["forward_with_rates_ms_per_step"] + adj["backward_ms_per_step"]) / (tmax / a.steps), 3)
     return line, p
+
+
+def measure_extras(a, ctx, d, dtu, stream, prec, p):
+    """FP64-path throughput, adjoint cost and the batched ensemble (CUDA graph)."""
+    import numpy as np
+    import torch
+
+    import paper_1712_01294_gb300 as gz
+    from paper_1712_01294_gb300 import autotune
+    from paper_1712_01294_gb300 import inputs as I
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        # adjoint of one step (same workload, same precision), dt frozen, in the
+        # configuration MFMStep runs it: the forward saves its rates
+        # (gz_step_rates) and the converged H, the backward recomputes the
+        # density and gradient passes and every pair quantity
+        rng = np.random.default_rng(0)
+        T = d["x"].dtype
+        start = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in d.items()}
+        rates = torch.empty(4 * p.N, dtype=torch.float64, device="cuda")
+        K = max(2, a.steps // 2)
+        fwd = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in start.items()}
+        ctx.step(fwd, 0.0, dtu, rates)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(K):
+            ctx.step(fwd, 0.0, dtu, rates)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_fwd_ckpt = e0.elapsed_time(e1) / K
+        fwd = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in start.items()}
+        ctx.step(fwd, 0.0, dtu, rates)
+        dt = float(dtu.item())
+        ckpt = dict(start)
+        ckpt["h"] = fwd["h"]
+        gend = {k: torch.as_tensor(rng.normal(size=p.N), dtype=T).cuda() for k in
+                ("x", "y", "z", "vx", "vy", "vz", "u")}
+        gstart = {k: torch.zeros(p.N, dtype=T, device="cuda") for k in
+                  ("x", "y", "z", "vx", "vy", "vz", "u", "m")}
+        ctx.step_backward(ckpt, dt, gend, gstart, rates)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(K):
+            ctx.step_backward(ckpt, dt, gend, gstart, rates)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_bwd = e0.elapsed_time(e1) / K
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(K):
+            ctx.step_backward(start, dt, gend, gstart)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_bwd_full = e0.elapsed_time(e1) / K
+        st = ctx.status(reset=True)
+        out["adjoint"] = {"backward_ms_per_step": round(ms_bwd, 4),
+                          "forward_with_rates_ms_per_step": round(ms_fwd_ckpt, 4),
+                          "backward_full_recompute_ms_per_step": round(ms_bwd_full, 4),
+                          "steps": K, "status_ok": st["ok"],
+                          "what": "gz_step_backward from the MFMStep checkpoint (start state, "
+                                  "converged H, saved rates): density, gradient passes and all "
+                                  "pair quantities recomputed, then the adjoint passes"}
+        # FP64 path on the same workload
+        if prec == gz.GZ_MIXED32:
+            c64 = gz.Context([p.N], gz.default_params(precision=gz.GZ_FP64), stream=stream)
+            d64 = gz.to_device(p, gz.GZ_FP64)
+            c64.step(d64)
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            for _ in range(3):
+                c64.step(d64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64 = e0.elapsed_time(e1) / 3
+            out["fp64_path"] = {"value": round(p.N / (ms64 / 1e3), 1), "unit": UNIT,
+                                "ms_per_step": round(ms64, 3), "steps": 3,
+                                "status_ok": c64.status(reset=True)["ok"]}
+            c64.close()
+            del d64
+        # batched ensemble: 256 boxes, 20 steps captured as one CUDA graph
+        ens = I.ensemble(256, seed=1716)
+        counts = [int(c) for c in ens.counts]
+        cf, tune_ms = autotune.tune(ens, gz.GZ_MIXED32, steps=2, use_cache=False)
+        ce = gz.Context(counts, gz.default_params(precision=gz.GZ_MIXED32, cell_factor=cf),
+                        stream=stream)
+        de = gz.to_device(ens, gz.GZ_MIXED32)
+        dte = torch.zeros(len(counts), dtype=torch.float64, device="cuda")
+        l0 = ce.info()["launches"]
+        ce.graph_capture(de, 20, 0.0, dte)
+        ce.graph_launch()
+        e0, e1 = ev(), ev()
+        R = 3
+        l1 = ce.info()["launches"]
+        e0.record(stream)
+        for _ in range(R):
+            ce.graph_launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msg = e0.elapsed_time(e1) / R
+        ntot = sum(counts)
+        out["ensemble"] = {"value": round(ntot * 20 / (msg / 1e3), 1), "unit": UNIT,
+                           "boxes": len(counts), "particles": ntot, "steps_per_graph": 20,
+                           "ms_per_graph": round(msg, 3), "graph_replays": R,
+                           "kernels_per_graph": (ce.info()["launches"] - l1) // R,
+                           "cell_factor": cf, "tuning_ms_per_step": {str(k): round(v, 3) for k, v in
+                                                                      tune_ms.items()},
+                           "status_ok": ce.status(reset=True)["ok"]}
+        ce.close()
+    return out
 
 
 def cpu_sample_rate(p, threads=None, sample_frac=1.0 / 8):

@@ -187,13 +187,37 @@ gz_status gz_hydro_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const voi
  * doubles, may be NULL) receives the steps used.  No host synchronisation. */
 gz_status gz_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev);
 
+/* Captures nsteps consecutive gz_step calls on p (same arguments as gz_step)
+ * into a CUDA graph owned by the context, replacing any earlier one; nothing
+ * is executed.  The context's stream must be a created (non-default) stream.
+ * gz_graph_launch replays the captured steps on that stream (the graph
+ * keeps p's pointers: replays advance the same arrays).  Host
+ * synchronisation: none in either call. */
+gz_status gz_graph_capture(gz_ctx* ctx, gz_particles* p, int32_t nsteps, double dt_fixed,
+                           double* dt_used_dev);
+gz_status gz_graph_launch(gz_ctx* ctx);
+
+/* gz_step that also saves the step's conserved-variable rates for its
+ * adjoint: the momentum and total-energy rates of the MFM update (the
+ * "Arbitrary (Moving) Meshes" section, the MFM rates of O12).
+ * rates_out: device, [4][N] doubles in the caller's particle order, rows
+ * dp_x/dt, dp_y/dt, dp_z/dt, dE/dt; caller-owned; NULL makes the call
+ * identical to gz_step.  Host synchronisation: none. */
+gz_status gz_step_rates(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev,
+                        double* rates_out);
+
 /* Adjoint of one gz_step (all of O4-O14 with the step dt held fixed and
  * neighbour sets frozen at their forward values).  p_start is the state the
- * forward step started from (it is not modified); gbar_end holds dL/d(state
- * after the step) for x, y, z, vx, vy, vz, u (m, h, id ignored; arrays in the
- * working precision); gbar_start receives dL/d(state before the step) for
- * x, y, z, vx, vy, vz, u and m.  dt is the step the forward used. */
-gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt,
+ * forward step started from (it is not modified); its h is the initial guess
+ * of the support radius: passing the h that the forward step returned (the
+ * converged H) makes the h-iteration accept it at once, with the same H, lists
+ * and sums as the forward.  rates (device, [4][N] as written by gz_step_rates
+ * for this step, or NULL) replace the recomputed flux pass; NULL recomputes
+ * it.  gbar_end holds dL/d(state after the step) for x, y, z, vx, vy, vz, u
+ * (m, h, id ignored; arrays in the working precision); gbar_start receives
+ * dL/d(state before the step) for x, y, z, vx, vy, vz, u and m.  dt is the
+ * step the forward used (> 0).  Host synchronisation: none. */
+gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt, const double* rates,
                            const gz_particles* gbar_end, gz_particles* gbar_start);
 
 /* Copies the neighbour lists of the last gz_density / gz_step: count_out

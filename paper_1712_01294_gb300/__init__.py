@@ -82,7 +82,10 @@ def load_library(build_if_missing: bool = True):
             "gz_hydro_fluxes": (st, [vp, P, vp, vp, vp, d, vp, vp]),
             "gz_step": (st, [vp, P, d, vp]),
             "gz_hydro_fluxes_backward": (st, [vp, P, vp, vp, vp, d, vp, vp, vp, vp, vp, vp, vp, vp]),
-            "gz_step_backward": (st, [vp, P, d, P, P]),
+            "gz_graph_capture": (st, [vp, P, i32, d, vp]),
+            "gz_graph_launch": (st, [vp]),
+            "gz_step_rates": (st, [vp, P, d, vp, vp]),
+            "gz_step_backward": (st, [vp, P, d, vp, P, P]),
             "gz_get_neighbours": (st, [vp, vp, vp, i32]),
             "gz_get_status": (st, [vp, vp, vp, vp, i32]),
             "gz_last_error": (C.c_char_p, [vp]),
@@ -230,17 +233,44 @@ class Context:
             _ptr(out["grad"]), _ptr(out["B"])), "gz_hydro_fluxes_backward")
         return out
 
-    def step(self, p, dt_fixed: float = 0.0, dt_used=None):
-        """gz_step in place on p; dt_used (device float64 [nboxes]) receives the steps."""
+    def step(self, p, dt_fixed: float = 0.0, dt_used=None, rates=None):
+        """gz_step in place on p; dt_used (device float64 [nboxes]) receives the
+        steps; with rates (device float64 [4, N]) gz_step_rates also saves the
+        step's momentum and energy rates for gz_step_backward."""
         s = self._parts(p)
-        self._check(self.lib.gz_step(self.h, C.byref(s), float(dt_fixed), _ptr(dt_used)), "gz_step")
+        if rates is None:
+            self._check(self.lib.gz_step(self.h, C.byref(s), float(dt_fixed), _ptr(dt_used)), "gz_step")
+        else:
+            self._rates_ok(rates)
+            self._check(self.lib.gz_step_rates(self.h, C.byref(s), float(dt_fixed), _ptr(dt_used),
+                                               _ptr(rates)), "gz_step_rates")
         return dt_used
 
-    def step_backward(self, p_start, dt, gbar_end, gbar_start):
-        """gz_step_backward: adjoint of one step (see include/gz.h)."""
+    def _rates_ok(self, rates):
+        if (rates.dtype != self.torch.float64 or not rates.is_cuda or not rates.is_contiguous()
+                or rates.numel() != 4 * self.N):
+            raise ValueError("rates must be a contiguous CUDA float64 tensor of 4*N values")
+
+    def graph_capture(self, p, nsteps: int, dt_fixed: float = 0.0, dt_used=None):
+        """gz_graph_capture: record nsteps steps on p as one CUDA graph (the
+        context stream must be a created torch.cuda.Stream)."""
+        s = self._parts(p)
+        self._graph_parts = s  # the graph keeps these pointers
+        self._check(self.lib.gz_graph_capture(self.h, C.byref(s), int(nsteps), float(dt_fixed),
+                                              _ptr(dt_used)), "gz_graph_capture")
+
+    def graph_launch(self):
+        """gz_graph_launch: replay the captured steps."""
+        self._check(self.lib.gz_graph_launch(self.h), "gz_graph_launch")
+
+    def step_backward(self, p_start, dt, gbar_end, gbar_start, rates=None):
+        """gz_step_backward: adjoint of one step (see include/gz.h); rates are
+        the forward's saved rates (gz_step_rates) or None to recompute them."""
         a, b, c = self._parts(p_start), self._grad_parts(gbar_end), self._grad_parts(gbar_start)
-        self._check(self.lib.gz_step_backward(self.h, C.byref(a), float(dt), C.byref(b), C.byref(c)),
-                    "gz_step_backward")
+        if rates is not None:
+            self._rates_ok(rates)
+        self._check(self.lib.gz_step_backward(self.h, C.byref(a), float(dt), _ptr(rates), C.byref(b),
+                                              C.byref(c)), "gz_step_backward")
         return gbar_start
 
     def _grad_parts(self, g) -> _Particles:

@@ -1,11 +1,15 @@
 """torch.autograd bridge for the MFM step: forward = gz_step, backward =
 gz_step_backward (the hand-written adjoint in the CUDA library).
 
-Per-step checkpointing: each MFMStep node keeps only the state its step
-started from (x, y, z, vx, vy, vz, m, u, h); the backward pass re-runs that
-step's forward passes inside gz_step_backward (neighbour sets, H, gradients
-and pair quantities recomputed, not stored).  The step dt is frozen at the
-value the forward used: a CFL step is read back once per step.
+Per-step checkpointing: each MFMStep node keeps the state its step started
+from (x, y, z, vx, vy, vz, m, u), the converged support radius the step
+returned and the step's per-particle momentum and energy rates (4 doubles a
+particle, from gz_step_rates).  The backward pass re-runs that step's
+density and gradient passes inside gz_step_backward (neighbour sets, H,
+gradients and every pair quantity recomputed, not stored); starting the
+h-iteration at the converged H makes it accept that H at once, and the saved
+rates stand in for the flux pass.  The step dt is frozen at the value the
+forward used: a CFL step is read back once per step.
 
 Differentiable inputs: x, y, z, vx, vy, vz, m, u.  The support radius h is
 passed through (a converged H does not depend on its initial guess) and ids
@@ -28,9 +32,10 @@ class MFMStep(torch.autograd.Function):
         cur = {"x": x.clone(), "y": y.clone(), "z": z.clone(), "vx": vx.clone(), "vy": vy.clone(),
                "vz": vz.clone(), "m": m, "u": u.clone(), "h": h.clone(), "id": ids}
         dtu = torch.empty(1, dtype=torch.float64, device=x.device)
-        gz_ctx.step(cur, float(dt), dtu)
+        rates = torch.empty(4 * x.numel(), dtype=torch.float64, device=x.device)
+        gz_ctx.step(cur, float(dt), dtu, rates)
         used = float(dt) if dt > 0 else float(dtu.item())
-        fctx.save_for_backward(x, y, z, vx, vy, vz, m, u, h)
+        fctx.save_for_backward(x, y, z, vx, vy, vz, m, u, cur["h"], rates)
         fctx.gz_ctx, fctx.ids, fctx.dt = gz_ctx, ids, used
         gz_ctx.last_dt = used
         fctx.mark_non_differentiable(cur["h"])
@@ -38,14 +43,14 @@ class MFMStep(torch.autograd.Function):
 
     @staticmethod
     def backward(fctx, *gout):
-        x, y, z, vx, vy, vz, m, u, h = fctx.saved_tensors
-        start = {"x": x, "y": y, "z": z, "vx": vx, "vy": vy, "vz": vz, "m": m, "u": u, "h": h,
-                 "id": fctx.ids}
+        x, y, z, vx, vy, vz, m, u, h_conv, rates = fctx.saved_tensors
+        start = {"x": x, "y": y, "z": z, "vx": vx, "vy": vy, "vz": vz, "m": m, "u": u,
+                 "h": h_conv.clone(), "id": fctx.ids}
         gend = {}
         for k, g in zip(OUT[:-1], gout[:-1]):
             gend[k] = (g if g is not None else torch.zeros_like(x)).contiguous()
         gstart = {k: torch.zeros_like(x) for k in GRADS}
-        fctx.gz_ctx.step_backward(start, fctx.dt, gend, gstart)
+        fctx.gz_ctx.step_backward(start, fctx.dt, gend, gstart, rates)
         return (None, None, None, gstart["x"], gstart["y"], gstart["z"], gstart["vx"],
                 gstart["vy"], gstart["vz"], gstart["m"], gstart["u"], None)
 

@@ -37,8 +37,8 @@ __device__ __forceinline__ T dkern(T q) {
 // pair_rates does so every branch matches.
 template <typename T>
 __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)[kRecord], bool aL,
-                                             T hdt, T gam, bool hancock, T na, const double* wp,
-                                             double wE, double* adj) {
+                                             T hdt, T gam, bool hancock, T na, const T* wp,
+                                             T wE, T* adj) {
     // ---- forward (same operations as pair_rates)
     const T dx = mi_diff(b[0], a[0], a[0] - T(1));
     const T dy = mi_diff(b[1], a[1], a[1] - T(1));
@@ -117,43 +117,43 @@ __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)
     const T ss = pdiv(num, den);
     const T psr = PL + rL * aLv * (ss - uL);
     const T ps = psr < T(0) ? T(0) : psr;
-    // ---- reverse, in double
-    const double A_[3] = {A[0], A[1], A[2]};
-    const double wpA = (wp[0] * A_[0] + wp[1] * A_[1]) + wp[2] * A_[2];
+    // ---- reverse, in the working precision
+    const T A_[3] = {A[0], A[1], A[2]};
+    const T wpA = (wp[0] * A_[0] + wp[1] * A_[1]) + wp[2] * A_[2];
     // J = -ps (wp . A) - sg wE ps (ss + vfn) |A|
-    const double b_ps = -wpA - (double)sg * wE * ((double)ss + vfn) * (double)Am;
-    double bA[3] = {-(double)ps * wp[0], -(double)ps * wp[1], -(double)ps * wp[2]};
-    double b_ss = -(double)sg * wE * (double)ps * (double)Am;
-    const double b_vfn = b_ss;
-    const double b_Am = -(double)sg * wE * (double)ps * ((double)ss + vfn);
+    const T b_ps = -wpA - (T)sg * wE * ((T)ss + vfn) * (T)Am;
+    T bA[3] = {-(T)ps * wp[0], -(T)ps * wp[1], -(T)ps * wp[2]};
+    T b_ss = -(T)sg * wE * (T)ps * (T)Am;
+    const T b_vfn = b_ss;
+    const T b_Am = -(T)sg * wE * (T)ps * ((T)ss + vfn);
     // ps = max(psr, 0)
-    const double b_psr = psr < T(0) ? 0.0 : b_ps;
+    const T b_psr = psr < T(0) ? T(0) : b_ps;
     // psr = PL + rL aL (ss - uL)
-    double b_PL = b_psr, b_rL = b_psr * aLv * (ss - uL);
-    double b_aL = b_psr * (double)rL * (ss - uL);
-    b_ss += b_psr * (double)rL * aLv;
-    double b_uL = -b_psr * (double)rL * aLv;
-    double b_PR = 0.0, b_rR = 0.0, b_uR = 0.0, b_aR = 0.0;
+    T b_PL = b_psr, b_rL = b_psr * aLv * (ss - uL);
+    T b_aL = b_psr * (T)rL * (ss - uL);
+    b_ss += b_psr * (T)rL * aLv;
+    T b_uL = -b_psr * (T)rL * aLv;
+    T b_PR = T(0), b_rR = T(0), b_uR = T(0), b_aR = T(0);
     // ss = num / den
-    const double b_num = b_ss / (double)den;
-    const double b_den = -b_ss * (double)ss / (double)den;
+    const T b_num = b_ss / (T)den;
+    const T b_den = -b_ss * (T)ss / (T)den;
     b_PR += b_num;
     b_PL -= b_num;
-    b_rL += b_num * (double)uL * aLv;
-    b_uL += b_num * (double)rL * aLv;
-    b_aL += b_num * (double)rL * uL;
-    b_rR -= b_num * (double)uR * aRv;
-    b_uR -= b_num * (double)rR * aRv;
-    b_aR -= b_num * (double)rR * uR;
+    b_rL += b_num * (T)uL * aLv;
+    b_uL += b_num * (T)rL * aLv;
+    b_aL += b_num * (T)rL * uL;
+    b_rR -= b_num * (T)uR * aRv;
+    b_uR -= b_num * (T)rR * aRv;
+    b_aR -= b_num * (T)rR * uR;
     b_rL += b_den * aLv;
     b_aL += b_den * rL;
     b_rR -= b_den * aRv;
     b_aR -= b_den * rR;
     // aL = SL - uL, aR = SR - uR
-    const double b_SL = b_aL, b_SR = b_aR;
+    const T b_SL = b_aL, b_SR = b_aR;
     b_uL -= b_aL;
     b_uR -= b_aR;
-    double b_cL = 0.0, b_cR = 0.0;
+    T b_cL = T(0), b_cR = T(0);
     if (e1 <= e2) {
         b_uL += b_SL;
         b_cL -= b_SL;
@@ -170,83 +170,83 @@ __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)
     }
     // c = sqrt(gamma P / rho)
     if (cL > T(0)) {
-        b_PL += b_cL * (double)gam / (2.0 * (double)cL * (double)rL);
-        b_rL -= b_cL * (double)cL / (2.0 * (double)rL);
+        b_PL += b_cL * (T)gam / (T(2) * (T)cL * (T)rL);
+        b_rL -= b_cL * (T)cL / (T(2) * (T)rL);
     }
     if (cR > T(0)) {
-        b_PR += b_cR * (double)gam / (2.0 * (double)cR * (double)rR);
-        b_rR -= b_cR * (double)cR / (2.0 * (double)rR);
+        b_PR += b_cR * (T)gam / (T(2) * (T)cR * (T)rR);
+        b_rR -= b_cR * (T)cR / (T(2) * (T)rR);
     }
-    double bFL[5] = {b_rL, 0.0, 0.0, 0.0, b_PL};
-    double bFR[5] = {b_rR, 0.0, 0.0, 0.0, b_PR};
-    double bvf[3], bn[3];
+    T bFL[5] = {b_rL, T(0), T(0), T(0), b_PL};
+    T bFR[5] = {b_rR, T(0), T(0), T(0), b_PR};
+    T bvf[3], bn[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         bFL[1 + k] = b_uL * n[k];
         bFR[1 + k] = b_uR * n[k];
         bvf[k] = -(b_uL + b_uR) * n[k] + b_vfn * n[k];
-        bn[k] = b_uL * ((double)FL[1 + k] - vf[k]) + b_uR * ((double)FR[1 + k] - vf[k]) + b_vfn * vf[k];
+        bn[k] = b_uL * ((T)FL[1 + k] - vf[k]) + b_uR * ((T)FR[1 + k] - vf[k]) + b_vfn * vf[k];
     }
     // vf = vL + sL (vR - vL)
-    double bvL[3], bvR[3], b_sL = 0.0;
+    T bvL[3], bvR[3], b_sL = T(0);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        bvL[k] = bvf[k] * (1.0 - (double)sL);
-        bvR[k] = bvf[k] * (double)sL;
-        b_sL += bvf[k] * ((double)vR[k] - vL[k]);
+        bvL[k] = bvf[k] * (T(1) - (T)sL);
+        bvR[k] = bvf[k] * (T)sL;
+        b_sL += bvf[k] * ((T)vR[k] - vL[k]);
     }
     // back to a / b labels
-    double bGa[5], bGb[5];
+    T bGa[5], bGb[5];
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
         bGa[f] = aL ? bFL[f] : bFR[f];
         bGb[f] = aL ? bFR[f] : bFL[f];
     }
-    double bWa[5] = {0, 0, 0, 0, 0};
+    T bWa[5] = {0, 0, 0, 0, 0};
 #pragma unroll
     for (int k = 0; k < 3; ++k) bWa[1 + k] += aL ? bvL[k] : bvR[k];
-    double b_sa = aL ? b_sL : 0.0, b_sb = aL ? 0.0 : b_sL;
+    T b_sa = aL ? b_sL : T(0), b_sb = aL ? T(0) : b_sL;
     // normal n = sg A / |A|, and |A| itself
-    double bnh[3] = {sg * bn[0], sg * bn[1], sg * bn[2]};
-    const double nb_dot = (bnh[0] * nh[0] + bnh[1] * nh[1]) + bnh[2] * nh[2];
+    T bnh[3] = {sg * bn[0], sg * bn[1], sg * bn[2]};
+    const T nb_dot = (bnh[0] * nh[0] + bnh[1] * nh[1]) + bnh[2] * nh[2];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) bA[k] += (bnh[k] - nb_dot * nh[k]) / (double)Am + b_Am * nh[k];
+    for (int k = 0; k < 3; ++k) bA[k] += (bnh[k] - nb_dot * nh[k]) / (T)Am + b_Am * nh[k];
     // fallback and clamps
-    double bFa[5], bFb[5];
+    T bFa[5], bFb[5];
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
         if (fallback) {
             bWa[f] += bGa[f];
-            bFa[f] = 0.0;
-            bFb[f] = 0.0;
+            bFa[f] = T(0);
+            bFb[f] = T(0);
         } else {
-            bFa[f] = 0.0;
-            bFb[f] = 0.0;
+            bFa[f] = T(0);
+            bFb[f] = T(0);
             // a's face value
             if (ka[f] == 0)
                 bFa[f] = bGa[f];
             else if (ka[f] < 0)
-                bWa[f] += (Wa[f] <= Wb[f]) ? bGa[f] : 0.0;  // lower bound min(Wa, Wb)
+                bWa[f] += (Wa[f] <= Wb[f]) ? bGa[f] : T(0);  // lower bound min(Wa, Wb)
             else
-                bWa[f] += (Wa[f] >= Wb[f]) ? bGa[f] : 0.0;  // upper bound max(Wa, Wb)
+                bWa[f] += (Wa[f] >= Wb[f]) ? bGa[f] : T(0);  // upper bound max(Wa, Wb)
             // b's face value (its bounds can be a's values)
             if (kb[f] == 0)
                 bFb[f] = bGb[f];
             else if (kb[f] < 0)
-                bWa[f] += (Wa[f] <= Wb[f]) ? bGb[f] : 0.0;
+                bWa[f] += (Wa[f] <= Wb[f]) ? bGb[f] : T(0);
             else
-                bWa[f] += (Wa[f] >= Wb[f]) ? bGb[f] : 0.0;
+                bWa[f] += (Wa[f] >= Wb[f]) ? bGb[f] : T(0);
         }
     }
     // face states: F_a = W_a + g_a . (s_a d) + hdt D_a ; F_b = W_b + g_b . (s_b (-d)) + hdt D_b
-    double bd[3] = {0.0, 0.0, 0.0};
-    double bg[15];
+    T bd[3] = {T(0), T(0), T(0)};
+    T bg[15];
 #pragma unroll
-    for (int q = 0; q < 15; ++q) bg[q] = 0.0;
+    for (int q = 0; q < 15; ++q) bg[q] = T(0);
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
         bWa[f] += bFa[f];
-        const double g0 = a[11 + 3 * f], g1 = a[12 + 3 * f], g2 = a[13 + 3 * f];
+        const T g0 = a[11 + 3 * f], g1 = a[12 + 3 * f], g2 = a[13 + 3 * f];
         bg[3 * f] += bFa[f] * sa * dx;
         bg[3 * f + 1] += bFa[f] * sa * dy;
         bg[3 * f + 2] += bFa[f] * sa * dz;
@@ -254,35 +254,35 @@ __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)
         bd[0] += bFa[f] * sa * g0;
         bd[1] += bFa[f] * sa * g1;
         bd[2] += bFa[f] * sa * g2;
-        const double h0 = b[11 + 3 * f], h1 = b[12 + 3 * f], h2 = b[13 + 3 * f];
+        const T h0 = b[11 + 3 * f], h1 = b[12 + 3 * f], h2 = b[13 + 3 * f];
         b_sb -= bFb[f] * ((h0 * dx + h1 * dy) + h2 * dz);
         bd[0] -= bFb[f] * sb * h0;
         bd[1] -= bFb[f] * sb * h1;
         bd[2] -= bFb[f] * sb * h2;
     }
     if (hancock) {
-        const double div = ((double)a[11 + 3] + a[11 + 7]) + a[11 + 11];
-        const double rho = a[6], P = a[7];
-        const double b_div = bFa[0] * hdt * (-rho) + bFa[4] * hdt * (-(double)gam * P);
+        const T div = ((T)a[11 + 3] + a[11 + 7]) + a[11 + 11];
+        const T rho = a[6], P = a[7];
+        const T b_div = bFa[0] * hdt * (-rho) + bFa[4] * hdt * (-(T)gam * P);
         bWa[0] += bFa[0] * hdt * (-div);
         for (int k = 0; k < 3; ++k) {
-            bWa[0] += bFa[1 + k] * hdt * (double)a[11 + 12 + k] / (rho * rho);
-            bg[12 + k] += bFa[1 + k] * hdt * (-1.0 / rho);
+            bWa[0] += bFa[1 + k] * hdt * (T)a[11 + 12 + k] / (rho * rho);
+            bg[12 + k] += bFa[1 + k] * hdt * (T(-1) / rho);
         }
-        bWa[4] += bFa[4] * hdt * (-(double)gam * div);
+        bWa[4] += bFa[4] * hdt * (-(T)gam * div);
         bg[3] += b_div;
         bg[7] += b_div;
         bg[11] += b_div;
     }
     // s_a = Ha / Hs, s_b = Hb / Hs
-    const double Hsd = Hs;
-    double bHa = b_sa * (double)b[3] / (Hsd * Hsd) - b_sb * (double)b[3] / (Hsd * Hsd);
+    const T Hsd = Hs;
+    T bHa = b_sa * (T)b[3] / (Hsd * Hsd) - b_sb * (T)b[3] / (Hsd * Hsd);
     // A = ca B_a d + cb B_b d
-    const double bca = (bA[0] * Bda[0] + bA[1] * Bda[1]) + bA[2] * Bda[2];
-    const double bcb = (bA[0] * Bdb[0] + bA[1] * Bdb[1]) + bA[2] * Bdb[2];
-    const double bBda[3] = {(double)ca * bA[0], (double)ca * bA[1], (double)ca * bA[2]};
-    const double bBdb[3] = {(double)cb * bA[0], (double)cb * bA[1], (double)cb * bA[2]};
-    double bB[6];
+    const T bca = (bA[0] * Bda[0] + bA[1] * Bda[1]) + bA[2] * Bda[2];
+    const T bcb = (bA[0] * Bdb[0] + bA[1] * Bdb[1]) + bA[2] * Bdb[2];
+    const T bBda[3] = {(T)ca * bA[0], (T)ca * bA[1], (T)ca * bA[2]};
+    const T bBdb[3] = {(T)cb * bA[0], (T)cb * bA[1], (T)cb * bA[2]};
+    T bB[6];
     bB[0] = bBda[0] * dx;
     bB[1] = bBda[0] * dy + bBda[1] * dx;
     bB[2] = bBda[0] * dz + bBda[2] * dx;
@@ -296,21 +296,21 @@ __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)
     bd[1] += (Bb[1] * bBdb[0] + Bb[3] * bBdb[1]) + Bb[4] * bBdb[2];
     bd[2] += (Bb[2] * bBdb[0] + Bb[4] * bBdb[1]) + Bb[5] * bBdb[2];
     // ca = knorm_a w(r / Ha) inside a's support, cb likewise
-    double br = 0.0, bka = 0.0;
+    T br = T(0), bka = T(0);
     if (ina) {
         bka = bca * wa;
-        const double bq = bca * (double)a[5] * dkern(qa);
-        br += bq * (double)a[4];
-        bHa -= bq * (double)qa / (double)a[3];
+        const T bq = bca * (T)a[5] * dkern(qa);
+        br += bq * (T)a[4];
+        bHa -= bq * (T)qa / (T)a[3];
     }
-    if (inb) br += bcb * (double)b[5] * dkern(qb) * (double)b[4];
+    if (inb) br += bcb * (T)b[5] * dkern(qb) * (T)b[4];
     // knorm = 8 / (pi H^3 n^2)
-    bHa += bka * (-3.0 * (double)a[5] / (double)a[3]);
-    const double bna = bka * (-2.0 * (double)a[5] / (double)na);
+    bHa += bka * (T(-3) * (T)a[5] / (T)a[3]);
+    const T bna = bka * (-T(2) * (T)a[5] / (T)na);
     if (r > T(0)) {
-        bd[0] += br * dx / (double)r;
-        bd[1] += br * dy / (double)r;
-        bd[2] += br * dz / (double)r;
+        bd[0] += br * dx / (T)r;
+        bd[1] += br * dy / (T)r;
+        bd[2] += br * dz / (T)r;
     }
     // d = x_b - x_a
     adj[AX] -= bd[0];
@@ -331,7 +331,7 @@ __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)
 
 // Adjoint of the flux pass: per particle over its pairs (N_i then R_i).
 template <typename T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
     k_flux_adj(int N, const T* __restrict__ rec, const T* __restrict__ sn, const long long* __restrict__ sid,
                const int* __restrict__ sbox, const unsigned* __restrict__ nbr, const int* __restrict__ ncount,
                const unsigned* __restrict__ rnbr, const int* __restrict__ rcount, KParams p,
@@ -345,11 +345,11 @@ __global__ void __launch_bounds__(128)
     const T gam = (T)p.gamma;
     const bool hancock = p.hancock != 0;
     const T na = sn[i];
-    const double wi[4] = {wgt[4 * (size_t)i], wgt[4 * (size_t)i + 1], wgt[4 * (size_t)i + 2],
-                          wgt[4 * (size_t)i + 3]};
-    double acc[kAdj];
+    const T wi[4] = {(T)wgt[4 * (size_t)i], (T)wgt[4 * (size_t)i + 1], (T)wgt[4 * (size_t)i + 2],
+                     (T)wgt[4 * (size_t)i + 3]};
+    T acc[kAdj];
 #pragma unroll
-    for (int q = 0; q < kAdj; ++q) acc[q] = 0.0;
+    for (int q = 0; q < kAdj; ++q) acc[q] = T(0);
     for (int list = 0; list < 2; ++list) {
         const unsigned* L = list == 0 ? nbr + (size_t)i * p.cap : rnbr + (size_t)i * p.rcap;
         const int cnt = list == 0 ? min(ncount[i], p.cap) : min(rcount[i], p.rcap);
@@ -357,15 +357,15 @@ __global__ void __launch_bounds__(128)
             const int j = (int)L[k];
             T b[kRecord];
             load_rec(rec + (size_t)j * kRecord, b);
-            const double wp[3] = {wi[0] - wgt[4 * (size_t)j], wi[1] - wgt[4 * (size_t)j + 1],
-                                  wi[2] - wgt[4 * (size_t)j + 2]};
-            const double wE = wi[3] - wgt[4 * (size_t)j + 3];
+            const T wp[3] = {wi[0] - (T)wgt[4 * (size_t)j], wi[1] - (T)wgt[4 * (size_t)j + 1],
+                             wi[2] - (T)wgt[4 * (size_t)j + 2]};
+            const T wE = wi[3] - (T)wgt[4 * (size_t)j + 3];
             pair_adjoint(a, b, idi < sid[j], hdt, gam, hancock, na, wp, wE, acc);
         }
     }
     double* o = adj + (size_t)i * kAdj;
 #pragma unroll
-    for (int q = 0; q < kAdj; ++q) o[q] += acc[q];
+    for (int q = 0; q < kAdj; ++q) o[q] += (double)acc[q];
 }
 
 // Caller-order adjoint weights of the rates -> sorted [N][4].
@@ -414,37 +414,36 @@ __global__ void k_update_adj(int N, Sorted<T> s, const double* __restrict__ dpdt
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const unsigned o = s.orig[i];
-    const double dt = dt_use[s.box[i]];
-    const double m = s.m[i], u = s.u[i];
-    const double v[3] = {s.vx[i], s.vy[i], s.vz[i]};
-    const double dp[3] = {dpdt[i], dpdt[(size_t)N + i], dpdt[2 * (size_t)N + i]};
-    const double dE = dEdt[i];
+    const T dt = (T)dt_use[s.box[i]];
+    const T m = s.m[i];
+    const T v[3] = {s.vx[i], s.vy[i], s.vz[i]};
+    const T dp[3] = {(T)dpdt[i], (T)dpdt[(size_t)N + i], (T)dpdt[2 * (size_t)N + i]};
+    const T dE = (T)dEdt[i];
     // forward update in the working precision, for the floor decision
-    T X = s.x[i], Y = s.y[i], Z = s.z[i], VX = s.vx[i], VY = s.vy[i], VZ = s.vz[i], U = s.u[i];
-    update_one(s.m[i], X, Y, Z, VX, VY, VZ, U, dp[0], dp[1], dp[2], dE, dt);
+    T X = s.x[i], Y = s.y[i], Z = s.z[i], VX = v[0], VY = v[1], VZ = v[2], U = s.u[i];
+    update_one(m, X, Y, Z, VX, VY, VZ, U, dpdt[i], dpdt[(size_t)N + i], dpdt[2 * (size_t)N + i],
+               dEdt[i], dt_use[s.box[i]]);
     const bool floored = !(U > T(0));
-    double vn[3];
-    for (int k = 0; k < 3; ++k) vn[k] = v[k] + dt * dp[k] / m;
-    const double xb[3] = {gend.x ? (double)((const T*)gend.x)[o] : 0.0,
-                          gend.y ? (double)((const T*)gend.y)[o] : 0.0,
-                          gend.z ? (double)((const T*)gend.z)[o] : 0.0};
-    const double vb[3] = {gend.vx ? (double)((const T*)gend.vx)[o] : 0.0,
-                          gend.vy ? (double)((const T*)gend.vy)[o] : 0.0,
-                          gend.vz ? (double)((const T*)gend.vz)[o] : 0.0};
-    const double ub = (gend.u && !floored) ? (double)((const T*)gend.u)[o] : 0.0;
+    const T im = T(1) / m;
+    T vn[3];
+    for (int k = 0; k < 3; ++k) vn[k] = v[k] + dt * dp[k] * im;
+    const T xb[3] = {gend.x ? ((const T*)gend.x)[o] : T(0), gend.y ? ((const T*)gend.y)[o] : T(0),
+                     gend.z ? ((const T*)gend.z)[o] : T(0)};
+    const T vb[3] = {gend.vx ? ((const T*)gend.vx)[o] : T(0), gend.vy ? ((const T*)gend.vy)[o] : T(0),
+                     gend.vz ? ((const T*)gend.vz)[o] : T(0)};
+    const T ub = (gend.u && !floored) ? ((const T*)gend.u)[o] : T(0);
     double* a = adj + (size_t)i * kAdj;
-    double mb = -ub * dt * dE / (m * m);
+    T mb = -ub * dt * dE * im * im;
     for (int k = 0; k < 3; ++k) {
-        a[AX + k] += xb[k];
-        a[AV + k] += vb[k] + dt * xb[k] + ub * (v[k] - vn[k]);
-        const double w = vb[k] + 0.5 * dt * xb[k];
-        wgt[4 * (size_t)i + k] = dt / m * (w - ub * vn[k]);
-        mb += -(vn[k] - v[k]) / m * w + ub * vn[k] * (vn[k] - v[k]) / m;
+        a[AX + k] += (double)xb[k];
+        a[AV + k] += (double)(vb[k] + dt * xb[k] + ub * (v[k] - vn[k]));
+        const T w = vb[k] + T(0.5) * dt * xb[k];
+        wgt[4 * (size_t)i + k] = (double)(dt * im * (w - ub * vn[k]));
+        mb += -(vn[k] - v[k]) * im * w + ub * vn[k] * (vn[k] - v[k]) * im;
     }
-    wgt[4 * (size_t)i + 3] = ub * dt / m;
-    a[AU] += ub;
-    a[AM] += mb;
-    (void)u;
+    wgt[4 * (size_t)i + 3] = (double)(ub * dt * im);
+    a[AU] += (double)ub;
+    a[AM] += (double)mb;
 }
 
 // ---------------------------------------------------------- gradients
@@ -459,11 +458,12 @@ __global__ void __launch_bounds__(128)
     k_grad_seeds(int N, Sorted<T> s, const T* __restrict__ rec, const T* __restrict__ ginfo,
                  const int* __restrict__ lim, const unsigned* __restrict__ nbr,
                  const int* __restrict__ ncount, KParams p, double* __restrict__ adj,
-                 double* __restrict__ seeds) {
+                 T* __restrict__ seeds, unsigned long long* __restrict__ lbloom) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     double* a = adj + (size_t)i * kAdj;
-    double* sd = seeds + (size_t)i * kSeed;
+    T* sd = seeds + (size_t)i * kSeed;
+    unsigned long long bloom = 0ull;
     const T* G = ginfo + (size_t)i * kGInfo;
     const T* R = rec + (size_t)i * kRecord;
     const P4<T> me = s.pos[i];
@@ -471,56 +471,59 @@ __global__ void __launch_bounds__(128)
     const T xim1 = xi - T(1), yim1 = yi - T(1), zim1 = zi - T(1);
     const P4<T> pm = s.prim[i];
     const T Wi[5] = {pm.x, pm.y, pm.z, pm.w, s.prim2[i].x};
-    const double Bs[6] = {R[26], R[27], R[28], R[29], R[30], R[31]};
-    double fbi[5] = {0, 0, 0, 0, 0};
-    double xbi[3] = {0, 0, 0};
-    double Hbi = 0.0, nbi = 0.0;
-    double gb[15];
-    double Bb[6];
-    for (int q = 0; q < 6; ++q) Bb[q] = a[AB + q];
-    for (int q = 0; q < kSeed; ++q) sd[q] = 0.0;
-    const double beta = p.beta;
+    const T Bs[6] = {R[26], R[27], R[28], R[29], R[30], R[31]};
+    T fbi[5] = {0, 0, 0, 0, 0};
+    T xbi[3] = {0, 0, 0};
+    T Hbi = T(0.0), nbi = T(0.0);
+    T gb[15];
+    T Bb[6];
+    for (int q = 0; q < 6; ++q) Bb[q] = (T)a[AB + q];
+    for (int q = 28; q < kSeed; ++q) sd[q] = T(0.0);
+    const T beta = p.beta;
     for (int f = 0; f < 5; ++f) {
-        const double al = G[30 + f];
-        const double g[3] = {G[3 * f], G[3 * f + 1], G[3 * f + 2]};
-        const double ghb[3] = {a[AG + 3 * f], a[AG + 3 * f + 1], a[AG + 3 * f + 2]};
+        const T al = G[30 + f];
+        const T g[3] = {G[3 * f], G[3 * f + 1], G[3 * f + 2]};
+        const T ghb[3] = {(T)a[AG + 3 * f], (T)a[AG + 3 * f + 1], (T)a[AG + 3 * f + 2]};
         for (int k = 0; k < 3; ++k) gb[3 * f + k] = al * ghb[k];
-        const double alb = (ghb[0] * g[0] + ghb[1] * g[1]) + ghb[2] * g[2];
+        const T alb = (ghb[0] * g[0] + ghb[1] * g[1]) + ghb[2] * g[2];
         const int j = lim[(size_t)i * 10 + f];
-        if (j >= 0 && alb != 0.0) {
+        if (j >= 0 && alb != T(0.0)) {
             const int k = lim[(size_t)i * 10 + 5 + f];
-            const double D = G[35 + f];
-            const double c1 = alb * beta / D;
-            if (k == i)
+            const T D = G[35 + f];
+            const T c1 = alb * beta / D;
+            if (k == i) {
                 fbi[f] += c1;
-            else
-                sd[21 + 5 * f + 4] = c1;
+            } else {
+                sd[28 + 5 * f + 4] = c1;
+                bloom |= 1ull << (k & 63);
+            }
             fbi[f] -= c1;
-            const double Db = -alb * al / D;
+            bloom |= 1ull << (j & 63);
+            const T Db = -alb * al / D;
             const P4<T> qj = s.pos[j];
-            const double dx = mi_diff(qj.x, xi, xim1), dy = mi_diff(qj.y, yi, yim1),
+            const T dx = mi_diff(qj.x, xi, xim1), dy = mi_diff(qj.y, yi, yim1),
                          dz = mi_diff(qj.z, zi, zim1);
-            const double Hj = qj.w, Hs = (double)Hi + Hj;
-            const double sij = (double)Hi / Hs;
-            const double o[3] = {sij * dx, sij * dy, sij * dz};
+            const T Hj = qj.w, Hs = (T)Hi + Hj;
+            const T sij = (T)Hi / Hs;
+            const T o[3] = {sij * dx, sij * dy, sij * dz};
             for (int kk = 0; kk < 3; ++kk) gb[3 * f + kk] += Db * o[kk];
-            const double ob[3] = {Db * g[0], Db * g[1], Db * g[2]};
-            const double sb = (ob[0] * dx + ob[1] * dy) + ob[2] * dz;
+            const T ob[3] = {Db * g[0], Db * g[1], Db * g[2]};
+            const T sb = (ob[0] * dx + ob[1] * dy) + ob[2] * dz;
             Hbi += sb * Hj / (Hs * Hs);
-            sd[21 + 5 * f + 3] = -sb * (double)Hi / (Hs * Hs);
+            sd[28 + 5 * f + 3] = -sb * (T)Hi / (Hs * Hs);
             for (int kk = 0; kk < 3; ++kk) {
-                sd[21 + 5 * f + kk] = ob[kk] * sij;
+                sd[28 + 5 * f + kk] = ob[kk] * sij;
                 xbi[kk] -= ob[kk] * sij;
             }
         }
     }
     // g = B S
-    const bool singular = Bs[0] == 0.0 && Bs[1] == 0.0 && Bs[2] == 0.0 && Bs[3] == 0.0 &&
-                          Bs[4] == 0.0 && Bs[5] == 0.0;
-    double Sb[15];
+    const bool singular = Bs[0] == T(0.0) && Bs[1] == T(0.0) && Bs[2] == T(0.0) && Bs[3] == T(0.0) &&
+                          Bs[4] == T(0.0) && Bs[5] == T(0.0);
+    T Sb[15];
     for (int f = 0; f < 5; ++f) {
-        const double S0 = G[15 + 3 * f], S1 = G[16 + 3 * f], S2 = G[17 + 3 * f];
-        const double g0 = gb[3 * f], g1 = gb[3 * f + 1], g2 = gb[3 * f + 2];
+        const T S0 = G[15 + 3 * f], S1 = G[16 + 3 * f], S2 = G[17 + 3 * f];
+        const T g0 = gb[3 * f], g1 = gb[3 * f + 1], g2 = gb[3 * f + 2];
         Bb[0] += g0 * S0;
         Bb[1] += g0 * S1 + g1 * S0;
         Bb[2] += g0 * S2 + g2 * S0;
@@ -532,27 +535,32 @@ __global__ void __launch_bounds__(128)
         Sb[3 * f + 2] = Bs[2] * g0 + Bs[4] * g1 + Bs[5] * g2;
     }
     // B = E^-1: Ebar = -B Bbar B (full symmetric matrices)
-    const double Bm[3][3] = {{Bs[0], Bs[1], Bs[2]}, {Bs[1], Bs[3], Bs[4]}, {Bs[2], Bs[4], Bs[5]}};
-    const double Pm[3][3] = {{Bb[0], 0.5 * Bb[1], 0.5 * Bb[2]},
-                             {0.5 * Bb[1], Bb[3], 0.5 * Bb[4]},
-                             {0.5 * Bb[2], 0.5 * Bb[4], Bb[5]}};
-    double T1[3][3], Em[3][3];
+    const T Bm[3][3] = {{Bs[0], Bs[1], Bs[2]}, {Bs[1], Bs[3], Bs[4]}, {Bs[2], Bs[4], Bs[5]}};
+    const T Pm[3][3] = {{Bb[0], T(0.5) * Bb[1], T(0.5) * Bb[2]},
+                             {T(0.5) * Bb[1], Bb[3], T(0.5) * Bb[4]},
+                             {T(0.5) * Bb[2], T(0.5) * Bb[4], Bb[5]}};
+    T T1[3][3], Em[3][3];
     for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c) T1[r][c] = (Pm[r][0] * Bm[0][c] + Pm[r][1] * Bm[1][c]) + Pm[r][2] * Bm[2][c];
     for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c) Em[r][c] = -((Bm[r][0] * T1[0][c] + Bm[r][1] * T1[1][c]) + Bm[r][2] * T1[2][c]);
-    double Eb[6] = {Em[0][0], Em[0][1] + Em[1][0], Em[0][2] + Em[2][0], Em[1][1], Em[1][2] + Em[2][1], Em[2][2]};
+    T Eb[6] = {Em[0][0], Em[0][1] + Em[1][0], Em[0][2] + Em[2][0], Em[1][1], Em[1][2] + Em[2][1], Em[2][2]};
     if (singular) {
-        for (int q = 0; q < 6; ++q) Eb[q] = 0.0;
-        for (int q = 0; q < 15; ++q) Sb[q] = 0.0;
+        for (int q = 0; q < 6; ++q) Eb[q] = T(0.0);
+        for (int q = 0; q < 15; ++q) Sb[q] = T(0.0);
     }
-    for (int q = 0; q < 15; ++q) sd[q] = Sb[q];
-    for (int q = 0; q < 6; ++q) sd[15 + q] = Eb[q];
     // own terms of E = sum psi d d^T and S_f = sum (f_j - f_i) psi d
     const T ni = s.n[i];
     const T iH = T(1) / Hi;
     const T norm = T(8.0 / kPi) * iH * iH * iH / ni;
-    double normb = 0.0;
+    // record read by every j with j in N_i (k_grad_gather)
+    for (int q = 0; q < 15; ++q) sd[q] = Sb[q];
+    for (int q = 0; q < 6; ++q) sd[15 + q] = Eb[q];
+    sd[21] = norm;
+    for (int f = 0; f < 5; ++f) sd[22 + f] = Wi[f];
+    sd[27] = T(0);
+    lbloom[i] = bloom;
+    T normb = T(0.0);
     const int cnt = min(ncount[i], p.cap);
     const unsigned* L = nbr + (size_t)i * p.cap;
     for (int kk = 0; kk < cnt; ++kk) {
@@ -562,19 +570,19 @@ __global__ void __launch_bounds__(128)
         const T r2 = sep2(dxT, dyT, dzT);
         const T r = sqrt(r2);
         const T q = r * iH;
-        const double w = kern_w(q), dw = kern_dw(q);
-        const double psi = (double)(norm * kern_w(q));
-        const double dx = dxT, dy = dyT, dz = dzT;
+        const T w = kern_w(q), dw = kern_dw(q);
+        const T psi = (T)(norm * kern_w(q));
+        const T dx = dxT, dy = dyT, dz = dzT;
         const P4<T> pj = s.prim[j];
-        const double Wj[5] = {pj.x, pj.y, pj.z, pj.w, s.prim2[j].x};
-        double psib = ((Eb[0] * dx * dx + Eb[1] * dx * dy) + (Eb[2] * dx * dz + Eb[3] * dy * dy)) +
+        const T Wj[5] = {pj.x, pj.y, pj.z, pj.w, s.prim2[j].x};
+        T psib = ((Eb[0] * dx * dx + Eb[1] * dx * dy) + (Eb[2] * dx * dz + Eb[3] * dy * dy)) +
                       (Eb[4] * dy * dz + Eb[5] * dz * dz);
-        double db[3] = {psi * (2.0 * Eb[0] * dx + Eb[1] * dy + Eb[2] * dz),
-                        psi * (Eb[1] * dx + 2.0 * Eb[3] * dy + Eb[4] * dz),
-                        psi * (Eb[2] * dx + Eb[4] * dy + 2.0 * Eb[5] * dz)};
+        T db[3] = {psi * (T(2.0) * Eb[0] * dx + Eb[1] * dy + Eb[2] * dz),
+                        psi * (Eb[1] * dx + T(2.0) * Eb[3] * dy + Eb[4] * dz),
+                        psi * (Eb[2] * dx + Eb[4] * dy + T(2.0) * Eb[5] * dz)};
         for (int f = 0; f < 5; ++f) {
-            const double df = Wj[f] - (double)Wi[f];
-            const double t = (Sb[3 * f] * dx + Sb[3 * f + 1] * dy) + Sb[3 * f + 2] * dz;
+            const T df = Wj[f] - (T)Wi[f];
+            const T t = (Sb[3 * f] * dx + Sb[3 * f + 1] * dy) + Sb[3 * f + 2] * dz;
             fbi[f] -= psi * t;
             psib += df * t;
             db[0] += df * psi * Sb[3 * f];
@@ -582,20 +590,20 @@ __global__ void __launch_bounds__(128)
             db[2] += df * psi * Sb[3 * f + 2];
         }
         normb += psib * w;
-        const double qb = psib * (double)norm * dw;
-        Hbi -= qb * (double)q / (double)Hi;
+        const T qb = psib * (T)norm * dw;
+        Hbi -= qb * (T)q / (T)Hi;
         if (r > T(0)) {
-            const double rb = qb / (double)Hi;
-            db[0] += rb * dx / (double)r;
-            db[1] += rb * dy / (double)r;
-            db[2] += rb * dz / (double)r;
+            const T rb = qb / (T)Hi;
+            db[0] += rb * dx / (T)r;
+            db[1] += rb * dy / (T)r;
+            db[2] += rb * dz / (T)r;
         }
         xbi[0] -= db[0];
         xbi[1] -= db[1];
         xbi[2] -= db[2];
     }
-    Hbi += normb * (-3.0 * (double)norm / (double)Hi);
-    nbi += normb * (-(double)norm / (double)ni);
+    Hbi += normb * (-T(3.0) * (T)norm / (T)Hi);
+    nbi += normb * (-(T)norm / (T)ni);
     a[AX] += xbi[0];
     a[AX + 1] += xbi[1];
     a[AX + 2] += xbi[2];
@@ -609,19 +617,50 @@ __global__ void __launch_bounds__(128)
 }
 
 // Gradient-pass terms of particle j in the sums of every i with j in N_i
-// (all such i are in j's pair lists).
+// (all such i are in j's pair lists).  Per candidate i the thread reads i's
+// packed position and its 28-value record (S_bar, E_bar, psi norm, W_i) as
+// 128-bit loads; the limiter rows are read only when i's bloom mask has the
+// bit of j.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float4;
+    static constexpr int per = 4;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+    static constexpr int per = 2;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_record(const T* __restrict__ src, T (&dst)[28]) {
+    using V = typename Vec2<T>::type;
+    constexpr int per = Vec2<T>::per;
+    const V* v = reinterpret_cast<const V*>(src);
+#pragma unroll
+    for (int q = 0; q < 28 / per; ++q) {
+        const V w = __ldg(v + q);
+        const T* e = reinterpret_cast<const T*>(&w);
+#pragma unroll
+        for (int r = 0; r < per; ++r) dst[q * per + r] = e[r];
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128)
     k_grad_gather(int N, Sorted<T> s, const int* __restrict__ lim, const unsigned* __restrict__ nbr,
                   const int* __restrict__ ncount, const unsigned* __restrict__ rnbr,
-                  const int* __restrict__ rcount, KParams p, const double* __restrict__ seeds,
-                  double* __restrict__ adj) {
+                  const int* __restrict__ rcount, KParams p, const T* __restrict__ seeds,
+                  const unsigned long long* __restrict__ lbloom, double* __restrict__ adj) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     const P4<T> mj = s.pos[j];
     const P4<T> pj = s.prim[j];
-    const double Wj[5] = {pj.x, pj.y, pj.z, pj.w, s.prim2[j].x};
-    double fb[5] = {0, 0, 0, 0, 0}, xb[3] = {0, 0, 0}, Hb = 0.0;
+    const T Wj[5] = {pj.x, pj.y, pj.z, pj.w, s.prim2[j].x};
+    const unsigned long long jbit = 1ull << (j & 63);
+    T fb[5] = {0, 0, 0, 0, 0}, xb[3] = {0, 0, 0}, Hb = T(0.0);
     for (int list = 0; list < 2; ++list) {
         const unsigned* Lj = list == 0 ? nbr + (size_t)j * p.cap : rnbr + (size_t)j * p.rcap;
         const int cnt = list == 0 ? min(ncount[j], p.cap) : min(rcount[j], p.rcap);
@@ -630,29 +669,29 @@ __global__ void __launch_bounds__(128)
             const P4<T> mi = s.pos[i];
             const T Hi = mi.w;
             // offset as seen by i (x_j - x_i), exactly as i's gradient pass computed it
-            const T dxT = mi_diff(mj.x, mi.x, mi.x - T(1)), dyT = mi_diff(mj.y, mi.y, mi.y - T(1)),
-                    dzT = mi_diff(mj.z, mi.z, mi.z - T(1));
-            const T r2 = sep2(dxT, dyT, dzT);
+            const T dx = mi_diff(mj.x, mi.x, mi.x - T(1)), dy = mi_diff(mj.y, mi.y, mi.y - T(1)),
+                    dz = mi_diff(mj.z, mi.z, mi.z - T(1));
+            const T r2 = sep2(dx, dy, dz);
             if (!(r2 < Hi * Hi)) continue;  // j is not in N_i
-            const double* sd = seeds + (size_t)i * kSeed;
+            const T* R = seeds + (size_t)i * kSeed;
+            T sd[28];
+            load_record<T>(R, sd);
             const T r = sqrt(r2);
             const T iH = T(1) / Hi;
             const T q = r * iH;
-            const T norm = T(8.0 / kPi) * iH * iH * iH / s.n[i];
-            const double psi = (double)(norm * kern_w(q));
-            const double dw = kern_dw(q);
-            const double dx = dxT, dy = dyT, dz = dzT;
-            const P4<T> pi_ = s.prim[i];
-            const double Wi[5] = {pi_.x, pi_.y, pi_.z, pi_.w, s.prim2[i].x};
-            const double* Eb = sd + 15;
-            double psib = ((Eb[0] * dx * dx + Eb[1] * dx * dy) + (Eb[2] * dx * dz + Eb[3] * dy * dy)) +
-                          (Eb[4] * dy * dz + Eb[5] * dz * dz);
-            double db[3] = {psi * (2.0 * Eb[0] * dx + Eb[1] * dy + Eb[2] * dz),
-                            psi * (Eb[1] * dx + 2.0 * Eb[3] * dy + Eb[4] * dz),
-                            psi * (Eb[2] * dx + Eb[4] * dy + 2.0 * Eb[5] * dz)};
+            const T norm = sd[21];
+            const T psi = (T)(norm * kern_w(q));
+            const T dw = kern_dw(q);
+            const T* Eb = sd + 15;
+            T psib = ((Eb[0] * dx * dx + Eb[1] * dx * dy) + (Eb[2] * dx * dz + Eb[3] * dy * dy)) +
+                     (Eb[4] * dy * dz + Eb[5] * dz * dz);
+            T db[3] = {psi * (T(2.0) * Eb[0] * dx + Eb[1] * dy + Eb[2] * dz),
+                       psi * (Eb[1] * dx + T(2.0) * Eb[3] * dy + Eb[4] * dz),
+                       psi * (Eb[2] * dx + Eb[4] * dy + T(2.0) * Eb[5] * dz)};
+#pragma unroll
             for (int f = 0; f < 5; ++f) {
-                const double df = Wj[f] - Wi[f];
-                const double t = (sd[3 * f] * dx + sd[3 * f + 1] * dy) + sd[3 * f + 2] * dz;
+                const T df = Wj[f] - sd[22 + f];
+                const T t = (sd[3 * f] * dx + sd[3 * f + 1] * dy) + sd[3 * f + 2] * dz;
                 fb[f] += psi * t;
                 psib += df * t;
                 db[0] += df * psi * sd[3 * f];
@@ -660,23 +699,27 @@ __global__ void __launch_bounds__(128)
                 db[2] += df * psi * sd[3 * f + 2];
             }
             if (r > T(0)) {
-                const double rb = psib * (double)norm * dw / (double)Hi;
-                db[0] += rb * dx / (double)r;
-                db[1] += rb * dy / (double)r;
-                db[2] += rb * dz / (double)r;
+                const T rb = psib * norm * dw / Hi;
+                db[0] += rb * dx / r;
+                db[1] += rb * dy / r;
+                db[2] += rb * dz / r;
             }
             xb[0] += db[0];
             xb[1] += db[1];
             xb[2] += db[2];
             // limiter terms where j is i's active neighbour or extreme particle
-            for (int f = 0; f < 5; ++f) {
-                if (lim[(size_t)i * 10 + f] == j) {
-                    xb[0] += sd[21 + 5 * f];
-                    xb[1] += sd[21 + 5 * f + 1];
-                    xb[2] += sd[21 + 5 * f + 2];
-                    Hb += sd[21 + 5 * f + 3];
+            if (__ldg(lbloom + i) & jbit) {
+                const int* li = lim + (size_t)i * 10;
+                for (int f = 0; f < 5; ++f) {
+                    const int ja = li[f];
+                    if (ja == j) {
+                        xb[0] += R[28 + 5 * f];
+                        xb[1] += R[28 + 5 * f + 1];
+                        xb[2] += R[28 + 5 * f + 2];
+                        Hb += R[28 + 5 * f + 3];
+                    }
+                    if (ja >= 0 && li[5 + f] == j) fb[f] += R[28 + 5 * f + 4];
                 }
-                if (lim[(size_t)i * 10 + f] >= 0 && lim[(size_t)i * 10 + 5 + f] == j) fb[f] += sd[21 + 5 * f + 4];
             }
         }
     }
@@ -704,9 +747,9 @@ __global__ void __launch_bounds__(128)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     double* a = adj + (size_t)i * kAdj;
-    const double m = s.m[i], n = s.n[i], u = s.u[i], g1 = p.gamma - 1.0;
-    const double rhob = a[ARHO], Pb = a[AP];
-    const double nb = a[AN] + rhob * m + Pb * g1 * m * u;
+    const T m = s.m[i], n = s.n[i], u = s.u[i], g1 = T(p.gamma) - T(1.0);
+    const T rhob = a[ARHO], Pb = a[AP];
+    const T nb = a[AN] + rhob * m + Pb * g1 * m * u;
     a[AM] += rhob * n + Pb * g1 * n * u;
     a[AU] += Pb * g1 * m * n;
     const P4<T> me = s.pos[i];
@@ -715,28 +758,28 @@ __global__ void __launch_bounds__(128)
     const T iH = T(1) / Hi;
     const int cnt = min(ncount[i], p.cap);
     const unsigned* L = nbr + (size_t)i * p.cap;
-    double dsum = 0.0;
+    T dsum = T(0.0);
     for (int kk = 0; kk < cnt; ++kk) {
         const P4<T> qj = s.pos[L[kk]];
         const T r = sqrt(sep2(mi_diff(qj.x, xi, xim1), mi_diff(qj.y, yi, yim1), mi_diff(qj.z, zi, zim1)));
         const T q = r * iH;
-        dsum += (double)kern_dw(q) * (double)q;
+        dsum += (T)kern_dw(q) * (T)q;
     }
-    const double H = Hi;
-    const double c8 = 8.0 / (kPi * H * H * H);
-    const double dndH = -3.0 * n / H - c8 * dsum / H;
-    const double fH = -(32.0 / 3.0) * dsum / H;
-    const double Hbt = a[AH] + nb * dndH;
-    const double lam = fH != 0.0 ? -Hbt / fH : 0.0;
-    const double kappa = (nb * c8 + lam * 32.0 / 3.0) / H;
+    const T H = Hi;
+    const T c8 = T(8.0) / (T(kPi) * H * H * H);
+    const T dndH = -T(3.0) * n / H - c8 * dsum / H;
+    const T fH = -(T(32.0) / T(3.0)) * dsum / H;
+    const T Hbt = a[AH] + nb * dndH;
+    const T lam = fH != T(0.0) ? -Hbt / fH : T(0.0);
+    const T kappa = (nb * c8 + lam * T(32.0) / T(3.0)) / H;
     kap[i] = kappa;
-    double xb[3] = {0, 0, 0};
+    T xb[3] = {0, 0, 0};
     for (int kk = 0; kk < cnt; ++kk) {
         const P4<T> qj = s.pos[L[kk]];
         const T dx = mi_diff(qj.x, xi, xim1), dy = mi_diff(qj.y, yi, yim1), dz = mi_diff(qj.z, zi, zim1);
         const T r = sqrt(sep2(dx, dy, dz));
         if (!(r > T(0))) continue;
-        const double c = kappa * (double)kern_dw(r * iH) / (double)r;
+        const T c = kappa * (T)kern_dw(r * iH) / (T)r;
         xb[0] -= c * dx;
         xb[1] -= c * dy;
         xb[2] -= c * dz;
@@ -754,7 +797,7 @@ __global__ void __launch_bounds__(128)
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     const P4<T> mj = s.pos[j];
-    double xb[3] = {0, 0, 0};
+    T xb[3] = {0, 0, 0};
     for (int list = 0; list < 2; ++list) {
         const unsigned* Lj = list == 0 ? nbr + (size_t)j * p.cap : rnbr + (size_t)j * p.rcap;
         const int cnt = list == 0 ? min(ncount[j], p.cap) : min(rcount[j], p.rcap);
@@ -767,7 +810,7 @@ __global__ void __launch_bounds__(128)
             if (!(r2 < mi.w * mi.w)) continue;
             const T r = sqrt(r2);
             if (!(r > T(0))) continue;
-            const double c = kap[i] * (double)kern_dw(r * (T(1) / mi.w)) / (double)r;
+            const T c = (T)kap[i] * kern_dw(r * (T(1) / mi.w)) / r;
             xb[0] += c * dx;
             xb[1] += c * dy;
             xb[2] += c * dz;
@@ -810,9 +853,10 @@ cudaError_t run_step_adjoint(Ctx& c, const gz_particles& gend, gz_particles& gst
                                                          c.nbr, c.ncount, c.rnbr, c.rcount, kp, c.dt_use,
                                                          c.wgt, c.adj);
     k_grad_seeds<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, (const T*)c.rec, (const T*)c.ginfo, c.lim,
-                                                           c.nbr, c.ncount, kp, c.adj, c.seeds);
+                                                           c.nbr, c.ncount, kp, c.adj, (T*)c.seeds,
+                                                           c.lbloom);
     k_grad_gather<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, c.lim, c.nbr, c.ncount, c.rnbr, c.rcount,
-                                                            kp, c.seeds, c.adj);
+                                                            kp, (const T*)c.seeds, c.lbloom, c.adj);
     k_dens_seeds<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, c.nbr, c.ncount, kp, c.adj, c.wgt);
     k_dens_gather<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, c.nbr, c.ncount, c.rnbr, c.rcount, kp,
                                                             c.wgt, c.adj);
@@ -825,20 +869,27 @@ template cudaError_t run_step_adjoint<double>(Ctx&, const gz_particles&, gz_part
 cudaError_t ensure_adjoint_scratch(Ctx& c) {
     if (c.adj) return cudaSuccess;
     const size_t Nz = (size_t)c.N;
-    const size_t bytes = sizeof(double) * Nz * (kAdj + 4 + kSeed) + sizeof(int) * Nz * 10 +
-                         (size_t)(c.precision == GZ_FP64 ? 8 : 4) * Nz * kGInfo + 4 * 256;
+    const size_t tsz = c.precision == GZ_FP64 ? 8 : 4;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };  // 256-byte aligned slices
+    const size_t sz[6] = {up(sizeof(double) * Nz * kAdj), up(sizeof(double) * Nz * 4), up(tsz * Nz * kSeed),
+                          up(sizeof(unsigned long long) * Nz), up(sizeof(int) * Nz * 10),
+                          up(tsz * Nz * kGInfo)};
+    size_t bytes = 0;
+    for (size_t b : sz) bytes += b;
     char* base = nullptr;
     cudaError_t e = cudaMalloc((void**)&base, bytes);
     if (e != cudaSuccess) return e;
     c.adj_arena = base;
     c.adj = (double*)base;
-    base += sizeof(double) * Nz * kAdj;
+    base += sz[0];
     c.wgt = (double*)base;
-    base += sizeof(double) * Nz * 4;
-    c.seeds = (double*)base;
-    base += sizeof(double) * Nz * kSeed;
+    base += sz[1];
+    c.seeds = base;
+    base += sz[2];
+    c.lbloom = (unsigned long long*)base;
+    base += sz[3];
     c.lim = (int*)base;
-    base += sizeof(int) * Nz * 10;
+    base += sz[4];
     c.ginfo = base;
     return cudaSuccess;
 }

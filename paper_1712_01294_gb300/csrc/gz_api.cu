@@ -198,8 +198,8 @@ gz_status do_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const void* n, 
 // (neighbour sets, H, gradients, records and rates recomputed, not stored),
 // then the adjoint passes run in reverse order.
 template <typename T>
-gz_status do_step_backward(gz_ctx* ctx, const gz_particles* p, double dt, const gz_particles* gend,
-                           gz_particles* gstart) {
+gz_status do_step_backward(gz_ctx* ctx, const gz_particles* p, double dt, const double* rates,
+                           const gz_particles* gend, gz_particles* gstart) {
     Ctx& c = ctx->c;
     cudaError_t e = ensure_adjoint_scratch(c);
     if (e == cudaSuccess) {
@@ -219,7 +219,7 @@ gz_status do_step_backward(gz_ctx* ctx, const gz_particles* p, double dt, const 
     if (e == cudaSuccess) e = run_dt_set(c, dt);
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_FLUX);
-        e = run_fluxes<T>(c);
+        e = rates ? run_rates_in(c, rates) : run_fluxes<T>(c);
     }
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_UPDATE);
@@ -230,7 +230,8 @@ gz_status do_step_backward(gz_ctx* ctx, const gz_particles* p, double dt, const 
 }
 
 template <typename T>
-gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev) {
+gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev,
+                  double* rates_out) {
     Ctx& c = ctx->c;
     cudaError_t e;
     {
@@ -260,7 +261,7 @@ gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
     }
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_UPDATE);
-        e = run_update<T>(c, *p);
+        e = run_update<T>(c, *p, rates_out);
     }
     c.nbr_valid = 1;
     return cuda_check(ctx, e, "gz_step");
@@ -430,6 +431,8 @@ gz_status gz_destroy(gz_ctx* ctx) {
     for (auto ev : ctx->c.ev_pool) cudaEventDestroy(ev);
     cudaFree(ctx->c.arena);
     if (ctx->c.adj_arena) cudaFree(ctx->c.adj_arena);
+    if (ctx->c.graph_exec) cudaGraphExecDestroy(ctx->c.graph_exec);
+    if (ctx->c.graph) cudaGraphDestroy(ctx->c.graph);
     delete ctx;
     return GZ_OK;
 }
@@ -490,18 +493,77 @@ gz_status gz_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
     if (!ctx) return GZ_E_INVAL;
     if (gz_status s = check_particles(ctx, p, true)) return s;
     if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
-    return GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev),
-                       do_step<double>(ctx, p, dt_fixed, dt_used_dev));
+    return GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev, nullptr),
+                       do_step<double>(ctx, p, dt_fixed, dt_used_dev, nullptr));
 }
 
-gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt,
+gz_status gz_step_rates(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev,
+                        double* rates_out) {
+    if (!ctx) return GZ_E_INVAL;
+    if (gz_status s = check_particles(ctx, p, true)) return s;
+    if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
+    return GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev, rates_out),
+                       do_step<double>(ctx, p, dt_fixed, dt_used_dev, rates_out));
+}
+
+gz_status gz_graph_capture(gz_ctx* ctx, gz_particles* p, int32_t nsteps, double dt_fixed,
+                           double* dt_used_dev) {
+    if (!ctx || nsteps < 1) return GZ_E_INVAL;
+    if (gz_status s = check_particles(ctx, p, true)) return s;
+    Ctx& c = ctx->c;
+    if (!c.stream) return fail(ctx, GZ_E_INVAL, "graph capture needs a created (non-default) stream");
+    if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
+    if (c.graph_exec) cudaGraphExecDestroy(c.graph_exec);
+    if (c.graph) cudaGraphDestroy(c.graph);
+    c.graph_exec = nullptr;
+    c.graph = nullptr;
+    const int prof = c.prof;
+    c.prof = 0;
+    const long long l0 = c.launches;
+    cudaError_t e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        c.prof = prof;
+        return fail(ctx, GZ_E_CUDA, std::string("gz_graph_capture: ") + cudaGetErrorString(e));
+    }
+    gz_status st = GZ_OK;
+    for (int k = 0; k < nsteps && st == GZ_OK; ++k)
+        st = GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev, nullptr),
+                         do_step<double>(ctx, p, dt_fixed, dt_used_dev, nullptr));
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c.stream, &g);
+    c.prof = prof;
+    c.graph_kernels = c.launches - l0;
+    c.launches = l0;
+    if (st != GZ_OK || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st != GZ_OK ? st : fail(ctx, GZ_E_CUDA, std::string("gz_graph_capture: ") + cudaGetErrorString(e2));
+    }
+    e = cudaGraphInstantiate(&c.graph_exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return fail(ctx, GZ_E_CUDA, std::string("gz_graph_capture: ") + cudaGetErrorString(e));
+    }
+    c.graph = g;
+    return GZ_OK;
+}
+
+gz_status gz_graph_launch(gz_ctx* ctx) {
+    if (!ctx) return GZ_E_INVAL;
+    Ctx& c = ctx->c;
+    if (!c.graph_exec) return fail(ctx, GZ_E_INVAL, "no captured graph");
+    c.launches += c.graph_kernels;
+    return cuda_check(ctx, cudaGraphLaunch(c.graph_exec, c.stream), "gz_graph_launch");
+}
+
+gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt, const double* rates,
                            const gz_particles* gbar_end, gz_particles* gbar_start) {
     if (!ctx) return GZ_E_INVAL;
     if (gz_status s = check_particles(ctx, p_start, true)) return s;
     if (!gbar_end || !gbar_start) return fail(ctx, GZ_E_INVAL, "null adjoint set");
     if (!(dt > 0.0) || !isfinite(dt)) return fail(ctx, GZ_E_INVAL, "dt must be finite and > 0");
-    return GZ_DISPATCH(do_step_backward<float>(ctx, p_start, dt, gbar_end, gbar_start),
-                       do_step_backward<double>(ctx, p_start, dt, gbar_end, gbar_start));
+    return GZ_DISPATCH(do_step_backward<float>(ctx, p_start, dt, rates, gbar_end, gbar_start),
+                       do_step_backward<double>(ctx, p_start, dt, rates, gbar_end, gbar_start));
 }
 
 gz_status gz_get_neighbours(gz_ctx* ctx, int32_t* count_out, int64_t* ids_out, int32_t cap) {

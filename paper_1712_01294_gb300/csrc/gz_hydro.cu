@@ -617,11 +617,18 @@ __global__ void __launch_bounds__(kFluxBlock)
 template <typename T>
 __global__ void k_update(int N, Sorted<T> s, const double* __restrict__ dpdt,
                          const double* __restrict__ dEdt, const double* __restrict__ dt_use,
-                         gz_particles out, int* __restrict__ box_hits, DevStatus* st) {
+                         gz_particles out, int* __restrict__ box_hits, DevStatus* st,
+                         double* __restrict__ rates_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const unsigned o = s.orig[i];
     const int b = s.box[i];
+    if (rates_out) {  // the step's conserved-variable rates, caller order
+        rates_out[o] = dpdt[i];
+        rates_out[(size_t)N + o] = dpdt[(size_t)N + i];
+        rates_out[2 * (size_t)N + o] = dpdt[2 * (size_t)N + i];
+        rates_out[3 * (size_t)N + o] = dEdt[i];
+    }
     T x = s.x[i], y = s.y[i], z = s.z[i], vx = s.vx[i], vy = s.vy[i], vz = s.vz[i], u = s.u[i];
     update_one(s.m[i], x, y, z, vx, vy, vz, u, dpdt[i], dpdt[(size_t)N + i],
                dpdt[2 * (size_t)N + i], dEdt[i], dt_use[b]);
@@ -852,14 +859,32 @@ cudaError_t run_fluxes(Ctx& c) {
 }
 
 template <typename T>
-cudaError_t run_update(Ctx& c, gz_particles& p) {
+cudaError_t run_update(Ctx& c, gz_particles& p, double* rates_out) {
     c.launches += 2;
     int* hits = c.box_hits;
     cudaMemsetAsync(hits, 0, sizeof(int) * (size_t)c.nboxes, c.stream);
     k_update<T><<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, sorted_view<T>(c), c.dpdt, c.dEdt,
-                                                         c.dt_use, p, hits, c.status);
+                                                         c.dt_use, p, hits, c.status, rates_out);
     k_ufloor<T><<<c.nboxes, 1024, 0, c.stream>>>(sorted_view<T>(c), c.boxes, hits, p,
                                                   c.params.u_floor_frac);
+    return cudaGetLastError();
+}
+
+// Rates saved by a forward step (caller order) into the sorted rate arrays.
+__global__ void k_rates_in(int N, const unsigned* __restrict__ orig, const double* __restrict__ rates,
+                           double* __restrict__ dpdt, double* __restrict__ dEdt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const unsigned o = orig[i];
+    dpdt[i] = rates[o];
+    dpdt[(size_t)N + i] = rates[(size_t)N + o];
+    dpdt[2 * (size_t)N + i] = rates[2 * (size_t)N + o];
+    dEdt[i] = rates[3 * (size_t)N + o];
+}
+
+cudaError_t run_rates_in(Ctx& c, const double* rates) {
+    c.launches += 1;
+    k_rates_in<<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, c.vals, rates, c.dpdt, c.dEdt);
     return cudaGetLastError();
 }
 
@@ -905,7 +930,7 @@ cudaError_t run_get_neighbours(Ctx& c, int32_t* count_out, int64_t* ids_out, int
     template cudaError_t run_pack_given<T>(Ctx&, const T*, const T*); \
     template cudaError_t run_grad_out<T>(Ctx&, T*, T*);              \
     template cudaError_t run_fluxes<T>(Ctx&);                        \
-    template cudaError_t run_update<T>(Ctx&, gz_particles&);
+    template cudaError_t run_update<T>(Ctx&, gz_particles&, double*);
 GZ_INST(float)
 GZ_INST(double)
 #undef GZ_INST

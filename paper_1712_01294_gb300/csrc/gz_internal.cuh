@@ -15,7 +15,9 @@ namespace gz {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kRecord = 32;  // values per packed particle record (flux pass)
 constexpr int kAdj = 33;     // adjoint values per particle (see gz_adjoint.cu)
-constexpr int kSeed = 46;    // gradient-pass adjoint seeds per particle
+constexpr int kSeed = 56;    // gradient-pass adjoint record per particle (working precision):
+                             // [0,15) S_bar, [15,21) E_bar, 21 psi norm, [22,27) W, 27 pad,
+                             // [28,53) limiter seeds (5 per field), [53,56) pad
 constexpr int kGInfo = 40;   // raw gradients, S sums, limiter factors, active limiter Delta
 
 // Device status word (one per context).
@@ -122,11 +124,16 @@ struct Ctx {
     double prof_ms[GZ_NPASSES];
     long long prof_calls[GZ_NPASSES];
     long long* pairs_dev;  // scratch for gz_pair_count
+    // captured multi-step graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    long long graph_kernels = 0;
     // adjoint scratch, allocated on the first backward call
     void* adj_arena = nullptr;
     double* adj = nullptr;    // [N][kAdj]
     double* wgt = nullptr;    // [N][4] rate adjoints
-    double* seeds = nullptr;  // [N][kSeed]
+    void* seeds = nullptr;    // [N][kSeed] working precision
+    unsigned long long* lbloom = nullptr;  // [N] bit (j & 63) set for each limiter target j
     int* lim = nullptr;       // [N][10] limiter: active neighbour, extreme particle per field
     void* ginfo = nullptr;    // [N][kGInfo] working precision
 };

@@ -38,7 +38,8 @@ cudaError_t run_pack_given(Ctx& c, const T* grad, const T* B);
 template <typename T>
 cudaError_t run_fluxes(Ctx& c);
 template <typename T>
-cudaError_t run_update(Ctx& c, gz_particles& p);
+cudaError_t run_update(Ctx& c, gz_particles& p, double* rates_out = nullptr);
+cudaError_t run_rates_in(Ctx& c, const double* rates);
 template <typename T>
 cudaError_t run_grad_out(Ctx& c, T* grad_out, T* B_out);
 

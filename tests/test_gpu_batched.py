@@ -1,0 +1,79 @@
+"""Batched ensembles, CUDA-graph replay and the cell-grid autotuner (GPU)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1712_01294_gb300 import inputs as I
+
+from gpu_common import cast_state
+
+pytestmark = pytest.mark.gpu
+
+
+def gz():
+    import paper_1712_01294_gb300 as m
+    return m
+
+
+def test_graph_replay_equals_eager_steps():
+    m = gz()
+    p = I.ensemble(12, seed=4)
+    q = cast_state(p, m.GZ_MIXED32)
+    counts = [int(c) for c in p.counts]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        eager = m.to_device(q, m.GZ_MIXED32)
+        ctx = m.Context(counts, m.default_params(), stream=s)
+        for _ in range(6):
+            ctx.step(eager)
+        graphd = m.to_device(q, m.GZ_MIXED32)
+        ctx2 = m.Context(counts, m.default_params(), stream=s)
+        dtu = torch.zeros(len(counts), dtype=torch.float64, device="cuda")
+        ctx2.graph_capture(graphd, 3, 0.0, dtu)
+        # capture executes nothing
+        assert torch.equal(graphd["x"], m.to_device(q, m.GZ_MIXED32)["x"])
+        ctx2.graph_launch()
+        ctx2.graph_launch()
+        torch.cuda.synchronize()
+    assert ctx.status(reset=True)["ok"] and ctx2.status(reset=True)["ok"]
+    for k in ("x", "y", "z", "vx", "vy", "vz", "u", "h"):
+        assert torch.equal(eager[k], graphd[k]), k
+    assert bool((dtu > 0).all())
+
+
+def test_ensemble_boxes_take_their_own_steps():
+    m = gz()
+    p = I.ensemble(8, seed=9)
+    q = cast_state(p, m.GZ_MIXED32)
+    counts = [int(c) for c in p.counts]
+    ctx = m.Context(counts, m.default_params())
+    d = m.to_device(q, m.GZ_MIXED32)
+    dtu = torch.zeros(len(counts), dtype=torch.float64, device="cuda")
+    ctx.step(d, 0.0, dtu)
+    assert ctx.status(reset=True)["ok"]
+    dts = dtu.cpu().numpy()
+    assert np.all(dts > 0) and len(set(dts.tolist())) > 1
+    # each box's step equals the step of a context holding only that box
+    off = np.concatenate([[0], np.cumsum(counts)])
+    for b in (0, 3, 7):
+        qb = cast_state(p.box(b), m.GZ_MIXED32)
+        c1 = m.Context([qb.N], m.default_params())
+        d1 = m.to_device(qb, m.GZ_MIXED32)
+        t1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+        c1.step(d1, 0.0, t1)
+        assert float(t1.cpu()[0]) == dts[b]
+        for k in ("x", "vx", "u", "h"):
+            assert torch.equal(d1[k], d[k][off[b]:off[b + 1]]), (b, k)
+
+
+def test_autotuner_picks_a_measured_factor(tmp_path):
+    m = gz()
+    from paper_1712_01294_gb300 import autotune
+    p = I.turbulence(24, seed=2)
+    q = cast_state(p, m.GZ_MIXED32)
+    best, ms = autotune.tune(q, m.GZ_MIXED32, candidates=(0.8, 1.0, 1.3), steps=1,
+                             cache=str(tmp_path / "tune.json"))
+    assert best in ms and ms[best] == min(ms.values()) and len(ms) == 3
+    best2, ms2 = autotune.tune(q, m.GZ_MIXED32, candidates=(0.8, 1.0, 1.3), steps=1,
+                               cache=str(tmp_path / "tune.json"))
+    assert best2 == best and ms2 == ms  # served from the cache
