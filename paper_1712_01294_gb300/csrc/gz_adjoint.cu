@@ -211,31 +211,29 @@ __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)
     const T nb_dot = (bnh[0] * nh[0] + bnh[1] * nh[1]) + bnh[2] * nh[2];
 #pragma unroll
     for (int k = 0; k < 3; ++k) bA[k] += (bnh[k] - nb_dot * nh[k]) / (T)Am + b_Am * nh[k];
-    // fallback and clamps
+    // fallback and clamps; a bound min / max(W_L, W_R) passes its adjoint to
+    // L on a tie (the rule the derivative oracle's where() takes), so the two
+    // sides of a pair never both claim it
     T bFa[5], bFb[5];
 #pragma unroll
     for (int f = 0; f < 5; ++f) {
+        bFa[f] = T(0);
+        bFb[f] = T(0);
         if (fallback) {
             bWa[f] += bGa[f];
-            bFa[f] = T(0);
-            bFb[f] = T(0);
         } else {
-            bFa[f] = T(0);
-            bFb[f] = T(0);
+            const bool loA = aL ? (Wa[f] <= Wb[f]) : (Wa[f] < Wb[f]);
+            const bool hiA = aL ? (Wa[f] >= Wb[f]) : (Wa[f] > Wb[f]);
             // a's face value
             if (ka[f] == 0)
                 bFa[f] = bGa[f];
-            else if (ka[f] < 0)
-                bWa[f] += (Wa[f] <= Wb[f]) ? bGa[f] : T(0);  // lower bound min(Wa, Wb)
             else
-                bWa[f] += (Wa[f] >= Wb[f]) ? bGa[f] : T(0);  // upper bound max(Wa, Wb)
+                bWa[f] += ((ka[f] < 0) ? loA : hiA) ? bGa[f] : T(0);
             // b's face value (its bounds can be a's values)
             if (kb[f] == 0)
                 bFb[f] = bGb[f];
-            else if (kb[f] < 0)
-                bWa[f] += (Wa[f] <= Wb[f]) ? bGb[f] : T(0);
             else
-                bWa[f] += (Wa[f] >= Wb[f]) ? bGb[f] : T(0);
+                bWa[f] += ((kb[f] < 0) ? loA : hiA) ? bGb[f] : T(0);
         }
     }
     // face states: F_a = W_a + g_a . (s_a d) + hdt D_a ; F_b = W_b + g_b . (s_b (-d)) + hdt D_b

@@ -52,10 +52,20 @@ def assert_all():
     assert not msg, msg
 
 
+def _vz_zero():
+    """Smooth field with vz = 0 exactly: every pair's vz bounds tie (lo = hi =
+    0), so the clamp's adjoint must go to one side only (L, as the oracle's
+    where() does)."""
+    q = I.smooth_turbulence(12, seed=3)
+    q.vz[:] = 0.0
+    return q
+
+
+@pytest.mark.parametrize("case", ["smooth", "vz_tied"])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_flux_adjoint_matches_autograd(prec):
+def test_flux_adjoint_matches_autograd(prec, case):
     m = gz()
-    q = cast_state(I.smooth_turbulence(12, seed=3), prec)
+    q = cast_state(I.smooth_turbulence(12, seed=3) if case == "smooth" else _vz_zero(), prec)
     s = ostate(q)
     prm = O.params()
     Ho, no, _, _ = O.density(s, prm)
