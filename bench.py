@@ -242,7 +242,7 @@ def run_ours(a, world, rank, local):
         adj["forward_ms_per_step"] = round(tmax / a.steps, 4)
         # (forward that saves the checkpoint + backward) / plain forward
         adj["total_over_forward"] = round(
-            (adj["forward_with_rates_ms_per_step"] + adj["backward_ms_per_step"]) / (tmax / a.steps), 3)
+            (adj["forward_with_checkpoint_ms_per_step"] + adj["backward_ms_per_step"]) / (tmax / a.steps), 3)
     return line, p
 
 
@@ -258,37 +258,39 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p):
     ev = lambda: torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         # adjoint of one step (same workload, same precision), dt frozen, in the
-        # configuration MFMStep runs it: the forward saves its rates
-        # (gz_step_rates) and the converged H, the backward recomputes the
-        # density and gradient passes and every pair quantity
+        # configuration MFMStep runs it: the forward fills the step checkpoint
+        # (gz_step_checkpoint: rates and the gradient pass's per-particle
+        # outputs) and returns the converged H; the backward recomputes the
+        # sort, density and pair-list passes and every pair quantity
         rng = np.random.default_rng(0)
         T = d["x"].dtype
         start = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in d.items()}
-        rates = torch.empty(4 * p.N, dtype=torch.float64, device="cuda")
+        level = gz.GZ_CKPT_GRADIENTS
+        ck = ctx.new_checkpoint(level)
         K = max(2, a.steps // 2)
         fwd = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in start.items()}
-        ctx.step(fwd, 0.0, dtu, rates)
+        ctx.step(fwd, 0.0, dtu, ck, level)
         e0, e1 = ev(), ev()
         e0.record(stream)
         for _ in range(K):
-            ctx.step(fwd, 0.0, dtu, rates)
+            ctx.step(fwd, 0.0, dtu, ck, level)
         e1.record(stream)
         torch.cuda.synchronize()
         ms_fwd_ckpt = e0.elapsed_time(e1) / K
         fwd = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in start.items()}
-        ctx.step(fwd, 0.0, dtu, rates)
+        ctx.step(fwd, 0.0, dtu, ck, level)
         dt = float(dtu.item())
-        ckpt = dict(start)
-        ckpt["h"] = fwd["h"]
+        ckstate = dict(start)
+        ckstate["h"] = fwd["h"]
         gend = {k: torch.as_tensor(rng.normal(size=p.N), dtype=T).cuda() for k in
                 ("x", "y", "z", "vx", "vy", "vz", "u")}
         gstart = {k: torch.zeros(p.N, dtype=T, device="cuda") for k in
                   ("x", "y", "z", "vx", "vy", "vz", "u", "m")}
-        ctx.step_backward(ckpt, dt, gend, gstart, rates)
+        ctx.step_backward(ckstate, dt, gend, gstart, ck, level)
         e0, e1 = ev(), ev()
         e0.record(stream)
         for _ in range(K):
-            ctx.step_backward(ckpt, dt, gend, gstart, rates)
+            ctx.step_backward(ckstate, dt, gend, gstart, ck, level)
         e1.record(stream)
         torch.cuda.synchronize()
         ms_bwd = e0.elapsed_time(e1) / K
@@ -301,12 +303,15 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p):
         ms_bwd_full = e0.elapsed_time(e1) / K
         st = ctx.status(reset=True)
         out["adjoint"] = {"backward_ms_per_step": round(ms_bwd, 4),
-                          "forward_with_rates_ms_per_step": round(ms_fwd_ckpt, 4),
+                          "forward_with_checkpoint_ms_per_step": round(ms_fwd_ckpt, 4),
+                          "checkpoint_bytes_per_particle": round(ctx.checkpoint_bytes(level) / p.N, 1),
                           "backward_full_recompute_ms_per_step": round(ms_bwd_full, 4),
                           "steps": K, "status_ok": st["ok"],
                           "what": "gz_step_backward from the MFMStep checkpoint (start state, "
-                                  "converged H, saved rates): density, gradient passes and all "
-                                  "pair quantities recomputed, then the adjoint passes"}
+                                  "converged H, rates and gradient-pass outputs): sort, density, "
+                                  "pair lists and all pair quantities recomputed, then the adjoint "
+                                  "passes"}
+        del ck
         # FP64 path on the same workload
         if prec == gz.GZ_MIXED32:
             c64 = gz.Context([p.N], gz.default_params(precision=gz.GZ_FP64), stream=stream)

@@ -197,28 +197,39 @@ gz_status gz_graph_capture(gz_ctx* ctx, gz_particles* p, int32_t nsteps, double 
                            double* dt_used_dev);
 gz_status gz_graph_launch(gz_ctx* ctx);
 
-/* gz_step that also saves the step's conserved-variable rates for its
- * adjoint: the momentum and total-energy rates of the MFM update (the
- * "Arbitrary (Moving) Meshes" section, the MFM rates of O12).
- * rates_out: device, [4][N] doubles in the caller's particle order, rows
- * dp_x/dt, dp_y/dt, dp_z/dt, dE/dt; caller-owned; NULL makes the call
- * identical to gz_step.  Host synchronisation: none. */
-gz_status gz_step_rates(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev,
-                        double* rates_out);
+/* Step checkpoints for the adjoint (per-step checkpointing of a rollout).
+ * A checkpoint is a caller-owned device buffer, 16-byte aligned, of
+ * gz_checkpoint_bytes(level) bytes, written by gz_step_checkpoint and read
+ * by gz_step_backward of the same step; its layout is private.  Level
+ * GZ_CKPT_RATES keeps the step's conserved-variable rates (the momentum
+ * and total-energy rates of the MFM update, O12; 32 bytes a particle) so the
+ * backward pass skips the flux pass; GZ_CKPT_GRADIENTS also keeps the
+ * gradient pass's per-particle outputs (limited gradients, E^-1, limiter
+ * factors and the indices of the limiting particles; about 330 bytes a
+ * particle in FP32) so the backward pass skips that pass too.  No pair
+ * quantity is ever stored: the backward pass recomputes every one. */
+#define GZ_CKPT_RATES 0
+#define GZ_CKPT_GRADIENTS 1
+gz_status gz_checkpoint_bytes(gz_ctx* ctx, int32_t level, int64_t* bytes);
+
+/* gz_step (same arguments and effect) that also fills the checkpoint ckpt
+ * at the given level.  Host synchronisation: none. */
+gz_status gz_step_checkpoint(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev,
+                             void* ckpt, int32_t level);
 
 /* Adjoint of one gz_step (all of O4-O14 with the step dt held fixed and
  * neighbour sets frozen at their forward values).  p_start is the state the
  * forward step started from (it is not modified); its h is the initial guess
  * of the support radius: passing the h that the forward step returned (the
  * converged H) makes the h-iteration accept it at once, with the same H, lists
- * and sums as the forward.  rates (device, [4][N] as written by gz_step_rates
- * for this step, or NULL) replace the recomputed flux pass; NULL recomputes
- * it.  gbar_end holds dL/d(state after the step) for x, y, z, vx, vy, vz, u
- * (m, h, id ignored; arrays in the working precision); gbar_start receives
+ * and sums as the forward.  ckpt (with its level) is that step's checkpoint
+ * from gz_step_checkpoint, or NULL to recompute everything from p_start.
+ * gbar_end holds dL/d(state after the step) for x, y, z, vx, vy, vz, u (m, h,
+ * id ignored; arrays in the working precision); gbar_start receives
  * dL/d(state before the step) for x, y, z, vx, vy, vz, u and m.  dt is the
  * step the forward used (> 0).  Host synchronisation: none. */
-gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt, const double* rates,
-                           const gz_particles* gbar_end, gz_particles* gbar_start);
+gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt, const void* ckpt,
+                           int32_t level, const gz_particles* gbar_end, gz_particles* gbar_start);
 
 /* Copies the neighbour lists of the last gz_density / gz_step: count_out
  * ([N] int32, device) and, if ids_out is non-NULL, the neighbours' ids into

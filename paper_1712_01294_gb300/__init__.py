@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(HERE, "libgz.so")
 
 GZ_OK, GZ_E_INVAL, GZ_E_NOMEM, GZ_E_CUDA, GZ_E_DEVICE = 0, 1, 2, 3, 4
 GZ_FP64, GZ_MIXED32 = 0, 1
+GZ_CKPT_RATES, GZ_CKPT_GRADIENTS = 0, 1
 STATUS_BITS = {
     "hconv": 1 << 0, "singular": 1 << 1, "nonfinite": 1 << 2, "nbr_overflow": 1 << 3,
     "hlim": 1 << 4, "fallback": 1 << 8, "pstar_neg": 1 << 9, "ufloor": 1 << 10,
@@ -84,8 +85,9 @@ def load_library(build_if_missing: bool = True):
             "gz_hydro_fluxes_backward": (st, [vp, P, vp, vp, vp, d, vp, vp, vp, vp, vp, vp, vp, vp]),
             "gz_graph_capture": (st, [vp, P, i32, d, vp]),
             "gz_graph_launch": (st, [vp]),
-            "gz_step_rates": (st, [vp, P, d, vp, vp]),
-            "gz_step_backward": (st, [vp, P, d, vp, P, P]),
+            "gz_checkpoint_bytes": (st, [vp, i32, vp]),
+            "gz_step_checkpoint": (st, [vp, P, d, vp, vp, i32]),
+            "gz_step_backward": (st, [vp, P, d, vp, i32, P, P]),
             "gz_get_neighbours": (st, [vp, vp, vp, i32]),
             "gz_get_status": (st, [vp, vp, vp, vp, i32]),
             "gz_last_error": (C.c_char_p, [vp]),
@@ -233,23 +235,35 @@ class Context:
             _ptr(out["grad"]), _ptr(out["B"])), "gz_hydro_fluxes_backward")
         return out
 
-    def step(self, p, dt_fixed: float = 0.0, dt_used=None, rates=None):
+    def step(self, p, dt_fixed: float = 0.0, dt_used=None, ckpt=None, level: int = 1):
         """gz_step in place on p; dt_used (device float64 [nboxes]) receives the
-        steps; with rates (device float64 [4, N]) gz_step_rates also saves the
-        step's momentum and energy rates for gz_step_backward."""
+        steps.  With ckpt (a device buffer from new_checkpoint(level)),
+        gz_step_checkpoint also saves what gz_step_backward of this step reads."""
         s = self._parts(p)
-        if rates is None:
+        if ckpt is None:
             self._check(self.lib.gz_step(self.h, C.byref(s), float(dt_fixed), _ptr(dt_used)), "gz_step")
         else:
-            self._rates_ok(rates)
-            self._check(self.lib.gz_step_rates(self.h, C.byref(s), float(dt_fixed), _ptr(dt_used),
-                                               _ptr(rates)), "gz_step_rates")
+            self._ckpt_ok(ckpt, level)
+            self._check(self.lib.gz_step_checkpoint(self.h, C.byref(s), float(dt_fixed), _ptr(dt_used),
+                                                    _ptr(ckpt), int(level)), "gz_step_checkpoint")
         return dt_used
 
-    def _rates_ok(self, rates):
-        if (rates.dtype != self.torch.float64 or not rates.is_cuda or not rates.is_contiguous()
-                or rates.numel() != 4 * self.N):
-            raise ValueError("rates must be a contiguous CUDA float64 tensor of 4*N values")
+    def checkpoint_bytes(self, level: int = 1) -> int:
+        """gz_checkpoint_bytes: size of one step checkpoint at this level."""
+        v = C.c_int64()
+        self._check(self.lib.gz_checkpoint_bytes(self.h, int(level), C.byref(v)), "gz_checkpoint_bytes")
+        return int(v.value)
+
+    def new_checkpoint(self, level: int = 1):
+        """A device buffer for one step checkpoint (GZ_CKPT_RATES = 0 or
+        GZ_CKPT_GRADIENTS = 1)."""
+        return self.empty(self.checkpoint_bytes(level), dtype=self.torch.uint8)
+
+    def _ckpt_ok(self, ckpt, level):
+        if (ckpt.dtype != self.torch.uint8 or not ckpt.is_cuda or not ckpt.is_contiguous()
+                or ckpt.numel() < self.checkpoint_bytes(level) or ckpt.data_ptr() % 16):
+            raise ValueError("ckpt must be a contiguous, 16-byte aligned CUDA uint8 buffer of "
+                             "checkpoint_bytes(level) bytes")
 
     def graph_capture(self, p, nsteps: int, dt_fixed: float = 0.0, dt_used=None):
         """gz_graph_capture: record nsteps steps on p as one CUDA graph (the
@@ -263,14 +277,14 @@ class Context:
         """gz_graph_launch: replay the captured steps."""
         self._check(self.lib.gz_graph_launch(self.h), "gz_graph_launch")
 
-    def step_backward(self, p_start, dt, gbar_end, gbar_start, rates=None):
-        """gz_step_backward: adjoint of one step (see include/gz.h); rates are
-        the forward's saved rates (gz_step_rates) or None to recompute them."""
+    def step_backward(self, p_start, dt, gbar_end, gbar_start, ckpt=None, level: int = 1):
+        """gz_step_backward: adjoint of one step (see include/gz.h); ckpt is the
+        step's checkpoint (from step(..., ckpt=, level=)) or None to recompute."""
         a, b, c = self._parts(p_start), self._grad_parts(gbar_end), self._grad_parts(gbar_start)
-        if rates is not None:
-            self._rates_ok(rates)
-        self._check(self.lib.gz_step_backward(self.h, C.byref(a), float(dt), _ptr(rates), C.byref(b),
-                                              C.byref(c)), "gz_step_backward")
+        if ckpt is not None:
+            self._ckpt_ok(ckpt, level)
+        self._check(self.lib.gz_step_backward(self.h, C.byref(a), float(dt), _ptr(ckpt), int(level),
+                                              C.byref(b), C.byref(c)), "gz_step_backward")
         return gbar_start
 
     def _grad_parts(self, g) -> _Particles:

@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
     k_flux_adj(int N, const T* __restrict__ rec, const T* __restrict__ sn, const long long* __restrict__ sid,
                const int* __restrict__ sbox, const unsigned* __restrict__ nbr, const int* __restrict__ ncount,
                const unsigned* __restrict__ rnbr, const int* __restrict__ rcount, KParams p,
-               const double* __restrict__ dt_use, const double* __restrict__ wgt, double* __restrict__ adj) {
+               const double* __restrict__ dt_use, const T* __restrict__ wgt, double* __restrict__ adj) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     T a[kRecord];
@@ -343,8 +343,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
     const T gam = (T)p.gamma;
     const bool hancock = p.hancock != 0;
     const T na = sn[i];
-    const T wi[4] = {(T)wgt[4 * (size_t)i], (T)wgt[4 * (size_t)i + 1], (T)wgt[4 * (size_t)i + 2],
-                     (T)wgt[4 * (size_t)i + 3]};
+    T wi[4];
+    load4(wgt + 4 * (size_t)i, wi);
     T acc[kAdj];
 #pragma unroll
     for (int q = 0; q < kAdj; ++q) acc[q] = T(0);
@@ -355,9 +355,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
             const int j = (int)L[k];
             T b[kRecord];
             load_rec(rec + (size_t)j * kRecord, b);
-            const T wp[3] = {wi[0] - (T)wgt[4 * (size_t)j], wi[1] - (T)wgt[4 * (size_t)j + 1],
-                             wi[2] - (T)wgt[4 * (size_t)j + 2]};
-            const T wE = wi[3] - (T)wgt[4 * (size_t)j + 3];
+            T wj[4];
+            load4(wgt + 4 * (size_t)j, wj);
+            const T wp[3] = {wi[0] - wj[0], wi[1] - wj[1], wi[2] - wj[2]};
+            const T wE = wi[3] - wj[3];
             pair_adjoint(a, b, idi < sid[j], hdt, gam, hancock, na, wp, wE, acc);
         }
     }
@@ -367,15 +368,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
 }
 
 // Caller-order adjoint weights of the rates -> sorted [N][4].
+template <typename T>
 __global__ void k_gather_wgt(int N, const unsigned* __restrict__ orig, const double* __restrict__ dpbar,
-                             const double* __restrict__ dEbar, double* __restrict__ wgt) {
+                             const double* __restrict__ dEbar, T* __restrict__ wgt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const unsigned o = orig[i];
-    wgt[4 * (size_t)i] = dpbar[o];
-    wgt[4 * (size_t)i + 1] = dpbar[(size_t)N + o];
-    wgt[4 * (size_t)i + 2] = dpbar[2 * (size_t)N + o];
-    wgt[4 * (size_t)i + 3] = dEbar[o];
+    store4(wgt + 4 * (size_t)i, (T)dpbar[o], (T)dpbar[(size_t)N + o], (T)dpbar[2 * (size_t)N + o], (T)dEbar[o]);
 }
 
 // Sorted adjoint records -> caller-order outputs (any pointer may be null).
@@ -408,7 +407,7 @@ __global__ void k_adj_out_flux(int N, const unsigned* __restrict__ orig, const d
 template <typename T>
 __global__ void k_update_adj(int N, Sorted<T> s, const double* __restrict__ dpdt,
                              const double* __restrict__ dEdt, const double* __restrict__ dt_use,
-                             gz_particles gend, double* __restrict__ adj, double* __restrict__ wgt) {
+                             gz_particles gend, double* __restrict__ adj, T* __restrict__ wgt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const unsigned o = s.orig[i];
@@ -432,14 +431,15 @@ __global__ void k_update_adj(int N, Sorted<T> s, const double* __restrict__ dpdt
     const T ub = (gend.u && !floored) ? ((const T*)gend.u)[o] : T(0);
     double* a = adj + (size_t)i * kAdj;
     T mb = -ub * dt * dE * im * im;
+    T wv[3];
     for (int k = 0; k < 3; ++k) {
         a[AX + k] += (double)xb[k];
         a[AV + k] += (double)(vb[k] + dt * xb[k] + ub * (v[k] - vn[k]));
         const T w = vb[k] + T(0.5) * dt * xb[k];
-        wgt[4 * (size_t)i + k] = (double)(dt * im * (w - ub * vn[k]));
+        wv[k] = dt * im * (w - ub * vn[k]);
         mb += -(vn[k] - v[k]) * im * w + ub * vn[k] * (vn[k] - v[k]) * im;
     }
-    wgt[4 * (size_t)i + 3] = (double)(ub * dt * im);
+    store4(wgt + 4 * (size_t)i, wv[0], wv[1], wv[2], ub * dt * im);
     a[AU] += (double)ub;
     a[AM] += (double)mb;
 }
@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(128)
 template <typename T>
 __global__ void __launch_bounds__(128)
     k_dens_seeds(int N, Sorted<T> s, const unsigned* __restrict__ nbr, const int* __restrict__ ncount,
-                 KParams p, double* __restrict__ adj, double* __restrict__ kap) {
+                 KParams p, double* __restrict__ adj, T* __restrict__ kap) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     double* a = adj + (size_t)i * kAdj;
@@ -791,7 +791,7 @@ template <typename T>
 __global__ void __launch_bounds__(128)
     k_dens_gather(int N, Sorted<T> s, const unsigned* __restrict__ nbr, const int* __restrict__ ncount,
                   const unsigned* __restrict__ rnbr, const int* __restrict__ rcount, KParams p,
-                  const double* __restrict__ kap, double* __restrict__ adj) {
+                  const T* __restrict__ kap, double* __restrict__ adj) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     const P4<T> mj = s.pos[j];
@@ -808,7 +808,7 @@ __global__ void __launch_bounds__(128)
             if (!(r2 < mi.w * mi.w)) continue;
             const T r = sqrt(r2);
             if (!(r > T(0))) continue;
-            const T c = (T)kap[i] * kern_dw(r * (T(1) / mi.w)) / r;
+            const T c = kap[i] * kern_dw(r * (T(1) / mi.w)) / r;
             xb[0] += c * dx;
             xb[1] += c * dy;
             xb[2] += c * dz;
@@ -846,18 +846,18 @@ cudaError_t run_step_adjoint(Ctx& c, const gz_particles& gend, gz_particles& gst
     Sorted<T> s = sorted_view<T>(c);
     c.launches += 8;
     cudaMemsetAsync(c.adj, 0, sizeof(double) * (size_t)N * kAdj, c.stream);
-    k_update_adj<T><<<blocks(N, 256), 256, 0, c.stream>>>(N, s, c.dpdt, c.dEdt, c.dt_use, gend, c.adj, c.wgt);
+    k_update_adj<T><<<blocks(N, 256), 256, 0, c.stream>>>(N, s, c.dpdt, c.dEdt, c.dt_use, gend, c.adj, (T*)c.wgt);
     k_flux_adj<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, (const T*)c.rec, (const T*)c.sn, c.sid, c.sbox,
                                                          c.nbr, c.ncount, c.rnbr, c.rcount, kp, c.dt_use,
-                                                         c.wgt, c.adj);
+                                                         (const T*)c.wgt, c.adj);
     k_grad_seeds<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, (const T*)c.rec, (const T*)c.ginfo, c.lim,
                                                            c.nbr, c.ncount, kp, c.adj, (T*)c.seeds,
                                                            c.lbloom);
     k_grad_gather<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, c.lim, c.nbr, c.ncount, c.rnbr, c.rcount,
                                                             kp, (const T*)c.seeds, c.lbloom, c.adj);
-    k_dens_seeds<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, c.nbr, c.ncount, kp, c.adj, c.wgt);
+    k_dens_seeds<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, c.nbr, c.ncount, kp, c.adj, (T*)c.wgt);
     k_dens_gather<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, c.nbr, c.ncount, c.rnbr, c.rcount, kp,
-                                                            c.wgt, c.adj);
+                                                            (const T*)c.wgt, c.adj);
     k_adj_out_step<T><<<blocks(N, 256), 256, 0, c.stream>>>(N, c.vals, c.adj, gstart);
     return cudaGetLastError();
 }
@@ -880,7 +880,7 @@ cudaError_t ensure_adjoint_scratch(Ctx& c) {
     c.adj_arena = base;
     c.adj = (double*)base;
     base += sz[0];
-    c.wgt = (double*)base;
+    c.wgt = base;
     base += sz[1];
     c.seeds = base;
     base += sz[2];
@@ -896,10 +896,10 @@ template <typename T>
 cudaError_t run_flux_adjoint(Ctx& c, const double* dpbar, const double* dEbar) {
     c.launches += 2;
     cudaMemsetAsync(c.adj, 0, sizeof(double) * (size_t)c.N * kAdj, c.stream);
-    k_gather_wgt<<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, c.vals, dpbar, dEbar, c.wgt);
+    k_gather_wgt<T><<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, c.vals, dpbar, dEbar, (T*)c.wgt);
     k_flux_adj<T><<<blocks(c.N, 128), 128, 0, c.stream>>>(c.N, (const T*)c.rec, (const T*)c.sn, c.sid,
                                                            c.sbox, c.nbr, c.ncount, c.rnbr, c.rcount,
-                                                           kparams(c), c.dt_use, c.wgt, c.adj);
+                                                           kparams(c), c.dt_use, (const T*)c.wgt, c.adj);
     return cudaGetLastError();
 }
 

@@ -194,14 +194,72 @@ gz_status do_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const void* n, 
     return cuda_check(ctx, e, "gz_hydro_fluxes_backward");
 }
 
+// Step checkpoint blob (device, caller-owned): [rates: 4 N doubles, caller
+// order] then, at GZ_CKPT_GRADIENTS, the gradient pass's per-particle
+// outputs in sorted order: flux record [N][kRecord], adjoint info
+// [N][kGInfo] (working precision) and limiter indices [N][10]; slices start
+// on 256-byte boundaries.
+struct Ckpt {
+    double* rates = nullptr;
+    void* rec = nullptr;
+    void* ginfo = nullptr;
+    int* lim = nullptr;
+};
+size_t ckpt_slice(size_t b) { return (b + 255) & ~(size_t)255; }
+size_t ckpt_bytes(const Ctx& c, int level) {
+    const size_t N = (size_t)c.N, ts = c.precision == GZ_FP64 ? 8 : 4;
+    size_t b = ckpt_slice(sizeof(double) * 4 * N);
+    if (level >= GZ_CKPT_GRADIENTS)
+        b += ckpt_slice(ts * N * kRecord) + ckpt_slice(ts * N * kGInfo) + ckpt_slice(sizeof(int) * N * 10);
+    return b;
+}
+Ckpt ckpt_view(const Ctx& c, void* base, int level) {
+    Ckpt k;
+    if (!base) return k;
+    const size_t N = (size_t)c.N, ts = c.precision == GZ_FP64 ? 8 : 4;
+    char* p = (char*)base;
+    k.rates = (double*)p;
+    p += ckpt_slice(sizeof(double) * 4 * N);
+    if (level >= GZ_CKPT_GRADIENTS) {
+        k.rec = p;
+        p += ckpt_slice(ts * N * kRecord);
+        k.ginfo = p;
+        p += ckpt_slice(ts * N * kGInfo);
+        k.lim = (int*)p;
+    }
+    return k;
+}
+
+// Points the context's gradient-pass outputs at a checkpoint for one call.
+struct GradOutputs {
+    Ctx& c;
+    void *rec, *ginfo;
+    int* lim;
+    GradOutputs(Ctx& c_, const Ckpt& k) : c(c_), rec(c_.rec), ginfo(c_.ginfo), lim(c_.lim) {
+        if (k.rec) {
+            c.rec = k.rec;
+            c.ginfo = k.ginfo;
+            c.lim = k.lim;
+        }
+    }
+    ~GradOutputs() {
+        c.rec = rec;
+        c.ginfo = ginfo;
+        c.lim = lim;
+    }
+};
+
 // Adjoint of gz_step: the forward passes are re-run from the start state
-// (neighbour sets, H, gradients, records and rates recomputed, not stored),
-// then the adjoint passes run in reverse order.
+// (neighbour sets, H and every pair quantity recomputed, not stored; the
+// rates and, at GZ_CKPT_GRADIENTS, the gradient pass's per-particle outputs
+// come from the step's checkpoint when one is given), then the adjoint
+// passes run in reverse order.
 template <typename T>
-gz_status do_step_backward(gz_ctx* ctx, const gz_particles* p, double dt, const double* rates,
+gz_status do_step_backward(gz_ctx* ctx, const gz_particles* p, double dt, const Ckpt& ck,
                            const gz_particles* gend, gz_particles* gstart) {
     Ctx& c = ctx->c;
     cudaError_t e = ensure_adjoint_scratch(c);
+    GradOutputs outs(c, ck);
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_SORT);
         e = sort_and_bin<T>(c, *p, nullptr);
@@ -212,14 +270,14 @@ gz_status do_step_backward(gz_ctx* ctx, const gz_particles* p, double dt, const 
     }
     if (e == cudaSuccess) e = run_prim<T>(c);
     if (e == cudaSuccess) e = run_reverse<T>(c);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !ck.rec) {
         Pass t(c, GZ_PASS_GRAD);
         e = run_gradients<T>(c, false, true);
     }
     if (e == cudaSuccess) e = run_dt_set(c, dt);
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_FLUX);
-        e = rates ? run_rates_in(c, rates) : run_fluxes<T>(c);
+        e = ck.rates ? run_rates_in(c, ck.rates) : run_fluxes<T>(c);
     }
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_UPDATE);
@@ -230,9 +288,9 @@ gz_status do_step_backward(gz_ctx* ctx, const gz_particles* p, double dt, const 
 }
 
 template <typename T>
-gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev,
-                  double* rates_out) {
+gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev, const Ckpt& ck) {
     Ctx& c = ctx->c;
+    GradOutputs outs(c, ck);
     cudaError_t e;
     {
         Pass t(c, GZ_PASS_SORT);
@@ -252,7 +310,7 @@ gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
     }
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_GRAD);
-        e = run_gradients<T>(c, !(dt_fixed > 0.0));
+        e = run_gradients<T>(c, !(dt_fixed > 0.0), ck.rec != nullptr);
         if (e == cudaSuccess) e = run_dt_finalize(c, dt_fixed, dt_used_dev);
     }
     if (e == cudaSuccess) {
@@ -261,7 +319,7 @@ gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
     }
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_UPDATE);
-        e = run_update<T>(c, *p, rates_out);
+        e = run_update<T>(c, *p, ck.rates);
     }
     c.nbr_valid = 1;
     return cuda_check(ctx, e, "gz_step");
@@ -493,17 +551,26 @@ gz_status gz_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
     if (!ctx) return GZ_E_INVAL;
     if (gz_status s = check_particles(ctx, p, true)) return s;
     if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
-    return GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev, nullptr),
-                       do_step<double>(ctx, p, dt_fixed, dt_used_dev, nullptr));
+    return GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev, Ckpt()),
+                       do_step<double>(ctx, p, dt_fixed, dt_used_dev, Ckpt()));
 }
 
-gz_status gz_step_rates(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev,
-                        double* rates_out) {
+gz_status gz_checkpoint_bytes(gz_ctx* ctx, int32_t level, int64_t* bytes) {
+    if (!ctx || !bytes || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS) return GZ_E_INVAL;
+    *bytes = (int64_t)ckpt_bytes(ctx->c, level);
+    return GZ_OK;
+}
+
+gz_status gz_step_checkpoint(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev,
+                             void* ckpt, int32_t level) {
     if (!ctx) return GZ_E_INVAL;
     if (gz_status s = check_particles(ctx, p, true)) return s;
     if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
-    return GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev, rates_out),
-                       do_step<double>(ctx, p, dt_fixed, dt_used_dev, rates_out));
+    if (!ckpt || ((uintptr_t)ckpt & 15) || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS)
+        return fail(ctx, GZ_E_INVAL, "checkpoint: need a 16-byte aligned buffer and a valid level");
+    const Ckpt ck = ckpt_view(ctx->c, ckpt, level);
+    return GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev, ck),
+                       do_step<double>(ctx, p, dt_fixed, dt_used_dev, ck));
 }
 
 gz_status gz_graph_capture(gz_ctx* ctx, gz_particles* p, int32_t nsteps, double dt_fixed,
@@ -527,8 +594,8 @@ gz_status gz_graph_capture(gz_ctx* ctx, gz_particles* p, int32_t nsteps, double 
     }
     gz_status st = GZ_OK;
     for (int k = 0; k < nsteps && st == GZ_OK; ++k)
-        st = GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev, nullptr),
-                         do_step<double>(ctx, p, dt_fixed, dt_used_dev, nullptr));
+        st = GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev, Ckpt()),
+                         do_step<double>(ctx, p, dt_fixed, dt_used_dev, Ckpt()));
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c.stream, &g);
     c.prof = prof;
@@ -556,14 +623,17 @@ gz_status gz_graph_launch(gz_ctx* ctx) {
     return cuda_check(ctx, cudaGraphLaunch(c.graph_exec, c.stream), "gz_graph_launch");
 }
 
-gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt, const double* rates,
-                           const gz_particles* gbar_end, gz_particles* gbar_start) {
+gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt, const void* ckpt,
+                           int32_t level, const gz_particles* gbar_end, gz_particles* gbar_start) {
     if (!ctx) return GZ_E_INVAL;
     if (gz_status s = check_particles(ctx, p_start, true)) return s;
     if (!gbar_end || !gbar_start) return fail(ctx, GZ_E_INVAL, "null adjoint set");
     if (!(dt > 0.0) || !isfinite(dt)) return fail(ctx, GZ_E_INVAL, "dt must be finite and > 0");
-    return GZ_DISPATCH(do_step_backward<float>(ctx, p_start, dt, rates, gbar_end, gbar_start),
-                       do_step_backward<double>(ctx, p_start, dt, rates, gbar_end, gbar_start));
+    if (ckpt && (((uintptr_t)ckpt & 15) || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS))
+        return fail(ctx, GZ_E_INVAL, "checkpoint: need a 16-byte aligned buffer and a valid level");
+    const Ckpt ck = ckpt_view(ctx->c, const_cast<void*>(ckpt), level);
+    return GZ_DISPATCH(do_step_backward<float>(ctx, p_start, dt, ck, gbar_end, gbar_start),
+                       do_step_backward<double>(ctx, p_start, dt, ck, gbar_end, gbar_start));
 }
 
 gz_status gz_get_neighbours(gz_ctx* ctx, int32_t* count_out, int64_t* ids_out, int32_t cap) {

@@ -101,6 +101,30 @@ __device__ __forceinline__ void face_state(const T (&a)[kRecord], T s, T dx, T d
     }
 }
 
+// Four values to / from 16-byte-aligned memory.
+__device__ __forceinline__ void store4(float* dst, float a, float b, float c, float d) {
+    *reinterpret_cast<float4*>(dst) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void store4(double* dst, double a, double b, double c, double d) {
+    reinterpret_cast<double2*>(dst)[0] = make_double2(a, b);
+    reinterpret_cast<double2*>(dst)[1] = make_double2(c, d);
+}
+__device__ __forceinline__ void load4(const float* src, float (&v)[4]) {
+    const float4 w = __ldg(reinterpret_cast<const float4*>(src));
+    v[0] = w.x;
+    v[1] = w.y;
+    v[2] = w.z;
+    v[3] = w.w;
+}
+__device__ __forceinline__ void load4(const double* src, double (&v)[4]) {
+    const double2 w0 = __ldg(reinterpret_cast<const double2*>(src));
+    const double2 w1 = __ldg(reinterpret_cast<const double2*>(src) + 1);
+    v[0] = w0.x;
+    v[1] = w0.y;
+    v[2] = w1.x;
+    v[3] = w1.y;
+}
+
 // Contribution of the pair (a, b) to particle a's rates: dp (3) and dE.
 // Returns false when the face area vanishes.  flags: 1 fallback, 2 P* < 0.
 template <typename T>

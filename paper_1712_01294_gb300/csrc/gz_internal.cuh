@@ -131,7 +131,7 @@ struct Ctx {
     // adjoint scratch, allocated on the first backward call
     void* adj_arena = nullptr;
     double* adj = nullptr;    // [N][kAdj]
-    double* wgt = nullptr;    // [N][4] rate adjoints
+    void* wgt = nullptr;      // [N][4] rate adjoints (working precision); then kappa [N]
     void* seeds = nullptr;    // [N][kSeed] working precision
     unsigned long long* lbloom = nullptr;  // [N] bit (j & 63) set for each limiter target j
     int* lim = nullptr;       // [N][10] limiter: active neighbour, extreme particle per field

@@ -161,37 +161,46 @@ def test_step_adjoint_matches_autograd(prec):
     assert_all()
 
 
+@pytest.mark.parametrize("level", [0, 1])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_saved_rates_and_converged_h_give_the_same_adjoint(prec):
-    """gz_step_backward from the checkpoint MFMStep keeps (saved rates, the
-    converged H as the initial guess) equals the full recompute bit for bit:
-    the h-iteration accepts the converged H at once and the saved rates are the
-    ones the recomputed flux pass would produce."""
+def test_checkpointed_backward_equals_full_recompute(prec, level):
+    """gz_step_backward from a step checkpoint (saved rates, and at level 1
+    the gradient pass's outputs) with the converged H as the initial guess
+    equals the full recompute from the start state bit for bit: the
+    h-iteration accepts the converged H at once and the saved values are the
+    ones the recomputed passes would produce."""
     m = gz()
     q = cast_state(I.smooth_turbulence(12, seed=5), prec)
     ctx = m.Context([q.N], m.default_params(precision=prec))
     start = device(q, prec)
     d = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in start.items()}
-    rates = torch.empty(4 * q.N, dtype=torch.float64, device="cuda")
+    ck = ctx.new_checkpoint(level)
+    assert ck.numel() == ctx.checkpoint_bytes(level)
+    assert ctx.checkpoint_bytes(1) > ctx.checkpoint_bytes(0) >= 32 * q.N
     dtu = torch.zeros(1, dtype=torch.float64, device="cuda")
-    ctx.step(d, 0.0, dtu, rates)
+    ctx.step(d, 0.0, dtu, ck, level)
     dt = float(dtu.item())
+    # the checkpointing step advances the state exactly like gz_step
+    d2 = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in start.items()}
+    ctx.step(d2, dt)
+    for k in ("x", "y", "z", "vx", "vy", "vz", "u", "h"):
+        assert torch.equal(d[k], d2[k]), k
     T = d["x"].dtype
     rng = np.random.default_rng(11)
     gend = {k: torch.as_tensor(rng.normal(size=q.N), dtype=T).cuda() for k in OUTK}
     g_full = {k: torch.zeros(q.N, dtype=T, device="cuda") for k in KEYS}
     g_ckpt = {k: torch.zeros(q.N, dtype=T, device="cuda") for k in KEYS}
     ctx.step_backward(start, dt, gend, g_full)
-    ck = dict(start)
-    ck["h"] = d["h"].clone()
-    ctx.step_backward(ck, dt, gend, g_ckpt, rates)
+    st = dict(start)
+    st["h"] = d["h"].clone()
+    ctx.step_backward(st, dt, gend, g_ckpt, ck, level)
     st_ = ctx.status(reset=True)
     assert st_["ok"], st_
     for k in KEYS:
         assert torch.equal(g_full[k], g_ckpt[k]), k
     # saved momentum rates are pairwise antisymmetric: they sum to round-off
     # (FP32 pair terms are summed in FP32 in groups of 8 before the FP64 flush)
-    r = rates.view(4, q.N).cpu().numpy()
+    r = ck[:32 * q.N].view(torch.float64).view(4, q.N).cpu().numpy()
     for k in range(3):
         assert abs(r[k].sum()) <= (1e-12 if prec == 0 else 1e-6) * np.abs(r[k]).sum(), k
 
