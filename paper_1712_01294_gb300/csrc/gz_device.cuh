@@ -58,25 +58,24 @@ __device__ __forceinline__ void invert_sym(const A E[6], A B[6], A& det, A& kap)
 }
 
 // ---------------------------------------------------------- O10-O12
+// A flux record is one 128-byte line (FP32) or two (FP64), read with 32-byte
+// vector loads (sm_100+ ld.global.v8.f32 / v4.f64): a warp gathering 32
+// records from scattered lines then moves whole sectors per L1 wavefront
+// instead of half sectors.  Records start on 128-byte boundaries.
 __device__ __forceinline__ void load_rec(const float* __restrict__ p, float (&v)[kRecord]) {
-    const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
-    for (int k = 0; k < kRecord / 4; ++k) {
-        const float4 t = __ldg(q + k);
-        v[4 * k] = t.x;
-        v[4 * k + 1] = t.y;
-        v[4 * k + 2] = t.z;
-        v[4 * k + 3] = t.w;
-    }
+    for (int k = 0; k < kRecord / 8; ++k)
+        asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=f"(v[8 * k]), "=f"(v[8 * k + 1]), "=f"(v[8 * k + 2]), "=f"(v[8 * k + 3]), "=f"(v[8 * k + 4]),
+              "=f"(v[8 * k + 5]), "=f"(v[8 * k + 6]), "=f"(v[8 * k + 7])
+            : "l"(p + 8 * k));
 }
 __device__ __forceinline__ void load_rec(const double* __restrict__ p, double (&v)[kRecord]) {
-    const double2* q = reinterpret_cast<const double2*>(p);
 #pragma unroll
-    for (int k = 0; k < kRecord / 2; ++k) {
-        const double2 t = __ldg(q + k);
-        v[2 * k] = t.x;
-        v[2 * k + 1] = t.y;
-    }
+    for (int k = 0; k < kRecord / 4; ++k)
+        asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+            : "=d"(v[4 * k]), "=d"(v[4 * k + 1]), "=d"(v[4 * k + 2]), "=d"(v[4 * k + 3])
+            : "l"(p + 4 * k));
 }
 
 // Face state of particle a toward the face at a + s o (o = offset to the

@@ -25,9 +25,13 @@ inline int blocks(int n, int t) { return (n + t - 1) / t; }
 // than kDensCache candidates falls back to scanning the cells at every
 // evaluation.  The neighbour list of the returned H is written at the end.
 constexpr int kDensBlock = 64;
-constexpr int kDensCache = 48;
+// Cache entries per thread: 40 (the largest count within 1.05 H seen on the
+// workloads with N_ngb = 32) for boxes of 32^3 particles or more, where the
+// smaller cache buys occupancy; 48 for smaller boxes, whose strong contrasts
+// (blasts in a few thousand particles) overflow 40 more often.
+constexpr int kDensCacheLarge = 40, kDensCacheSmall = 48;
 
-template <typename T>
+template <typename T, int kDensCache>
 __global__ void __launch_bounds__(kDensBlock)
     k_density(int N, Sorted<T> s, Grid g, KParams p, unsigned* __restrict__ nbr,
               int* __restrict__ ncount, int* __restrict__ iters, DevStatus* st) {
@@ -268,7 +272,7 @@ __global__ void k_prim(int N, Sorted<T> s, KParams p, DevStatus* st) {
 // Neighbours are read four at a time (one 16-byte load of indices, then the
 // packed records of all four) so their loads are in flight together.
 template <typename T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
     k_gradients(int N, Sorted<T> s, const unsigned* __restrict__ nbr, const int* __restrict__ ncount,
                 const unsigned* __restrict__ rnbr, const int* __restrict__ rcount, KParams p,
                 T* __restrict__ rec, double* __restrict__ dti, unsigned long long* __restrict__ dtmin,
@@ -809,8 +813,14 @@ static Grid grid_of(const Ctx& c) {
 template <typename T>
 cudaError_t run_density(Ctx& c) {
     c.launches += 1;
-    k_density<T><<<blocks(c.N, kDensBlock), kDensBlock, 0, c.stream>>>(
-        c.N, sorted_view<T>(c), grid_of(c), kparams(c), c.nbr, c.ncount, c.iters, c.status);
+    int min_count = c.N;
+    for (const BoxInfo& b : c.hboxes) min_count = std::min(min_count, b.count);
+    if (min_count >= 32 * 32 * 32)
+        k_density<T, kDensCacheLarge><<<blocks(c.N, kDensBlock), kDensBlock, 0, c.stream>>>(
+            c.N, sorted_view<T>(c), grid_of(c), kparams(c), c.nbr, c.ncount, c.iters, c.status);
+    else
+        k_density<T, kDensCacheSmall><<<blocks(c.N, kDensBlock), kDensBlock, 0, c.stream>>>(
+            c.N, sorted_view<T>(c), grid_of(c), kparams(c), c.nbr, c.ncount, c.iters, c.status);
     return cudaGetLastError();
 }
 
