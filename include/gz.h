@@ -198,7 +198,7 @@ gz_status gz_graph_capture(gz_ctx* ctx, gz_particles* p, int32_t nsteps, double 
 gz_status gz_graph_launch(gz_ctx* ctx);
 
 /* Step checkpoints for the adjoint (per-step checkpointing of a rollout).
- * A checkpoint is a caller-owned device buffer, 16-byte aligned, of
+ * A checkpoint is a caller-owned device buffer, 256-byte aligned, of
  * gz_checkpoint_bytes(level) bytes, written by gz_step_checkpoint and read
  * by gz_step_backward of the same step; its layout is private.  Level
  * GZ_CKPT_RATES keeps the step's conserved-variable rates (the momentum

@@ -261,8 +261,8 @@ class Context:
 
     def _ckpt_ok(self, ckpt, level):
         if (ckpt.dtype != self.torch.uint8 or not ckpt.is_cuda or not ckpt.is_contiguous()
-                or ckpt.numel() < self.checkpoint_bytes(level) or ckpt.data_ptr() % 16):
-            raise ValueError("ckpt must be a contiguous, 16-byte aligned CUDA uint8 buffer of "
+                or ckpt.numel() < self.checkpoint_bytes(level) or ckpt.data_ptr() % 256):
+            raise ValueError("ckpt must be a contiguous, 256-byte aligned CUDA uint8 buffer of "
                              "checkpoint_bytes(level) bytes")
 
     def graph_capture(self, p, nsteps: int, dt_fixed: float = 0.0, dt_used=None):

@@ -9,7 +9,7 @@
 // visits i's pairs and adds only the terms that belong to i, so there are no
 // atomics and the result is deterministic.
 //
-// Adjoint record per particle (double, sorted order), kAdj values:
+// Adjoint record per particle (working precision, sorted order), kAdj values:
 //   0-2 x   3-5 v   6 u   7 m   8 H   9 n   10 rho   11 P   12-26 g (limited)
 //   27-32 B (xx xy xz yy yz zz)
 #include <algorithm>
@@ -34,10 +34,12 @@ __device__ __forceinline__ T dkern(T q) {
 // Adjoint of particle a's share of the pair (a, b).  wp = dpbar_a - dpbar_b
 // and wE = dEbar_a - dEbar_b weight the pair's rate contributions; adj
 // receives dJ/d(a's inputs).  Re-evaluates the forward exactly as
-// pair_rates does so every branch matches.
+// pair_rates does so every branch matches.  inv_na = 1/n_a and irho =
+// 1/rho_a are the particle's own reciprocals; every division of the reverse
+// sweep is a product with a reciprocal (pdiv: hardware reciprocal in FP32).
 template <typename T>
 __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)[kRecord], bool aL,
-                                             T hdt, T gam, bool hancock, T na, const T* wp,
+                                             T hdt, T gam, bool hancock, T inv_na, T irho, const T* wp,
                                              T wE, T* adj) {
     // ---- forward (same operations as pair_rates)
     const T dx = mi_diff(b[0], a[0], a[0] - T(1));
@@ -135,8 +137,8 @@ __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)
     T b_uL = -b_psr * (T)rL * aLv;
     T b_PR = T(0), b_rR = T(0), b_uR = T(0), b_aR = T(0);
     // ss = num / den
-    const T b_num = b_ss / (T)den;
-    const T b_den = -b_ss * (T)ss / (T)den;
+    const T b_num = b_ss * pdiv(T(1), den);
+    const T b_den = -b_num * ss;
     b_PR += b_num;
     b_PL -= b_num;
     b_rL += b_num * (T)uL * aLv;
@@ -170,12 +172,14 @@ __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)
     }
     // c = sqrt(gamma P / rho)
     if (cL > T(0)) {
-        b_PL += b_cL * (T)gam / (T(2) * (T)cL * (T)rL);
-        b_rL -= b_cL * (T)cL / (T(2) * (T)rL);
+        const T h = pdiv(T(0.5), rL);
+        b_PL += b_cL * gam * pdiv(h, cL);
+        b_rL -= b_cL * cL * h;
     }
     if (cR > T(0)) {
-        b_PR += b_cR * (T)gam / (T(2) * (T)cR * (T)rR);
-        b_rR -= b_cR * (T)cR / (T(2) * (T)rR);
+        const T h = pdiv(T(0.5), rR);
+        b_PR += b_cR * gam * pdiv(h, cR);
+        b_rR -= b_cR * cR * h;
     }
     T bFL[5] = {b_rL, T(0), T(0), T(0), b_PL};
     T bFR[5] = {b_rR, T(0), T(0), T(0), b_PR};
@@ -210,7 +214,7 @@ __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)
     T bnh[3] = {sg * bn[0], sg * bn[1], sg * bn[2]};
     const T nb_dot = (bnh[0] * nh[0] + bnh[1] * nh[1]) + bnh[2] * nh[2];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) bA[k] += (bnh[k] - nb_dot * nh[k]) / (T)Am + b_Am * nh[k];
+    for (int k = 0; k < 3; ++k) bA[k] += (bnh[k] - nb_dot * nh[k]) * iA + b_Am * nh[k];
     // fallback and clamps; a bound min / max(W_L, W_R) passes its adjoint to
     // L on a tie (the rule the derivative oracle's where() takes), so the two
     // sides of a pair never both claim it
@@ -264,8 +268,8 @@ __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)
         const T b_div = bFa[0] * hdt * (-rho) + bFa[4] * hdt * (-(T)gam * P);
         bWa[0] += bFa[0] * hdt * (-div);
         for (int k = 0; k < 3; ++k) {
-            bWa[0] += bFa[1 + k] * hdt * (T)a[11 + 12 + k] / (rho * rho);
-            bg[12 + k] += bFa[1 + k] * hdt * (T(-1) / rho);
+            bWa[0] += bFa[1 + k] * hdt * a[11 + 12 + k] * irho * irho;
+            bg[12 + k] -= bFa[1 + k] * hdt * irho;
         }
         bWa[4] += bFa[4] * hdt * (-(T)gam * div);
         bg[3] += b_div;
@@ -274,7 +278,7 @@ __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)
     }
     // s_a = Ha / Hs, s_b = Hb / Hs
     const T Hsd = Hs;
-    T bHa = b_sa * (T)b[3] / (Hsd * Hsd) - b_sb * (T)b[3] / (Hsd * Hsd);
+    T bHa = (b_sa - b_sb) * b[3] * pdiv(T(1), Hsd * Hsd);
     // A = ca B_a d + cb B_b d
     const T bca = (bA[0] * Bda[0] + bA[1] * Bda[1]) + bA[2] * Bda[2];
     const T bcb = (bA[0] * Bdb[0] + bA[1] * Bdb[1]) + bA[2] * Bdb[2];
@@ -299,16 +303,17 @@ __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)
         bka = bca * wa;
         const T bq = bca * (T)a[5] * dkern(qa);
         br += bq * (T)a[4];
-        bHa -= bq * (T)qa / (T)a[3];
+        bHa -= bq * qa * a[4];
     }
     if (inb) br += bcb * (T)b[5] * dkern(qb) * (T)b[4];
     // knorm = 8 / (pi H^3 n^2)
-    bHa += bka * (T(-3) * (T)a[5] / (T)a[3]);
-    const T bna = bka * (-T(2) * (T)a[5] / (T)na);
+    bHa += bka * (T(-3) * a[5] * a[4]);
+    const T bna = bka * (-T(2) * a[5] * inv_na);
     if (r > T(0)) {
-        bd[0] += br * dx / (T)r;
-        bd[1] += br * dy / (T)r;
-        bd[2] += br * dz / (T)r;
+        const T bri = br * pdiv(T(1), r);
+        bd[0] += bri * dx;
+        bd[1] += bri * dy;
+        bd[2] += bri * dz;
     }
     // d = x_b - x_a
     adj[AX] -= bd[0];
@@ -333,7 +338,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
     k_flux_adj(int N, const T* __restrict__ rec, const T* __restrict__ sn, const long long* __restrict__ sid,
                const int* __restrict__ sbox, const unsigned* __restrict__ nbr, const int* __restrict__ ncount,
                const unsigned* __restrict__ rnbr, const int* __restrict__ rcount, KParams p,
-               const double* __restrict__ dt_use, const T* __restrict__ wgt, double* __restrict__ adj) {
+               const double* __restrict__ dt_use, const T* __restrict__ wgt, T* __restrict__ adj) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     T a[kRecord];
@@ -342,7 +347,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
     const T hdt = (T)(0.5 * dt_use[sbox[i]]);
     const T gam = (T)p.gamma;
     const bool hancock = p.hancock != 0;
-    const T na = sn[i];
+    const T inv_na = pdiv(T(1), sn[i]), irho = pdiv(T(1), a[6]);
     T wi[4];
     load4(wgt + 4 * (size_t)i, wi);
     T acc[kAdj];
@@ -359,12 +364,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
             load4(wgt + 4 * (size_t)j, wj);
             const T wp[3] = {wi[0] - wj[0], wi[1] - wj[1], wi[2] - wj[2]};
             const T wE = wi[3] - wj[3];
-            pair_adjoint(a, b, idi < sid[j], hdt, gam, hancock, na, wp, wE, acc);
+            pair_adjoint(a, b, idi < sid[j], hdt, gam, hancock, inv_na, irho, wp, wE, acc);
         }
     }
-    double* o = adj + (size_t)i * kAdj;
+    T* o = adj + (size_t)i * kAdj;
 #pragma unroll
-    for (int q = 0; q < kAdj; ++q) o[q] += (double)acc[q];
+    for (int q = 0; q < kAdj; ++q) o[q] += acc[q];
 }
 
 // Caller-order adjoint weights of the rates -> sorted [N][4].
@@ -378,14 +383,15 @@ __global__ void k_gather_wgt(int N, const unsigned* __restrict__ orig, const dou
 }
 
 // Sorted adjoint records -> caller-order outputs (any pointer may be null).
-__global__ void k_adj_out_flux(int N, const unsigned* __restrict__ orig, const double* __restrict__ adj,
+template <typename T>
+__global__ void k_adj_out_flux(int N, const unsigned* __restrict__ orig, const T* __restrict__ adj,
                                double* __restrict__ xbar, double* __restrict__ hbar,
                                double* __restrict__ nbar, double* __restrict__ Wbar,
                                double* __restrict__ gbar, double* __restrict__ Bbar) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const unsigned o = orig[i];
-    const double* a = adj + (size_t)i * kAdj;
+    const T* a = adj + (size_t)i * kAdj;
     if (xbar)
         for (int k = 0; k < 3; ++k) xbar[(size_t)k * N + o] = a[AX + k];
     if (hbar) hbar[o] = a[AH];
@@ -407,7 +413,7 @@ __global__ void k_adj_out_flux(int N, const unsigned* __restrict__ orig, const d
 template <typename T>
 __global__ void k_update_adj(int N, Sorted<T> s, const double* __restrict__ dpdt,
                              const double* __restrict__ dEdt, const double* __restrict__ dt_use,
-                             gz_particles gend, double* __restrict__ adj, T* __restrict__ wgt) {
+                             gz_particles gend, T* __restrict__ adj, T* __restrict__ wgt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const unsigned o = s.orig[i];
@@ -429,19 +435,19 @@ __global__ void k_update_adj(int N, Sorted<T> s, const double* __restrict__ dpdt
     const T vb[3] = {gend.vx ? ((const T*)gend.vx)[o] : T(0), gend.vy ? ((const T*)gend.vy)[o] : T(0),
                      gend.vz ? ((const T*)gend.vz)[o] : T(0)};
     const T ub = (gend.u && !floored) ? ((const T*)gend.u)[o] : T(0);
-    double* a = adj + (size_t)i * kAdj;
+    T* a = adj + (size_t)i * kAdj;
     T mb = -ub * dt * dE * im * im;
     T wv[3];
     for (int k = 0; k < 3; ++k) {
-        a[AX + k] += (double)xb[k];
-        a[AV + k] += (double)(vb[k] + dt * xb[k] + ub * (v[k] - vn[k]));
+        a[AX + k] += xb[k];
+        a[AV + k] += vb[k] + dt * xb[k] + ub * (v[k] - vn[k]);
         const T w = vb[k] + T(0.5) * dt * xb[k];
         wv[k] = dt * im * (w - ub * vn[k]);
         mb += -(vn[k] - v[k]) * im * w + ub * vn[k] * (vn[k] - v[k]) * im;
     }
     store4(wgt + 4 * (size_t)i, wv[0], wv[1], wv[2], ub * dt * im);
-    a[AU] += (double)ub;
-    a[AM] += (double)mb;
+    a[AU] += ub;
+    a[AM] += mb;
 }
 
 // ---------------------------------------------------------- gradients
@@ -455,11 +461,11 @@ template <typename T>
 __global__ void __launch_bounds__(128)
     k_grad_seeds(int N, Sorted<T> s, const T* __restrict__ rec, const T* __restrict__ ginfo,
                  const int* __restrict__ lim, const unsigned* __restrict__ nbr,
-                 const int* __restrict__ ncount, KParams p, double* __restrict__ adj,
+                 const int* __restrict__ ncount, KParams p, T* __restrict__ adj,
                  T* __restrict__ seeds, unsigned long long* __restrict__ lbloom) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double* a = adj + (size_t)i * kAdj;
+    T* a = adj + (size_t)i * kAdj;
     T* sd = seeds + (size_t)i * kSeed;
     unsigned long long bloom = 0ull;
     const T* G = ginfo + (size_t)i * kGInfo;
@@ -589,12 +595,12 @@ __global__ void __launch_bounds__(128)
         }
         normb += psib * w;
         const T qb = psib * (T)norm * dw;
-        Hbi -= qb * (T)q / (T)Hi;
+        Hbi -= qb * q * iH;
         if (r > T(0)) {
-            const T rb = qb / (T)Hi;
-            db[0] += rb * dx / (T)r;
-            db[1] += rb * dy / (T)r;
-            db[2] += rb * dz / (T)r;
+            const T rb = qb * iH * pdiv(T(1), r);
+            db[0] += rb * dx;
+            db[1] += rb * dy;
+            db[2] += rb * dz;
         }
         xbi[0] -= db[0];
         xbi[1] -= db[1];
@@ -620,38 +626,11 @@ __global__ void __launch_bounds__(128)
 // 128-bit loads; the limiter rows are read only when i's bloom mask has the
 // bit of j.
 template <typename T>
-struct Vec2;
-template <>
-struct Vec2<float> {
-    using type = float4;
-    static constexpr int per = 4;
-};
-template <>
-struct Vec2<double> {
-    using type = double2;
-    static constexpr int per = 2;
-};
-
-template <typename T>
-__device__ __forceinline__ void load_record(const T* __restrict__ src, T (&dst)[28]) {
-    using V = typename Vec2<T>::type;
-    constexpr int per = Vec2<T>::per;
-    const V* v = reinterpret_cast<const V*>(src);
-#pragma unroll
-    for (int q = 0; q < 28 / per; ++q) {
-        const V w = __ldg(v + q);
-        const T* e = reinterpret_cast<const T*>(&w);
-#pragma unroll
-        for (int r = 0; r < per; ++r) dst[q * per + r] = e[r];
-    }
-}
-
-template <typename T>
 __global__ void __launch_bounds__(128)
     k_grad_gather(int N, Sorted<T> s, const int* __restrict__ lim, const unsigned* __restrict__ nbr,
                   const int* __restrict__ ncount, const unsigned* __restrict__ rnbr,
                   const int* __restrict__ rcount, KParams p, const T* __restrict__ seeds,
-                  const unsigned long long* __restrict__ lbloom, double* __restrict__ adj) {
+                  const unsigned long long* __restrict__ lbloom, T* __restrict__ adj) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     const P4<T> mj = s.pos[j];
@@ -672,8 +651,8 @@ __global__ void __launch_bounds__(128)
             const T r2 = sep2(dx, dy, dz);
             if (!(r2 < Hi * Hi)) continue;  // j is not in N_i
             const T* R = seeds + (size_t)i * kSeed;
-            T sd[28];
-            load_record<T>(R, sd);
+            T sd[32];  // record 0-27 (and 4 limiter values, unused here)
+            load_row32<32>(R, sd);
             const T r = sqrt(r2);
             const T iH = T(1) / Hi;
             const T q = r * iH;
@@ -697,10 +676,10 @@ __global__ void __launch_bounds__(128)
                 db[2] += df * psi * sd[3 * f + 2];
             }
             if (r > T(0)) {
-                const T rb = psib * norm * dw / Hi;
-                db[0] += rb * dx / r;
-                db[1] += rb * dy / r;
-                db[2] += rb * dz / r;
+                const T rb = psib * norm * dw * iH * pdiv(T(1), r);
+                db[0] += rb * dx;
+                db[1] += rb * dy;
+                db[2] += rb * dz;
             }
             xb[0] += db[0];
             xb[1] += db[1];
@@ -721,7 +700,7 @@ __global__ void __launch_bounds__(128)
             }
         }
     }
-    double* a = adj + (size_t)j * kAdj;
+    T* a = adj + (size_t)j * kAdj;
     a[AX] += xb[0];
     a[AX + 1] += xb[1];
     a[AX + 2] += xb[2];
@@ -741,10 +720,10 @@ __global__ void __launch_bounds__(128)
 template <typename T>
 __global__ void __launch_bounds__(128)
     k_dens_seeds(int N, Sorted<T> s, const unsigned* __restrict__ nbr, const int* __restrict__ ncount,
-                 KParams p, double* __restrict__ adj, T* __restrict__ kap) {
+                 KParams p, T* __restrict__ adj, T* __restrict__ kap) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    double* a = adj + (size_t)i * kAdj;
+    T* a = adj + (size_t)i * kAdj;
     const T m = s.m[i], n = s.n[i], u = s.u[i], g1 = T(p.gamma) - T(1.0);
     const T rhob = a[ARHO], Pb = a[AP];
     const T nb = a[AN] + rhob * m + Pb * g1 * m * u;
@@ -756,13 +735,9 @@ __global__ void __launch_bounds__(128)
     const T iH = T(1) / Hi;
     const int cnt = min(ncount[i], p.cap);
     const unsigned* L = nbr + (size_t)i * p.cap;
-    T dsum = T(0.0);
-    for (int kk = 0; kk < cnt; ++kk) {
-        const P4<T> qj = s.pos[L[kk]];
-        const T r = sqrt(sep2(mi_diff(qj.x, xi, xim1), mi_diff(qj.y, yi, yim1), mi_diff(qj.z, zi, zim1)));
-        const T q = r * iH;
-        dsum += (T)kern_dw(q) * (T)q;
-    }
+    // sum over N_i of w'(q) q: the density pass kept its negative (same
+    // terms, same order), so no loop over N_i is needed for it here
+    const T dsum = -s.sd[i];
     const T H = Hi;
     const T c8 = T(8.0) / (T(kPi) * H * H * H);
     const T dndH = -T(3.0) * n / H - c8 * dsum / H;
@@ -777,7 +752,7 @@ __global__ void __launch_bounds__(128)
         const T dx = mi_diff(qj.x, xi, xim1), dy = mi_diff(qj.y, yi, yim1), dz = mi_diff(qj.z, zi, zim1);
         const T r = sqrt(sep2(dx, dy, dz));
         if (!(r > T(0))) continue;
-        const T c = kappa * (T)kern_dw(r * iH) / (T)r;
+        const T c = kappa * (T)kern_dw(r * iH) * pdiv(T(1), r);
         xb[0] -= c * dx;
         xb[1] -= c * dy;
         xb[2] -= c * dz;
@@ -791,7 +766,7 @@ template <typename T>
 __global__ void __launch_bounds__(128)
     k_dens_gather(int N, Sorted<T> s, const unsigned* __restrict__ nbr, const int* __restrict__ ncount,
                   const unsigned* __restrict__ rnbr, const int* __restrict__ rcount, KParams p,
-                  const T* __restrict__ kap, double* __restrict__ adj) {
+                  const T* __restrict__ kap, T* __restrict__ adj) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     const P4<T> mj = s.pos[j];
@@ -808,25 +783,25 @@ __global__ void __launch_bounds__(128)
             if (!(r2 < mi.w * mi.w)) continue;
             const T r = sqrt(r2);
             if (!(r > T(0))) continue;
-            const T c = kap[i] * kern_dw(r * (T(1) / mi.w)) / r;
+            const T c = kap[i] * kern_dw(r * pdiv(T(1), mi.w)) * pdiv(T(1), r);
             xb[0] += c * dx;
             xb[1] += c * dy;
             xb[2] += c * dz;
         }
     }
-    double* a = adj + (size_t)j * kAdj;
+    T* a = adj + (size_t)j * kAdj;
     a[AX] += xb[0];
     a[AX + 1] += xb[1];
     a[AX + 2] += xb[2];
 }
 
 template <typename T>
-__global__ void k_adj_out_step(int N, const unsigned* __restrict__ orig, const double* __restrict__ adj,
+__global__ void k_adj_out_step(int N, const unsigned* __restrict__ orig, const T* __restrict__ adj,
                                gz_particles gs) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const unsigned o = orig[i];
-    const double* a = adj + (size_t)i * kAdj;
+    const T* a = adj + (size_t)i * kAdj;
     if (gs.x) ((T*)gs.x)[o] = (T)a[AX];
     if (gs.y) ((T*)gs.y)[o] = (T)a[AX + 1];
     if (gs.z) ((T*)gs.z)[o] = (T)a[AX + 2];
@@ -845,20 +820,20 @@ cudaError_t run_step_adjoint(Ctx& c, const gz_particles& gend, gz_particles& gst
     const KParams kp = kparams(c);
     Sorted<T> s = sorted_view<T>(c);
     c.launches += 8;
-    cudaMemsetAsync(c.adj, 0, sizeof(double) * (size_t)N * kAdj, c.stream);
-    k_update_adj<T><<<blocks(N, 256), 256, 0, c.stream>>>(N, s, c.dpdt, c.dEdt, c.dt_use, gend, c.adj, (T*)c.wgt);
+    cudaMemsetAsync(c.adj, 0, sizeof(T) * (size_t)N * kAdj, c.stream);
+    k_update_adj<T><<<blocks(N, 256), 256, 0, c.stream>>>(N, s, c.dpdt, c.dEdt, c.dt_use, gend, (T*)c.adj, (T*)c.wgt);
     k_flux_adj<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, (const T*)c.rec, (const T*)c.sn, c.sid, c.sbox,
                                                          c.nbr, c.ncount, c.rnbr, c.rcount, kp, c.dt_use,
-                                                         (const T*)c.wgt, c.adj);
+                                                         (const T*)c.wgt, (T*)c.adj);
     k_grad_seeds<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, (const T*)c.rec, (const T*)c.ginfo, c.lim,
-                                                           c.nbr, c.ncount, kp, c.adj, (T*)c.seeds,
+                                                           c.nbr, c.ncount, kp, (T*)c.adj, (T*)c.seeds,
                                                            c.lbloom);
     k_grad_gather<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, c.lim, c.nbr, c.ncount, c.rnbr, c.rcount,
-                                                            kp, (const T*)c.seeds, c.lbloom, c.adj);
-    k_dens_seeds<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, c.nbr, c.ncount, kp, c.adj, (T*)c.wgt);
+                                                            kp, (const T*)c.seeds, c.lbloom, (T*)c.adj);
+    k_dens_seeds<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, c.nbr, c.ncount, kp, (T*)c.adj, (T*)c.wgt);
     k_dens_gather<T><<<blocks(N, 128), 128, 0, c.stream>>>(N, s, c.nbr, c.ncount, c.rnbr, c.rcount, kp,
-                                                            (const T*)c.wgt, c.adj);
-    k_adj_out_step<T><<<blocks(N, 256), 256, 0, c.stream>>>(N, c.vals, c.adj, gstart);
+                                                            (const T*)c.wgt, (T*)c.adj);
+    k_adj_out_step<T><<<blocks(N, 256), 256, 0, c.stream>>>(N, c.vals, (const T*)c.adj, gstart);
     return cudaGetLastError();
 }
 template cudaError_t run_step_adjoint<float>(Ctx&, const gz_particles&, gz_particles&);
@@ -878,7 +853,7 @@ cudaError_t ensure_adjoint_scratch(Ctx& c) {
     cudaError_t e = cudaMalloc((void**)&base, bytes);
     if (e != cudaSuccess) return e;
     c.adj_arena = base;
-    c.adj = (double*)base;
+    c.adj = base;
     base += sz[0];
     c.wgt = base;
     base += sz[1];
@@ -895,19 +870,23 @@ cudaError_t ensure_adjoint_scratch(Ctx& c) {
 template <typename T>
 cudaError_t run_flux_adjoint(Ctx& c, const double* dpbar, const double* dEbar) {
     c.launches += 2;
-    cudaMemsetAsync(c.adj, 0, sizeof(double) * (size_t)c.N * kAdj, c.stream);
+    cudaMemsetAsync(c.adj, 0, sizeof(T) * (size_t)c.N * kAdj, c.stream);
     k_gather_wgt<T><<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, c.vals, dpbar, dEbar, (T*)c.wgt);
     k_flux_adj<T><<<blocks(c.N, 128), 128, 0, c.stream>>>(c.N, (const T*)c.rec, (const T*)c.sn, c.sid,
                                                            c.sbox, c.nbr, c.ncount, c.rnbr, c.rcount,
-                                                           kparams(c), c.dt_use, (const T*)c.wgt, c.adj);
+                                                           kparams(c), c.dt_use, (const T*)c.wgt, (T*)c.adj);
     return cudaGetLastError();
 }
 
 cudaError_t run_adj_out_flux(Ctx& c, double* xbar, double* hbar, double* nbar, double* Wbar, double* gbar,
                              double* Bbar) {
     c.launches += 1;
-    k_adj_out_flux<<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, c.vals, c.adj, xbar, hbar, nbar, Wbar, gbar,
-                                                           Bbar);
+    if (c.precision == GZ_FP64)
+        k_adj_out_flux<double><<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, c.vals, (const double*)c.adj, xbar,
+                                                                       hbar, nbar, Wbar, gbar, Bbar);
+    else
+        k_adj_out_flux<float><<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, c.vals, (const float*)c.adj, xbar,
+                                                                      hbar, nbar, Wbar, gbar, Bbar);
     return cudaGetLastError();
 }
 

@@ -429,6 +429,7 @@ gz_status gz_create(const gz_params* params, int32_t nboxes, const int64_t* coun
         {(void**)&c.svy, sz * Nz},        {(void**)&c.svz, sz * Nz},
         {(void**)&c.sm, sz * Nz},         {(void**)&c.su, sz * Nz},
         {(void**)&c.sh, sz * Nz},         {(void**)&c.sn, sz * Nz},
+        {(void**)&c.ssd, sz * Nz},
         {(void**)&c.srho, sz * Nz},       {(void**)&c.sP, sz * Nz},
         {(void**)&c.sc, sz * Nz},         {(void**)&c.sid, 8 * Nz},
         {(void**)&c.spos, 4 * sz * Nz},   {(void**)&c.sprim, 4 * sz * Nz},
@@ -566,8 +567,8 @@ gz_status gz_step_checkpoint(gz_ctx* ctx, gz_particles* p, double dt_fixed, doub
     if (!ctx) return GZ_E_INVAL;
     if (gz_status s = check_particles(ctx, p, true)) return s;
     if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
-    if (!ckpt || ((uintptr_t)ckpt & 15) || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS)
-        return fail(ctx, GZ_E_INVAL, "checkpoint: need a 16-byte aligned buffer and a valid level");
+    if (!ckpt || ((uintptr_t)ckpt & 255) || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS)
+        return fail(ctx, GZ_E_INVAL, "checkpoint: need a 256-byte aligned buffer and a valid level");
     const Ckpt ck = ckpt_view(ctx->c, ckpt, level);
     return GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev, ck),
                        do_step<double>(ctx, p, dt_fixed, dt_used_dev, ck));
@@ -629,8 +630,8 @@ gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt, 
     if (gz_status s = check_particles(ctx, p_start, true)) return s;
     if (!gbar_end || !gbar_start) return fail(ctx, GZ_E_INVAL, "null adjoint set");
     if (!(dt > 0.0) || !isfinite(dt)) return fail(ctx, GZ_E_INVAL, "dt must be finite and > 0");
-    if (ckpt && (((uintptr_t)ckpt & 15) || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS))
-        return fail(ctx, GZ_E_INVAL, "checkpoint: need a 16-byte aligned buffer and a valid level");
+    if (ckpt && (((uintptr_t)ckpt & 255) || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS))
+        return fail(ctx, GZ_E_INVAL, "checkpoint: need a 256-byte aligned buffer and a valid level");
     const Ckpt ck = ckpt_view(ctx->c, const_cast<void*>(ckpt), level);
     return GZ_DISPATCH(do_step_backward<float>(ctx, p_start, dt, ck, gbar_end, gbar_start),
                        do_step_backward<double>(ctx, p_start, dt, ck, gbar_end, gbar_start));

@@ -100,6 +100,29 @@ __device__ __forceinline__ void face_state(const T (&a)[kRecord], T s, T dx, T d
     }
 }
 
+// n values (a multiple of 32 bytes) from 32-byte-aligned global memory with
+// 32-byte vector loads, for per-particle rows read by other particles'
+// threads (scattered rows: whole sectors per L1 wavefront).
+template <int n>
+__device__ __forceinline__ void load_row32(const float* __restrict__ p, float* v) {
+    static_assert(n % 8 == 0, "rows of whole 32-byte vectors");
+#pragma unroll
+    for (int k = 0; k < n / 8; ++k)
+        asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=f"(v[8 * k]), "=f"(v[8 * k + 1]), "=f"(v[8 * k + 2]), "=f"(v[8 * k + 3]), "=f"(v[8 * k + 4]),
+              "=f"(v[8 * k + 5]), "=f"(v[8 * k + 6]), "=f"(v[8 * k + 7])
+            : "l"(p + 8 * k));
+}
+template <int n>
+__device__ __forceinline__ void load_row32(const double* __restrict__ p, double* v) {
+    static_assert(n % 4 == 0, "rows of whole 32-byte vectors");
+#pragma unroll
+    for (int k = 0; k < n / 4; ++k)
+        asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+            : "=d"(v[4 * k]), "=d"(v[4 * k + 1]), "=d"(v[4 * k + 2]), "=d"(v[4 * k + 3])
+            : "l"(p + 4 * k));
+}
+
 // Four values to / from 16-byte-aligned memory.
 __device__ __forceinline__ void store4(float* dst, float a, float b, float c, float d) {
     *reinterpret_cast<float4*>(dst) = make_float4(a, b, c, d);

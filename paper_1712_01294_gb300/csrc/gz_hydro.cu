@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kDensBlock)
     const double C = 32.0 / 3.0;
     double lo = 0.0, hi = 0.0, S = 0.0, Hev = H;
     bool has_lo = false, has_hi = false, conv = false, clamped = false, cached = false;
-    T Rc = T(0);
+    T Rc = T(0), sd_last = T(0);
     int it, cnt = 0, ncache = 0;
     for (it = 1; it <= p.max_iter; ++it) {
         const T Ht = (T)H;
@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(kDensBlock)
         }
         cnt = c;
         S = sw.value();
+        sd_last = sd;
         Hev = (double)Ht;
         const double f = C * (1.0 + S) - p.ngb;
         if (fabs(f) <= p.tol * p.ngb) {
@@ -159,7 +160,13 @@ __global__ void __launch_bounds__(kDensBlock)
         }
     }
     s.h[i] = (T)Hev;
-    s.n[i] = (T)(8.0 * (1.0 + S) / (kPi * Hev * Hev * Hev));
+    if (std::is_same<T, float>::value) {  // FP32 path: no FP64 division per particle
+        const float Hf = (float)Hev;
+        s.n[i] = (T)(8.f * (float)(1.0 + S) / ((float)kPi * Hf * Hf * Hf));
+    } else {
+        s.n[i] = (T)(8.0 * (1.0 + S) / (kPi * Hev * Hev * Hev));
+    }
+    if (s.sd) s.sd[i] = sd_last;  // (absent in the allocation-free density call)
     iters[i] = it;
     ncount[i] = cnt;
     if (!conv) {
@@ -353,7 +360,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
                 }
                 if (want_dt) {
                     const T vd = ((Wj[1] - Wi[1]) * dx + (Wj[2] - Wi[2]) * dy) + (Wj[3] - Wi[3]) * dz;
-                    const T vs = ci + w2[u].y - min(vd / r, T(0));
+                    const T vs = ci + w2[u].y - min(pdiv(vd, r), T(0));
                     vmax = any ? max(vmax, vs) : vs;
                     any = true;
                 }
@@ -430,16 +437,16 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
                 if (k0 + u >= cnt) break;
                 const T dx = mi_diff(q[u].x, xi, xim1), dy = mi_diff(q[u].y, yi, yim1),
                         dz = mi_diff(q[u].z, zi, zim1);
-                const T sij = Hi / (Hi + q[u].w);
+                const T sij = pdiv(Hi, Hi + q[u].w);
                 const T ox = sij * dx, oy = sij * dy, oz = sij * dz;
 #pragma unroll
                 for (int f = 0; f < 5; ++f) {
                     const T D = (gt[3 * f] * ox + gt[3 * f + 1] * oy) + gt[3 * f + 2] * oz;
                     T a = T(1);
                     if (D > T(0))
-                        a = min(T(1), beta * (fmax[f] - Wi[f]) / D);
+                        a = min(T(1), pdiv(beta * (fmax[f] - Wi[f]), D));
                     else if (D < T(0))
-                        a = min(T(1), beta * (fmin[f] - Wi[f]) / D);
+                        a = min(T(1), pdiv(beta * (fmin[f] - Wi[f]), D));
                     if (a < al[f]) {
                         al[f] = a;
                         jact[f] = (int)js[u];
@@ -460,7 +467,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
                         dz = mi_diff(q.z, zi, zim1);
                 const T r = sqrt(sep2(dx, dy, dz));
                 const T vd = ((w.y - Wi[1]) * dx + (w.z - Wi[2]) * dy) + (w.w - Wi[3]) * dz;
-                const T vs = ci + s.prim2[j].y - min(vd / r, T(0));
+                const T vs = ci + s.prim2[j].y - min(pdiv(vd, r), T(0));
                 vmax = any ? max(vmax, vs) : vs;
                 any = true;
             }

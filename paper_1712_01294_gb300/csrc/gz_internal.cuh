@@ -60,6 +60,7 @@ struct Sorted {
     unsigned* orig;     // caller index of sorted particle
     int* box;           // box of sorted particle
     T *n, *rho, *P, *c;
+    T* sd;              // sum over N_i of -w'(q) q at the converged H (density pass)
     P4<T>* pos;         // (x, y, z, H)
     P4<T>* prim;        // (rho, vx, vy, vz)
     P2<T>* prim2;       // (P, c)
@@ -93,7 +94,7 @@ struct Ctx {
     int hist_len;
     int* box_of;  // caller order
     // sorted state (working precision) and derived per-particle data
-    void *sx, *sy, *sz, *svx, *svy, *svz, *sm, *su, *sh, *sn, *srho, *sP, *sc;
+    void *sx, *sy, *sz, *svx, *svy, *svz, *sm, *su, *sh, *sn, *srho, *sP, *sc, *ssd;
     void *spos, *sprim, *sprim2;  // packed records P4 (x y z H), P4 (rho v), P2 (P c)
     long long* sid;
     int* sbox;
@@ -130,7 +131,7 @@ struct Ctx {
     long long graph_kernels = 0;
     // adjoint scratch, allocated on the first backward call
     void* adj_arena = nullptr;
-    double* adj = nullptr;    // [N][kAdj]
+    void* adj = nullptr;      // [N][kAdj] working precision
     void* wgt = nullptr;      // [N][4] rate adjoints (working precision); then kappa [N]
     void* seeds = nullptr;    // [N][kSeed] working precision
     unsigned long long* lbloom = nullptr;  // [N] bit (j & 63) set for each limiter target j

@@ -226,6 +226,7 @@ Sorted<T> sorted_view(Ctx& c) {
     s.rho = (T*)c.srho;
     s.P = (T*)c.sP;
     s.c = (T*)c.sc;
+    s.sd = (T*)c.ssd;
     s.pos = (P4<T>*)c.spos;
     s.prim = (P4<T>*)c.sprim;
     s.prim2 = (P2<T>*)c.sprim2;
