@@ -202,8 +202,9 @@ gz_status gz_graph_launch(gz_ctx* ctx);
  * gz_checkpoint_bytes(level) bytes, written by gz_step_checkpoint and read
  * by gz_step_backward of the same step; its layout is private.  Level
  * GZ_CKPT_RATES keeps the step's conserved-variable rates (the momentum
- * and total-energy rates of the MFM update, O12; 32 bytes a particle) so the
- * backward pass skips the flux pass; GZ_CKPT_GRADIENTS also keeps the
+ * and total-energy rates of the MFM update, O12) and the converged support
+ * radii (O4; 36 bytes a particle in FP32) so the backward pass skips the
+ * h-iteration and the flux pass; GZ_CKPT_GRADIENTS also keeps the
  * gradient pass's per-particle outputs (limited gradients, E^-1, limiter
  * factors and the indices of the limiting particles; about 330 bytes a
  * particle in FP32) so the backward pass skips that pass too.  No pair
@@ -219,11 +220,11 @@ gz_status gz_step_checkpoint(gz_ctx* ctx, gz_particles* p, double dt_fixed, doub
 
 /* Adjoint of one gz_step (all of O4-O14 with the step dt held fixed and
  * neighbour sets frozen at their forward values).  p_start is the state the
- * forward step started from (it is not modified); its h is the initial guess
- * of the support radius: passing the h that the forward step returned (the
- * converged H) makes the h-iteration accept it at once, with the same H, lists
- * and sums as the forward.  ckpt (with its level) is that step's checkpoint
- * from gz_step_checkpoint, or NULL to recompute everything from p_start.
+ * forward step started from (it is not modified).  ckpt (with its level) is
+ * that step's checkpoint from gz_step_checkpoint, or NULL to recompute
+ * everything from p_start; without a checkpoint, p_start's h is the initial
+ * guess of the h-iteration (passing the h the forward step returned makes it
+ * accept that H at once, with the same H, lists and sums as the forward).
  * gbar_end holds dL/d(state after the step) for x, y, z, vx, vy, vz, u (m, h,
  * id ignored; arrays in the working precision); gbar_start receives
  * dL/d(state before the step) for x, y, z, vx, vy, vz, u and m.  dt is the

@@ -70,8 +70,11 @@ __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)
     const T Hs = a[3] + b[3];
     const T sa = pdiv(a[3], Hs), sb = pdiv(b[3], Hs);
     T Fa[5], Fb[5];
-    face_state(a, sa, dx, dy, dz, hdt, gam, hancock, Fa);
-    face_state(b, sb, -dx, -dy, -dz, hdt, gam, hancock, Fb);
+    T inca[5], incb[5];
+    hancock_inc(a, hdt, gam, hancock, inca);
+    hancock_inc(b, hdt, gam, hancock, incb);
+    face_state(a, sa, dx, dy, dz, inca, Fa);
+    face_state(b, sb, -dx, -dy, -dz, incb, Fb);
     const T Wa[5] = {a[6], a[8], a[9], a[10], a[7]};
     const T Wb[5] = {b[6], b[8], b[9], b[10], b[7]};
     // clamp sides: 0 inside, -1 clamped to the lower bound, +1 to the upper
@@ -240,7 +243,7 @@ __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)
                 bWa[f] += ((kb[f] < 0) ? loA : hiA) ? bGb[f] : T(0);
         }
     }
-    // face states: F_a = W_a + g_a . (s_a d) + hdt D_a ; F_b = W_b + g_b . (s_b (-d)) + hdt D_b
+    // face states: F_a = W_a + g_a . (s_a d) + inc_a ; F_b = W_b + g_b . (s_b (-d)) + inc_b
     T bd[3] = {T(0), T(0), T(0)};
     T bg[15];
 #pragma unroll
@@ -262,16 +265,17 @@ __device__ __forceinline__ void pair_adjoint(const T (&a)[kRecord], const T (&b)
         bd[1] -= bFb[f] * sb * h1;
         bd[2] -= bFb[f] * sb * h2;
     }
-    if (hancock) {
-        const T div = ((T)a[11 + 3] + a[11 + 7]) + a[11 + 11];
+    if (hancock) {  // inc_a = (dt/2)(-rho div v, -grad P / rho, -gamma P div v)
+        const T div = (a[11 + 3] + a[11 + 7]) + a[11 + 11];
         const T rho = a[6], P = a[7];
-        const T b_div = bFa[0] * hdt * (-rho) + bFa[4] * hdt * (-(T)gam * P);
+        const T b_div = bFa[0] * hdt * (-rho) + bFa[4] * hdt * (-gam * P);
         bWa[0] += bFa[0] * hdt * (-div);
+#pragma unroll
         for (int k = 0; k < 3; ++k) {
             bWa[0] += bFa[1 + k] * hdt * a[11 + 12 + k] * irho * irho;
             bg[12 + k] -= bFa[1 + k] * hdt * irho;
         }
-        bWa[4] += bFa[4] * hdt * (-(T)gam * div);
+        bWa[4] += bFa[4] * hdt * (-gam * div);
         bg[3] += b_div;
         bg[7] += b_div;
         bg[11] += b_div;

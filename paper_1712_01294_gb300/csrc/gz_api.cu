@@ -195,12 +195,14 @@ gz_status do_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const void* n, 
 }
 
 // Step checkpoint blob (device, caller-owned): [rates: 4 N doubles, caller
-// order] then, at GZ_CKPT_GRADIENTS, the gradient pass's per-particle
-// outputs in sorted order: flux record [N][kRecord], adjoint info
-// [N][kGInfo] (working precision) and limiter indices [N][10]; slices start
-// on 256-byte boundaries.
+// order] [converged H, sorted order] then, at GZ_CKPT_GRADIENTS, the
+// gradient pass's per-particle outputs in sorted order: flux record
+// [N][kRecord], adjoint info [N][kGInfo] (working precision) and limiter
+// indices [N][10]; slices start on 256-byte boundaries.  (The backward
+// pass sorts the same start state, so sorted order is the same.)
 struct Ckpt {
     double* rates = nullptr;
+    void* H = nullptr;
     void* rec = nullptr;
     void* ginfo = nullptr;
     int* lim = nullptr;
@@ -208,7 +210,7 @@ struct Ckpt {
 size_t ckpt_slice(size_t b) { return (b + 255) & ~(size_t)255; }
 size_t ckpt_bytes(const Ctx& c, int level) {
     const size_t N = (size_t)c.N, ts = c.precision == GZ_FP64 ? 8 : 4;
-    size_t b = ckpt_slice(sizeof(double) * 4 * N);
+    size_t b = ckpt_slice(sizeof(double) * 4 * N) + ckpt_slice(ts * N);
     if (level >= GZ_CKPT_GRADIENTS)
         b += ckpt_slice(ts * N * kRecord) + ckpt_slice(ts * N * kGInfo) + ckpt_slice(sizeof(int) * N * 10);
     return b;
@@ -220,6 +222,8 @@ Ckpt ckpt_view(const Ctx& c, void* base, int level) {
     char* p = (char*)base;
     k.rates = (double*)p;
     p += ckpt_slice(sizeof(double) * 4 * N);
+    k.H = p;
+    p += ckpt_slice(ts * N);
     if (level >= GZ_CKPT_GRADIENTS) {
         k.rec = p;
         p += ckpt_slice(ts * N * kRecord);
@@ -266,7 +270,12 @@ gz_status do_step_backward(gz_ctx* ctx, const gz_particles* p, double dt, const 
     }
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_DENSITY);
-        e = run_density<T>(c);
+        if (ck.H) {  // the forward's converged H: no h-iteration
+            e = cudaMemcpyAsync(c.sh, ck.H, sizeof(T) * (size_t)c.N, cudaMemcpyDeviceToDevice, c.stream);
+            if (e == cudaSuccess) e = run_density_given<T>(c);
+        } else {
+            e = run_density<T>(c);
+        }
     }
     if (e == cudaSuccess) e = run_prim<T>(c);
     if (e == cudaSuccess) e = run_reverse<T>(c);
@@ -299,6 +308,8 @@ gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_DENSITY);
         e = run_density<T>(c);
+        if (e == cudaSuccess && ck.H)
+            e = cudaMemcpyAsync(ck.H, c.sh, sizeof(T) * (size_t)c.N, cudaMemcpyDeviceToDevice, c.stream);
     }
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_PRIM);

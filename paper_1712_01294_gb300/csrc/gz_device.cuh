@@ -81,23 +81,35 @@ __device__ __forceinline__ void load_rec(const double* __restrict__ p, double (&
 // Face state of particle a toward the face at a + s o (o = offset to the
 // partner): linear reconstruction with a's limited gradients plus the Hancock
 // half step (dt/2) (-rho div v, -grad P / rho, -gamma P div v).
+// Hancock half-step increments of a particle's primitives (O11):
+// (dt/2)(-rho div v, -grad P / rho, -gamma P div v), each product rounded
+// once so that every pass that forms them gets the same bits.
 template <typename T>
-__device__ __forceinline__ void face_state(const T (&a)[kRecord], T s, T dx, T dy, T dz, T hdt,
-                                           T gam, bool hancock, T (&F)[5]) {
+__device__ __forceinline__ void hancock_inc(const T (&a)[kRecord], T hdt, T gam, bool hancock, T (&inc)[5]) {
+    if (!hancock) {
+#pragma unroll
+        for (int f = 0; f < 5; ++f) inc[f] = T(0);
+        return;
+    }
+    const T div = (a[11 + 3] + a[11 + 7]) + a[11 + 11];
+    const T ir = pdiv(T(1), a[6]);
+    inc[0] = mul_rn(hdt, -a[6] * div);
+    inc[1] = mul_rn(hdt, -a[11 + 12] * ir);
+    inc[2] = mul_rn(hdt, -a[11 + 13] * ir);
+    inc[3] = mul_rn(hdt, -a[11 + 14] * ir);
+    inc[4] = mul_rn(hdt, -gam * a[7] * div);
+}
+
+// Face state of a record at offset s (dx, dy, dz) from the particle:
+// W + g . (s d) + the Hancock increments.
+template <typename T>
+__device__ __forceinline__ void face_state(const T (&a)[kRecord], T s, T dx, T dy, T dz, const T (&inc)[5],
+                                           T (&F)[5]) {
     const T ox = s * dx, oy = s * dy, oz = s * dz;
     const T W[5] = {a[6], a[8], a[9], a[10], a[7]};
 #pragma unroll
     for (int f = 0; f < 5; ++f)
-        F[f] = W[f] + ((a[11 + 3 * f] * ox + a[12 + 3 * f] * oy) + a[13 + 3 * f] * oz);
-    if (hancock) {
-        const T div = (a[11 + 3] + a[11 + 7]) + a[11 + 11];
-        const T ir = pdiv(T(1), a[6]);
-        F[0] += hdt * (-a[6] * div);
-        F[1] += hdt * (-a[11 + 12] * ir);
-        F[2] += hdt * (-a[11 + 13] * ir);
-        F[3] += hdt * (-a[11 + 14] * ir);
-        F[4] += hdt * (-gam * a[7] * div);
-    }
+        F[f] = add_rn(W[f] + ((a[11 + 3 * f] * ox + a[12 + 3 * f] * oy) + a[13 + 3 * f] * oz), inc[f]);
 }
 
 // n values (a multiple of 32 bytes) from 32-byte-aligned global memory with
@@ -151,7 +163,8 @@ __device__ __forceinline__ void load4(const double* src, double (&v)[4]) {
 // Returns false when the face area vanishes.  flags: 1 fallback, 2 P* < 0.
 template <typename T>
 __device__ __forceinline__ bool pair_rates(const T (&a)[kRecord], const T (&b)[kRecord], bool aL,
-                                           T hdt, T gam, bool hancock, T (&dp)[3], T& dE, int& fl) {
+                                           T hdt, T gam, bool hancock, const T (&inca)[5], T (&dp)[3],
+                                           T& dE, int& fl) {
     const T dx = mi_diff(b[0], a[0], a[0] - T(1));
     const T dy = mi_diff(b[1], a[1], a[1] - T(1));
     const T dz = mi_diff(b[2], a[2], a[2] - T(1));
@@ -176,8 +189,10 @@ __device__ __forceinline__ bool pair_rates(const T (&a)[kRecord], const T (&b)[k
     const T Hs = a[3] + b[3];
     const T sa = pdiv(a[3], Hs), sb = pdiv(b[3], Hs);
     T Fa[5], Fb[5];
-    face_state(a, sa, dx, dy, dz, hdt, gam, hancock, Fa);
-    face_state(b, sb, -dx, -dy, -dz, hdt, gam, hancock, Fb);
+    T incb[5];
+    hancock_inc(b, hdt, gam, hancock, incb);
+    face_state(a, sa, dx, dy, dz, inca, Fa);
+    face_state(b, sb, -dx, -dy, -dz, incb, Fb);
     const T Wa[5] = {a[6], a[8], a[9], a[10], a[7]};
     const T Wb[5] = {b[6], b[8], b[9], b[10], b[7]};
 #pragma unroll

@@ -199,6 +199,47 @@ __global__ void __launch_bounds__(128)
     if (c > p.cap) set_status(st, GZ_S_NBR_OVERFLOW, GZ_C_NBR_OVERFLOW, s.id[i]);
 }
 
+// Density pass for a known converged H (a step checkpoint's): the neighbour
+// list of H, n and the sum of -w'(q) q in one cell scan of radius H.  The
+// candidates inside H come in the h-iteration's scan order and are summed the
+// same way, so n and the sums equal the h-iteration's last evaluation bit
+// for bit.
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_dens_given(int N, Sorted<T> s, Grid g, KParams p, unsigned* __restrict__ nbr,
+                 int* __restrict__ ncount, DevStatus* st) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const BoxInfo bx = g.boxes[s.box[i]];
+    const T Ht = s.h[i];
+    const T H2 = Ht * Ht;
+    const T iH = T(1) / Ht;
+    const P4<T> me = s.pos[i];
+    Acc<T> sw;
+    T sd = T(0);
+    int c = 0;
+    for_candidates<T>(g, bx, s.pos, i, me.x, me.y, me.z, Ht,
+                      [&](int j, T, T, T, T r2) {
+                          if (r2 < H2) {
+                              const T q = sqrt(r2) * iH;
+                              sw.add(kern_w(q));
+                              sd += -kern_dw(q) * q;
+                              if (c < p.cap) nbr[(size_t)i * p.cap + c] = (unsigned)j;
+                              ++c;
+                          }
+                      });
+    const double S = sw.value(), Hev = (double)Ht;
+    if (std::is_same<T, float>::value) {
+        const float Hf = (float)Hev;
+        s.n[i] = (T)(8.f * (float)(1.0 + S) / ((float)kPi * Hf * Hf * Hf));
+    } else {
+        s.n[i] = (T)(8.0 * (1.0 + S) / (kPi * Hev * Hev * Hev));
+    }
+    s.sd[i] = sd;
+    ncount[i] = c;
+    if (c > p.cap) set_status(st, GZ_S_NBR_OVERFLOW, GZ_C_NBR_OVERFLOW, s.id[i]);
+}
+
 // Reverse pairs (O10): j in N_i with r_ij >= H_j is appended to j's list.
 // Reads the packed positions, whose w component is the converged H.
 template <typename T>
@@ -587,6 +628,8 @@ __global__ void __launch_bounds__(kFluxBlock)
     const T hdt = (T)(0.5 * dt_use[sbox[i]]);
     const T gam = (T)p.gamma;
     const bool hancock = p.hancock != 0;
+    T inca[5];
+    hancock_inc(a, hdt, gam, hancock, inca);
     T part[4] = {T(0), T(0), T(0), T(0)};
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     int np = 0, nfall = 0, nneg = 0;
@@ -605,7 +648,7 @@ __global__ void __launch_bounds__(kFluxBlock)
                 load_rec(rec + (size_t)j * kRecord, b);
                 T dp[3], dE;
                 int fl = 0;
-                if (pair_rates(a, b, idi < sid[j], hdt, gam, hancock, dp, dE, fl)) {
+                if (pair_rates(a, b, idi < sid[j], hdt, gam, hancock, inca, dp, dE, fl)) {
                     part[0] += dp[0];
                     part[1] += dp[1];
                     part[2] += dp[2];
@@ -832,6 +875,14 @@ cudaError_t run_density(Ctx& c) {
 }
 
 template <typename T>
+cudaError_t run_density_given(Ctx& c) {
+    c.launches += 1;
+    k_dens_given<T><<<blocks(c.N, 128), 128, 0, c.stream>>>(c.N, sorted_view<T>(c), grid_of(c), kparams(c),
+                                                             c.nbr, c.ncount, c.status);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t run_build_lists(Ctx& c) {
     c.launches += 1;
     k_lists<T><<<blocks(c.N, 128), 128, 0, c.stream>>>(c.N, sorted_view<T>(c), grid_of(c), kparams(c),
@@ -955,6 +1006,7 @@ cudaError_t run_get_neighbours(Ctx& c, int32_t* count_out, int64_t* ids_out, int
 
 #define GZ_INST(T)                                                   \
     template cudaError_t run_density<T>(Ctx&);                       \
+    template cudaError_t run_density_given<T>(Ctx&);                 \
     template cudaError_t run_build_lists<T>(Ctx&);                   \
     template cudaError_t run_reverse<T>(Ctx&);                       \
     template cudaError_t run_prim<T>(Ctx&);                          \

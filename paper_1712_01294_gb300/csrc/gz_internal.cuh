@@ -191,8 +191,10 @@ __device__ __forceinline__ bool finite_(double v) { return isfinite(v); }
 __device__ __forceinline__ double sep2(double dx, double dy, double dz) {
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
+// FP32: written with explicit fused multiply-adds so that every kernel forms
+// r^2 of a pair with the same bits, whatever the compiler contracts elsewhere.
 __device__ __forceinline__ float sep2(float dx, float dy, float dz) {
-    return (dx * dx + dy * dy) + dz * dz;
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
 // ordered-integer image of a non-negative double (for atomicMin)

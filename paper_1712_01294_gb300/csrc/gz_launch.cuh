@@ -24,6 +24,8 @@ cudaError_t unpermute_i(Ctx& c, const int* src, int* dst);
 template <typename T>
 cudaError_t run_density(Ctx& c);
 template <typename T>
+cudaError_t run_density_given(Ctx& c);
+template <typename T>
 cudaError_t run_build_lists(Ctx& c);
 template <typename T>
 cudaError_t run_reverse(Ctx& c);
