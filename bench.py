@@ -40,7 +40,15 @@ UNIT = "particle-updates/s"
 # squares of H 2, two volumes 2, two B d 30, face area 15, |A| 6, s 2, v_f 9,
 # normal 3, s_R 2, offsets 6, reconstruction 60, Hancock 37, v_f.n 5, u_L u_R
 # 16, HLLC 30, rates 6, accumulation into both particles 8.
-FLOPS_PER_PAIR = 276
+FLOPS_PER_PAIR = 276            # flux pass, per unordered pair
+FLOPS_PER_DENSITY_TERM = 24     # density pass, per (particle, evaluation, neighbour)
+FLOPS_PER_GRAD_NEIGHBOUR = 127  # gradient pass, per (particle, neighbour)
+FLOPS_PER_GRAD_PARTICLE = 60    # gradient pass, per particle
+# DRAM bytes (read + write) per work unit of each kernel, from the ncu capture
+# summarised in TRAFFIC_SOURCE (64^3 turbulence, scaled by units); empty
+# until a capture of the current kernels is recorded
+TRAFFIC_PER_UNIT = {}
+TRAFFIC_SOURCE = None
 SMS, FP32_LANES = 152, 128
 
 
@@ -172,6 +180,16 @@ def run_ours(a, world, rank, local):
         prof = ctx.profile_read(reset=True)
         ctx.profile(False)
         pairs = ctx.pair_count()
+        # work units of the density and gradient passes: one density pass on a
+        # copy of the state (the start of the next step), outside the timing
+        dcopy = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in d.items()}
+        _, iters = ctx.density(dcopy)
+        nbr_counts, _ = ctx.neighbours(0)
+        it64 = iters.to(torch.int64)
+        nc64 = nbr_counts.to(torch.int64)
+        work = {"density_eval_neighbours": int((it64 * nc64).sum()), "neighbours": int(nc64.sum()),
+                "mean_iterations": round(float(it64.double().mean()), 3)}
+        del dcopy
         st = ctx.status(reset=True)
         if not st["ok"]:
             raise RuntimeError(f"device status after timed steps: {st}")
@@ -201,19 +219,35 @@ def run_ours(a, world, rank, local):
         tmax, ms_e2e = float(tt[0]), float(tt[1])
     value = world * N * a.steps / (tmax / 1e3)
     e2e = world * N * a.e2e_steps / (ms_e2e / 1e3) if a.e2e_steps > 0 else None
-    # roofline of the dominant kernel
+    # roofline: each pair pass against the FP32 ALU peak, by its algorithmic
+    # FLOP (counted on the oracle's routines); the dominant one by time is
+    # the headline entry
     pk = peaks()
     clocks = clk.summary()
-    dom = max(("density", "gradients", "fluxes", "sort", "update"), key=lambda k: prof[k][0])
-    flux_ms = prof["fluxes"][0] / max(prof["fluxes"][1], 1)
     sm_max = pk.get("sm_max_mhz", 2070.0)
     peak_fp32 = SMS * FP32_LANES * 2 * sm_max * 1e6 / 1e12
-    achieved = FLOPS_PER_PAIR * (pairs / 2) / (flux_ms / 1e3) / 1e12
-    roof = {"kernel": "k_fluxes", "bound": "alu", "achieved": round(achieved, 3),
-            "peak": round(peak_fp32, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_fp32, 4),
-            "traffic": None, "peak_basis": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {sm_max:.0f} MHz",
-            "flops_per_pair": FLOPS_PER_PAIR, "unordered_pairs": pairs // 2,
-            "avg_launch_ms": round(flux_ms, 4)}
+    flops = {"density": FLOPS_PER_DENSITY_TERM * work["density_eval_neighbours"],
+             "gradients": FLOPS_PER_GRAD_NEIGHBOUR * work["neighbours"] + FLOPS_PER_GRAD_PARTICLE * N,
+             "fluxes": FLOPS_PER_PAIR * (pairs // 2)}
+    units = {"density": (work["density_eval_neighbours"], "particle-evaluation-neighbour terms",
+                         FLOPS_PER_DENSITY_TERM),
+             "gradients": (work["neighbours"], "particle-neighbour terms (+60 FLOP per particle)",
+                           FLOPS_PER_GRAD_NEIGHBOUR),
+             "fluxes": (pairs // 2, "unordered flux pairs", FLOPS_PER_PAIR)}
+    kern = {"density": "k_density", "gradients": "k_gradients", "fluxes": "k_fluxes"}
+    kernels = []
+    for name in ("density", "gradients", "fluxes"):
+        ms_k = prof[name][0] / max(prof[name][1], 1)
+        ach = flops[name] / (ms_k / 1e3) / 1e12
+        kernels.append({"kernel": kern[name], "bound": "alu", "achieved": round(ach, 3),
+                        "peak": round(peak_fp32, 2), "unit": "TFLOP/s", "frac": round(ach / peak_fp32, 4),
+                        "avg_launch_ms": round(ms_k, 4), "units_per_launch": units[name][0],
+                        "unit_kind": units[name][1], "flop_per_unit": units[name][2],
+                        "traffic": TRAFFIC_PER_UNIT.get(name) and round(TRAFFIC_PER_UNIT[name] * units[name][0]),
+                        "traffic_source": TRAFFIC_SOURCE if name in TRAFFIC_PER_UNIT else None})
+    roof = dict(max(kernels, key=lambda k: k["avg_launch_ms"]))
+    dom = max(("density", "gradients", "fluxes", "sort", "update"), key=lambda k: prof[k][0])
+    roof["peak_basis"] = f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 x {sm_max:.0f} MHz (ALU, not tensor)"
     shares = {k: round(v[0] / max(sum(x[0] for x in prof.values()), 1e-9), 4) for k, v in prof.items()
               if v[1]}
     line = {
@@ -227,6 +261,8 @@ def run_ours(a, world, rank, local):
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "working set (~2 GB) far above the 129 MB L2; no flush needed"},
         "roofline": roof,
+        "roofline_kernels": kernels,
+        "work": work,
         "pass_ms_per_step": {k: round(v[0] / max(v[1], 1), 4) for k, v in prof.items() if v[1]},
         "pass_share": shares, "dominant_pass": dom,
         "e2e": {"value": round(e2e, 1) if e2e else None, "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -22,6 +22,7 @@ struct Acc<float> {
         s = t;
     }
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+    __device__ __forceinline__ float fvalue() const { return __fsub_rn(s, c); }
 };
 
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }

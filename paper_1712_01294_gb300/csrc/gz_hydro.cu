@@ -103,10 +103,20 @@ __global__ void __launch_bounds__(kDensBlock)
                               });
         }
         cnt = c;
-        S = sw.value();
         sd_last = sd;
         Hev = (double)Ht;
-        const double f = C * (1.0 + S) - p.ngb;
+        // f = (32/3)(1 + S) - N_ngb.  FP32 path: in FP32 (its rounding, about
+        // 4e-6, is well inside the stop tolerance 1e-6 N_ngb); H, the bracket
+        // and the update below stay FP64
+        double f;
+        if constexpr (std::is_same<T, float>::value) {
+            const float Sf = sw.fvalue();
+            S = (double)Sf;
+            f = (double)((32.f / 3.f) * (1.f + Sf) - (float)p.ngb);
+        } else {
+            S = sw.value();
+            f = C * (1.0 + S) - p.ngb;
+        }
         if (fabs(f) <= p.tol * p.ngb) {
             conv = true;
             break;
@@ -228,7 +238,12 @@ __global__ void __launch_bounds__(128)
                               ++c;
                           }
                       });
-    const double S = sw.value(), Hev = (double)Ht;
+    double S;
+    if constexpr (std::is_same<T, float>::value)
+        S = (double)sw.fvalue();  // as the h-iteration forms it
+    else
+        S = sw.value();
+    const double Hev = (double)Ht;
     if (std::is_same<T, float>::value) {
         const float Hf = (float)Hev;
         s.n[i] = (T)(8.f * (float)(1.0 + S) / ((float)kPi * Hf * Hf * Hf));
