@@ -571,9 +571,22 @@ __global__ void __launch_bounds__(128)
     T normb = T(0.0);
     const int cnt = min(ncount[i], p.cap);
     const unsigned* L = nbr + (size_t)i * p.cap;
-    for (int kk = 0; kk < cnt; ++kk) {
-        const int j = (int)L[kk];
-        const P4<T> qj = s.pos[j];
+    for (int k0 = 0; k0 < cnt; k0 += 4) {  // four neighbours' loads in flight at a time
+      const uint4 jj = *reinterpret_cast<const uint4*>(L + k0);
+      const unsigned js[4] = {jj.x, jj.y, jj.z, jj.w};
+      P4<T> qv[4], pv[4];
+      T Pv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+          if (k0 + u < cnt) {
+              qv[u] = s.pos[js[u]];
+              pv[u] = s.prim[js[u]];
+              Pv[u] = s.prim2[js[u]].x;
+          }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (k0 + u >= cnt) break;
+        const P4<T> qj = qv[u];
         const T dxT = mi_diff(qj.x, xi, xim1), dyT = mi_diff(qj.y, yi, yim1), dzT = mi_diff(qj.z, zi, zim1);
         const T r2 = sep2(dxT, dyT, dzT);
         const T r = sqrt(r2);
@@ -581,8 +594,8 @@ __global__ void __launch_bounds__(128)
         const T w = kern_w(q), dw = kern_dw(q);
         const T psi = (T)(norm * kern_w(q));
         const T dx = dxT, dy = dyT, dz = dzT;
-        const P4<T> pj = s.prim[j];
-        const T Wj[5] = {pj.x, pj.y, pj.z, pj.w, s.prim2[j].x};
+        const P4<T> pj = pv[u];
+        const T Wj[5] = {pj.x, pj.y, pj.z, pj.w, Pv[u]};
         T psib = ((Eb[0] * dx * dx + Eb[1] * dx * dy) + (Eb[2] * dx * dz + Eb[3] * dy * dy)) +
                       (Eb[4] * dy * dz + Eb[5] * dz * dz);
         T db[3] = {psi * (T(2.0) * Eb[0] * dx + Eb[1] * dy + Eb[2] * dz),
@@ -609,6 +622,7 @@ __global__ void __launch_bounds__(128)
         xbi[0] -= db[0];
         xbi[1] -= db[1];
         xbi[2] -= db[2];
+      }
     }
     Hbi += normb * (-T(3.0) * (T)norm / (T)Hi);
     nbi += normb * (-(T)norm / (T)ni);
@@ -645,9 +659,18 @@ __global__ void __launch_bounds__(128)
     for (int list = 0; list < 2; ++list) {
         const unsigned* Lj = list == 0 ? nbr + (size_t)j * p.cap : rnbr + (size_t)j * p.rcap;
         const int cnt = list == 0 ? min(ncount[j], p.cap) : min(rcount[j], p.rcap);
-        for (int kk = 0; kk < cnt; ++kk) {
-            const int i = (int)Lj[kk];
-            const P4<T> mi = s.pos[i];
+        for (int k0 = 0; k0 < cnt; k0 += 4) {  // four candidates' loads in flight at a time
+          const uint4 ii = *reinterpret_cast<const uint4*>(Lj + k0);
+          const unsigned is[4] = {ii.x, ii.y, ii.z, ii.w};
+          P4<T> mv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+              if (k0 + u < cnt) mv[u] = s.pos[is[u]];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (k0 + u >= cnt) break;
+            const int i = (int)is[u];
+            const P4<T> mi = mv[u];
             const T Hi = mi.w;
             // offset as seen by i (x_j - x_i), exactly as i's gradient pass computed it
             const T dx = mi_diff(mj.x, mi.x, mi.x - T(1)), dy = mi_diff(mj.y, mi.y, mi.y - T(1)),
@@ -702,6 +725,7 @@ __global__ void __launch_bounds__(128)
                     if (ja >= 0 && li[5 + f] == j) fb[f] += R[28 + 5 * f + 4];
                 }
             }
+          }
         }
     }
     T* a = adj + (size_t)j * kAdj;
@@ -751,15 +775,25 @@ __global__ void __launch_bounds__(128)
     const T kappa = (nb * c8 + lam * T(32.0) / T(3.0)) / H;
     kap[i] = kappa;
     T xb[3] = {0, 0, 0};
-    for (int kk = 0; kk < cnt; ++kk) {
-        const P4<T> qj = s.pos[L[kk]];
-        const T dx = mi_diff(qj.x, xi, xim1), dy = mi_diff(qj.y, yi, yim1), dz = mi_diff(qj.z, zi, zim1);
-        const T r = sqrt(sep2(dx, dy, dz));
-        if (!(r > T(0))) continue;
-        const T c = kappa * (T)kern_dw(r * iH) * pdiv(T(1), r);
-        xb[0] -= c * dx;
-        xb[1] -= c * dy;
-        xb[2] -= c * dz;
+    for (int k0 = 0; k0 < cnt; k0 += 4) {  // four neighbours' loads in flight at a time
+        const uint4 jj = *reinterpret_cast<const uint4*>(L + k0);
+        const unsigned js[4] = {jj.x, jj.y, jj.z, jj.w};
+        P4<T> qv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (k0 + u < cnt) qv[u] = s.pos[js[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (k0 + u >= cnt) break;
+            const P4<T> qj = qv[u];
+            const T dx = mi_diff(qj.x, xi, xim1), dy = mi_diff(qj.y, yi, yim1), dz = mi_diff(qj.z, zi, zim1);
+            const T r = sqrt(sep2(dx, dy, dz));
+            if (!(r > T(0))) continue;
+            const T c = kappa * (T)kern_dw(r * iH) * pdiv(T(1), r);
+            xb[0] -= c * dx;
+            xb[1] -= c * dy;
+            xb[2] -= c * dz;
+        }
     }
     a[AX] += xb[0];
     a[AX + 1] += xb[1];
@@ -778,19 +812,29 @@ __global__ void __launch_bounds__(128)
     for (int list = 0; list < 2; ++list) {
         const unsigned* Lj = list == 0 ? nbr + (size_t)j * p.cap : rnbr + (size_t)j * p.rcap;
         const int cnt = list == 0 ? min(ncount[j], p.cap) : min(rcount[j], p.rcap);
-        for (int kk = 0; kk < cnt; ++kk) {
-            const int i = (int)Lj[kk];
-            const P4<T> mi = s.pos[i];
-            const T dx = mi_diff(mj.x, mi.x, mi.x - T(1)), dy = mi_diff(mj.y, mi.y, mi.y - T(1)),
-                    dz = mi_diff(mj.z, mi.z, mi.z - T(1));
-            const T r2 = sep2(dx, dy, dz);
-            if (!(r2 < mi.w * mi.w)) continue;
-            const T r = sqrt(r2);
-            if (!(r > T(0))) continue;
-            const T c = kap[i] * kern_dw(r * pdiv(T(1), mi.w)) * pdiv(T(1), r);
-            xb[0] += c * dx;
-            xb[1] += c * dy;
-            xb[2] += c * dz;
+        for (int k0 = 0; k0 < cnt; k0 += 4) {  // four candidates' loads in flight at a time
+            const uint4 ii = *reinterpret_cast<const uint4*>(Lj + k0);
+            const unsigned is[4] = {ii.x, ii.y, ii.z, ii.w};
+            P4<T> mv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (k0 + u < cnt) mv[u] = s.pos[is[u]];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (k0 + u >= cnt) break;
+                const int i = (int)is[u];
+                const P4<T> mi = mv[u];
+                const T dx = mi_diff(mj.x, mi.x, mi.x - T(1)), dy = mi_diff(mj.y, mi.y, mi.y - T(1)),
+                        dz = mi_diff(mj.z, mi.z, mi.z - T(1));
+                const T r2 = sep2(dx, dy, dz);
+                if (!(r2 < mi.w * mi.w)) continue;
+                const T r = sqrt(r2);
+                if (!(r > T(0))) continue;
+                const T c = kap[i] * kern_dw(r * pdiv(T(1), mi.w)) * pdiv(T(1), r);
+                xb[0] += c * dx;
+                xb[1] += c * dy;
+                xb[2] += c * dz;
+            }
         }
     }
     T* a = adj + (size_t)j * kAdj;

@@ -247,22 +247,39 @@ __device__ __forceinline__ void for_candidates(const Grid& g, const BoxInfo& bx,
                 const T ax = cx < 0 ? T(-1) : T(0), bxx = cx >= nc ? xim1 : xi;
                 const int2 se = cells[row + wx];
                 if (percell) {
-                    for (int j = se.x; j < se.y; ++j) {
-                        if (j == self) continue;
-                        const P4<T> q = pos[j];
-                        const T dx = (q.x + ax) - bxx;
-                        const T dy = (q.y + ay) - by;
-                        const T dz = (q.z + az) - bz;
-                        fn(j, dx, dy, dz, sep2(dx, dy, dz));
+                    // four candidates' positions in flight at a time
+                    for (int j0 = se.x; j0 < se.y; j0 += 4) {
+                        P4<T> q[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (j0 + u < se.y) q[u] = pos[j0 + u];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int j = j0 + u;
+                            if (j >= se.y) break;
+                            if (j == self) continue;
+                            const T dx = (q[u].x + ax) - bxx;
+                            const T dy = (q[u].y + ay) - by;
+                            const T dz = (q[u].z + az) - bz;
+                            fn(j, dx, dy, dz, sep2(dx, dy, dz));
+                        }
                     }
                 } else {
-                    for (int j = se.x; j < se.y; ++j) {
-                        if (j == self) continue;
-                        const P4<T> q = pos[j];
-                        const T dx = mi_diff(q.x, xi, xim1);
-                        const T dy = mi_diff(q.y, yi, yim1);
-                        const T dz = mi_diff(q.z, zi, zim1);
-                        fn(j, dx, dy, dz, sep2(dx, dy, dz));
+                    for (int j0 = se.x; j0 < se.y; j0 += 4) {
+                        P4<T> q[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (j0 + u < se.y) q[u] = pos[j0 + u];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int j = j0 + u;
+                            if (j >= se.y) break;
+                            if (j == self) continue;
+                            const T dx = mi_diff(q[u].x, xi, xim1);
+                            const T dy = mi_diff(q[u].y, yi, yim1);
+                            const T dz = mi_diff(q[u].z, zi, zim1);
+                            fn(j, dx, dy, dz, sep2(dx, dy, dz));
+                        }
                     }
                 }
             }
