@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--cell-factor", type=float, default=None)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-path, adjoint and ensemble measurements")
+    ap.add_argument("--extras", default="all", choices=["all", "adjoint"],
+                    help="which extra measurements to run (adjoint: only the adjoint cost)")
     return ap.parse_args()
 
 
@@ -348,6 +350,8 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p):
                                   "pair lists and all pair quantities recomputed, then the adjoint "
                                   "passes"}
         del ck
+        if a.extras == "adjoint":
+            return out
         # FP64 path on the same workload
         if prec == gz.GZ_MIXED32:
             c64 = gz.Context([p.N], gz.default_params(precision=gz.GZ_FP64), stream=stream)
