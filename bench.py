@@ -45,10 +45,11 @@ FLOPS_PER_DENSITY_TERM = 24     # density pass, per (particle, evaluation, neigh
 FLOPS_PER_GRAD_NEIGHBOUR = 127  # gradient pass, per (particle, neighbour)
 FLOPS_PER_GRAD_PARTICLE = 60    # gradient pass, per particle
 # DRAM bytes (read + write) per work unit of each kernel, from the ncu capture
-# summarised in TRAFFIC_SOURCE (64^3 turbulence, scaled by units); empty
-# until a capture of the current kernels is recorded
-TRAFFIC_PER_UNIT = {}
-TRAFFIC_SOURCE = None
+# summarised in TRAFFIC_SOURCE (64^3 turbulence, one launch each), scaled to a
+# launch by the work units of the run; to be emptied whenever one of these
+# kernels changes after that capture
+TRAFFIC_PER_UNIT = {"density": 1.02, "gradients": 8.33, "fluxes": 23.1}
+TRAFFIC_SOURCE = "profiles/kernels_turb64_fp32.md (64^3 capture, scaled by work units)"
 SMS, FP32_LANES = 152, 128
 
 
