@@ -71,6 +71,23 @@ def parse():
     return ap.parse_args()
 
 
+def replica_aggregate(ms_local, dist=None, device="cpu"):
+    """Max over ranks of the per-rank timings (each rank runs an independent
+    replica of the workload; the slowest bounds the job).  ms_local: list of
+    floats; returns the list of maxima (the input itself without dist)."""
+    if dist is None:
+        return list(ms_local)
+    import torch
+    t = torch.tensor(ms_local, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def replica_rate(world, n_per_rank, steps, ms_max):
+    """Whole-job particle-updates/s: all ranks' particles over the slowest rank's time."""
+    return world * n_per_rank * steps / (ms_max / 1e3)
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -217,11 +234,9 @@ def run_ours(a, world, rank, local):
         extras = {} if a.no_extras else measure_extras(a, ctx, d, dtu, stream, prec, p)
     tmax = ms
     if dist:
-        tt = torch.tensor([ms, ms_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tmax, ms_e2e = float(tt[0]), float(tt[1])
-    value = world * N * a.steps / (tmax / 1e3)
-    e2e = world * N * a.e2e_steps / (ms_e2e / 1e3) if a.e2e_steps > 0 else None
+        tmax, ms_e2e = replica_aggregate([ms, ms_e2e], dist, "cuda")
+    value = replica_rate(world, N, a.steps, tmax)
+    e2e = replica_rate(world, N, a.e2e_steps, ms_e2e) if a.e2e_steps > 0 else None
     # roofline: each pair pass against the FP32 ALU peak, by its algorithmic
     # FLOP (counted on the oracle's routines); the dominant one by time is
     # the headline entry
