@@ -47,7 +47,7 @@ class Params(C.Structure):
                 ("cfl", C.c_double), ("kappa_max", C.c_double), ("beta", C.c_double),
                 ("u_floor_frac", C.c_double), ("h_lim", C.c_double),
                 ("hancock", C.c_int32), ("max_iter", C.c_int32), ("use_cells", C.c_int32),
-                ("pad", C.c_int32)]
+                ("scheme", C.c_int32)]
 
 
 class Counters(C.Structure):
@@ -59,10 +59,14 @@ class Counters(C.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+MFM, MFV = 0, 1
+
+
 def params(gamma=5.0 / 3.0, ngb=32.0, tol=1e-6, cfl=0.2, kappa_max=100.0, beta=1.0,
-           u_floor_frac=1e-10, h_lim=0.5, hancock=1, max_iter=64, use_cells=1) -> Params:
+           u_floor_frac=1e-10, h_lim=0.5, hancock=1, max_iter=64, use_cells=1,
+           scheme=MFM) -> Params:
     return Params(gamma, ngb, tol, cfl, kappa_max, beta, u_floor_frac, h_lim, hancock,
-                  max_iter, use_cells, 0)
+                  max_iter, use_cells, scheme)
 
 
 _D = C.POINTER(C.c_double)
@@ -100,18 +104,20 @@ def _load():
             lib.gzo_timestep.restype = C.c_int
             lib.gzo_timestep.argtypes = [i64] + [vp] * 11 + [vp, C.POINTER(Params), vp, _D]
             lib.gzo_fluxes.restype = C.c_int
-            lib.gzo_fluxes.argtypes = [i64] + [vp] * 13 + [d, vp, C.POINTER(Params), vp, vp,
+            lib.gzo_fluxes.argtypes = [i64] + [vp] * 13 + [d, vp, C.POINTER(Params), vp, vp, vp,
                                                          C.POINTER(Counters)]
             lib.gzo_update.restype = C.c_int
-            lib.gzo_update.argtypes = [i64] + [vp] * 10 + [d, C.POINTER(Params),
+            lib.gzo_update.argtypes = [i64] + [vp] * 11 + [d, C.POINTER(Params),
                                                          C.POINTER(Counters)]
             lib.gzo_step.restype = C.c_int
-            lib.gzo_step.argtypes = [i64] + [vp] * 10 + [C.POINTER(Params), _D, vp, vp, vp,
+            lib.gzo_step.argtypes = [i64] + [vp] * 10 + [C.POINTER(Params), _D, vp, vp, vp, vp,
                                                        C.POINTER(Counters)]
             lib.gzo_pair.restype = C.c_int
             lib.gzo_pair.argtypes = [vp, d, d, vp, vp, vp, vp, d, d, vp, vp, vp, d,
-                                     C.POINTER(Params), vp, _D, _D, vp, vp, _D,
+                                     C.POINTER(Params), vp, _D, _D, vp, vp, _D, _D,
                                      C.POINTER(C.c_int)]
+            lib.gzo_hllc_flux.restype = None
+            lib.gzo_hllc_flux.argtypes = [vp, vp, vp, vp, d, _D, vp, _D]
             lib.gzo_hllc.restype = None
             lib.gzo_hllc.argtypes = [d] * 7 + [_D, _D]
             lib.gzo_riemann_star.restype = C.c_int
@@ -254,41 +260,51 @@ def timestep(s: State, H, n, p: Params, mask=None):
     return dti, dt.value
 
 
-def fluxes(s: State, H, n, grad, B, dt, p: Params, mask=None, counters: Counters | None = None):
-    """O10-O12: returns (dpdt [3,N], dEdt [N])."""
+def fluxes(s: State, H, n, grad, B, dt, p: Params, mask=None, counters: Counters | None = None,
+           with_mass: bool = False):
+    """O10-O12: returns (dpdt [3,N], dEdt [N]), and dmdt [N] with with_mass."""
     N = s.N
     dp = np.zeros((3, N))
     dE = np.zeros(N)
+    dm = np.zeros(N)
     mk = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
     cnt = counters if counters is not None else Counters()
     _load().gzo_fluxes(N, _p(s.x), _p(s.y), _p(s.z), _p(s.id), _p(s.m), _p(_f64(H)),
                        _p(_f64(n)), _p(s.vx), _p(s.vy), _p(s.vz), _p(s.u), _p(_f64(grad)),
-                       _p(_f64(B)), float(dt), _p(mk), C.byref(p), _p(dp), _p(dE), C.byref(cnt))
-    return dp, dE
+                       _p(_f64(B)), float(dt), _p(mk), C.byref(p), _p(dp), _p(dE), _p(dm),
+                       C.byref(cnt))
+    return (dp, dE, dm) if with_mass else (dp, dE)
 
 
-def update(s: State, dpdt, dEdt, dt, p: Params, counters: Counters | None = None) -> State:
-    """O14 on a copy of the state; returns the new state."""
+def update(s: State, dpdt, dEdt, dt, p: Params, counters: Counters | None = None,
+           dmdt=None) -> State:
+    """O14 on a copy of the state (masses too when dmdt is given); returns it."""
     o = s.copy()
     cnt = counters if counters is not None else Counters()
     _load().gzo_update(o.N, _p(o.x), _p(o.y), _p(o.z), _p(o.vx), _p(o.vy), _p(o.vz), _p(o.m),
-                       _p(o.u), _p(_f64(dpdt)), _p(_f64(dEdt)), float(dt), C.byref(p),
+                       _p(o.u), _p(_f64(dpdt)), _p(_f64(dEdt)),
+                       None if dmdt is None else _p(_f64(dmdt)), float(dt), C.byref(p),
                        C.byref(cnt))
     return o
 
 
-def step(s: State, p: Params, dt: float = 0.0, counters: Counters | None = None):
-    """O4..O14 on a copy; returns (new_state, dt_used, n, dpdt, dEdt)."""
+def step(s: State, p: Params, dt: float = 0.0, counters: Counters | None = None,
+         with_mass: bool = False):
+    """O4..O14 on a copy; returns (new_state, dt_used, n, dpdt, dEdt), and dmdt
+    after them with with_mass (the MFV mass rates; zero under MFM)."""
     o = s.copy()
     N = o.N
     n = np.zeros(N)
     dp = np.zeros((3, N))
     dE = np.zeros(N)
+    dm = np.zeros(N)
     dtc = C.c_double(float(dt))
     cnt = counters if counters is not None else Counters()
     _load().gzo_step(N, _p(o.x), _p(o.y), _p(o.z), _p(o.vx), _p(o.vy), _p(o.vz), _p(o.m),
                      _p(o.u), _p(o.H), _p(o.id), C.byref(p), C.byref(dtc), _p(n), _p(dp),
-                     _p(dE), C.byref(cnt))
+                     _p(dE), _p(dm), C.byref(cnt))
+    if with_mass:
+        return o, dtc.value, n, dp, dE, dm
     return o, dtc.value, n, dp, dE
 
 
@@ -297,15 +313,25 @@ def pair(L: dict, R: dict, dt: float, p: Params):
     A = np.zeros(3)
     vf = np.zeros(3)
     dp = np.zeros(3)
-    ps, ss, dE = C.c_double(), C.c_double(), C.c_double()
+    ps, ss, dE, dm = C.c_double(), C.c_double(), C.c_double(), C.c_double()
     fl = C.c_int()
     arrs = [_f64(L[k]) for k in ("x", "W", "g", "B")] + [_f64(R[k]) for k in ("x", "W", "g", "B")]
     ok = _load().gzo_pair(_p(arrs[0]), float(L["H"]), float(L["n"]), _p(arrs[1]), _p(arrs[2]),
                           _p(arrs[3]), _p(arrs[4]), float(R["H"]), float(R["n"]), _p(arrs[5]),
                           _p(arrs[6]), _p(arrs[7]), float(dt), C.byref(p), _p(A), C.byref(ps),
-                          C.byref(ss), _p(vf), _p(dp), C.byref(dE), C.byref(fl))
+                          C.byref(ss), _p(vf), _p(dp), C.byref(dE), C.byref(dm), C.byref(fl))
     return {"ok": ok, "A": A, "pstar": ps.value, "sstar": ss.value, "vf": vf, "dp": dp,
-            "dE": dE.value, "flags": fl.value}
+            "dE": dE.value, "dm": dm.value, "flags": fl.value}
+
+
+def hllc_flux(FL, FR, vf, nh, gamma):
+    """MFV face flux: (mass, momentum [3], energy) flux densities, lab frame."""
+    Fp = np.zeros(3)
+    Fm, FE = C.c_double(), C.c_double()
+    a = [_f64(v) for v in (FL, FR, vf, nh)]
+    _load().gzo_hllc_flux(_p(a[0]), _p(a[1]), _p(a[2]), _p(a[3]), float(gamma), C.byref(Fm), _p(Fp),
+                          C.byref(FE))
+    return Fm.value, Fp, FE.value
 
 
 def hllc(rhoL, uL, PL, rhoR, uR, PR, gamma):

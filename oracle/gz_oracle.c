@@ -615,6 +615,76 @@ void gzo_hllc(double rhoL, double uL, double PL, double rhoR, double uR, double 
     *pstar = PL + rhoL * (SL - uL) * (ss - uL);
 }
 
+/* MFV: the face moves with vf; in its frame (w = v - vf, u = w . n) the
+ * conserved state is U = (rho, rho w, E) with E = P/(g-1) + rho |w|^2 / 2 and
+ * the flux along n is F(U) = (rho u, rho u w + P n, u (E + P)).  HLLC takes
+ * F_L, F*_L = F_L + S_L (U*_L - U_L), F*_R, F_R on the four sides of the waves
+ * S_L, S*, S_R (Davis speeds, S* as in gzo_hllc), with the star states
+ * U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, w_K + (S* - u_K) n,
+ * E_K/rho_K + (S* - u_K)(S* + P_K/(rho_K (S_K - u_K)))); the face flux is the
+ * one at xi = 0.  Back to the lab frame: mass F_rho, momentum F_w + vf F_rho,
+ * energy F_E + vf . F_w + |vf|^2 F_rho / 2. */
+void gzo_hllc_flux(const double* FL, const double* FR, const double* vf, const double* nh,
+                   double gamma, double* Fm, double* Fp, double* FE) {
+    const double* S[2] = {FL, FR};
+    double rho[2], w[2][3], un[2], P[2], E[2], c[2];
+    for (int k = 0; k < 2; ++k) {
+        rho[k] = S[k][0];
+        P[k] = S[k][4];
+        for (int a = 0; a < 3; ++a) w[k][a] = S[k][1 + a] - vf[a];
+        un[k] = (w[k][0] * nh[0] + w[k][1] * nh[1]) + w[k][2] * nh[2];
+        double w2 = (w[k][0] * w[k][0] + w[k][1] * w[k][1]) + w[k][2] * w[k][2];
+        E[k] = P[k] / (gamma - 1.0) + 0.5 * rho[k] * w2;
+        c[k] = sqrt(gamma * P[k] / rho[k]);
+    }
+    double a = un[0] - c[0], b = un[1] - c[1];
+    double SL = a < b ? a : b;
+    double a2 = un[0] + c[0], b2 = un[1] + c[1];
+    double SR = a2 > b2 ? a2 : b2;
+    double num = P[1] - P[0] + rho[0] * un[0] * (SL - un[0]) - rho[1] * un[1] * (SR - un[1]);
+    double den = rho[0] * (SL - un[0]) - rho[1] * (SR - un[1]);
+    double ss = num / den;
+    int k;        /* side whose physical flux is used */
+    int star;     /* 1: add S_K (U*_K - U_K) */
+    if (SL >= 0.0) {
+        k = 0;
+        star = 0;
+    } else if (ss >= 0.0) {
+        k = 0;
+        star = 1;
+    } else if (SR > 0.0) {
+        k = 1;
+        star = 1;
+    } else {
+        k = 1;
+        star = 0;
+    }
+    double fr = rho[k] * un[k];
+    double fw[3], fe = un[k] * (E[k] + P[k]);
+    for (int q = 0; q < 3; ++q) fw[q] = rho[k] * un[k] * w[k][q] + P[k] * nh[q];
+    if (star) {
+        double SK = k == 0 ? SL : SR;
+        double f = rho[k] * (SK - un[k]) / (SK - ss);
+        double Us[5], U[5];
+        U[0] = rho[k];
+        Us[0] = f;
+        for (int q = 0; q < 3; ++q) {
+            U[1 + q] = rho[k] * w[k][q];
+            Us[1 + q] = f * (w[k][q] + (ss - un[k]) * nh[q]);
+        }
+        U[4] = E[k];
+        Us[4] = f * (E[k] / rho[k] + (ss - un[k]) * (ss + P[k] / (rho[k] * (SK - un[k]))));
+        fr += SK * (Us[0] - U[0]);
+        for (int q = 0; q < 3; ++q) fw[q] += SK * (Us[1 + q] - U[1 + q]);
+        fe += SK * (Us[4] - U[4]);
+    }
+    double vfw = (vf[0] * fw[0] + vf[1] * fw[1]) + vf[2] * fw[2];
+    double vf2 = (vf[0] * vf[0] + vf[1] * vf[1]) + vf[2] * vf[2];
+    *Fm = fr;
+    for (int q = 0; q < 3; ++q) Fp[q] = fw[q] + vf[q] * fr;
+    *FE = fe + vfw + 0.5 * vf2 * fr;
+}
+
 static inline double clampd(double v, double lo, double hi) {
     return v < lo ? lo : (v > hi ? hi : v);
 }
@@ -634,7 +704,7 @@ int gzo_pair(const double* xL, double HL, double nL, const double* WL, const dou
              const double* BL, const double* xR, double HR, double nR, const double* WR,
              const double* gR, const double* BR, double dt, const gzo_params* p,
              double* A, double* pstar, double* sstar, double* vf, double* dp, double* dE,
-             int* flags) {
+             double* dm, int* flags) {
     double d[3];
     for (int a = 0; a < 3; ++a) d[a] = gzo_min_image(xR[a] - xL[a]);
     double r2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
@@ -653,6 +723,7 @@ int gzo_pair(const double* xL, double HL, double nL, const double* WL, const dou
     double Amag = sqrt((A[0] * A[0] + A[1] * A[1]) + A[2] * A[2]);
     dp[0] = dp[1] = dp[2] = 0.0;
     *dE = 0.0;
+    *dm = 0.0;
     *pstar = 0.0;
     *sstar = 0.0;
     double s = HL / (HL + HR);
@@ -705,6 +776,14 @@ int gzo_pair(const double* xL, double HL, double nL, const double* WL, const dou
     }
     *pstar = ps;
     *sstar = ss;
+    if (p->scheme == 1) { /* MFV: full HLLC flux through the face moving with vf */
+        double Fm, Fp[3], FE;
+        gzo_hllc_flux(FL, FR, vf, nh, p->gamma, &Fm, Fp, &FE);
+        *dm = -Fm * Amag;
+        for (int a = 0; a < 3; ++a) dp[a] = -Fp[a] * Amag;
+        *dE = -FE * Amag;
+        return 1;
+    }
     for (int a = 0; a < 3; ++a) dp[a] = -ps * A[a];
     *dE = -ps * (ss + vfn) * Amag;
     return 1;
@@ -727,7 +806,8 @@ int gzo_fluxes(int64_t N, const double* x, const double* y, const double* z,
                const int64_t* id, const double* m, const double* H, const double* n,
                const double* vx, const double* vy, const double* vz, const double* u,
                const double* grad, const double* B, double dt, const uint8_t* mask,
-               const gzo_params* p, double* dpdt, double* dEdt, gzo_counters* cnt) {
+               const gzo_params* p, double* dpdt, double* dEdt, double* dmdt,
+               gzo_counters* cnt) {
     finder_t fd;
     finder_init(&fd, N, x, y, z, id, p->use_cells, median_cell_len(H, N));
     const double Hmax = max_of(H, N);
@@ -740,7 +820,7 @@ int gzo_fluxes(int64_t N, const double* x, const double* y, const double* z,
             if (mask && !mask[i]) continue;
             const int64_t* list;
             int64_t cntj = gather(&fd, &s, i, Hmax > H[i] ? Hmax : H[i], &list);
-            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
             double d[3];
             for (int64_t k = 0; k < cntj; ++k) {
                 int64_t j = list[k];
@@ -752,10 +832,10 @@ int gzo_fluxes(int64_t N, const double* x, const double* y, const double* z,
                 double pL[3], pR[3], WL[5], WR[5], gL[15], gR[15], BL[6], BR[6];
                 load_side(L, x, y, z, m, n, vx, vy, vz, u, grad, B, N, p->gamma, pL, WL, gL, BL);
                 load_side(R, x, y, z, m, n, vx, vy, vz, u, grad, B, N, p->gamma, pR, WR, gR, BR);
-                double A[3], ps, ss, vf[3], dp[3], dE;
+                double A[3], ps, ss, vf[3], dp[3], dE, dm;
                 int fl;
                 gzo_pair(pL, H[L], n[L], WL, gL, BL, pR, H[R], n[R], WR, gR, BR, dt, p, A, &ps,
-                         &ss, vf, dp, &dE, &fl);
+                         &ss, vf, dp, &dE, &dm, &fl);
                 if (fl & 1) nfall++;
                 if (fl & 2) nneg++;
                 double sg = (i == L) ? 1.0 : -1.0;
@@ -763,11 +843,13 @@ int gzo_fluxes(int64_t N, const double* x, const double* y, const double* z,
                 acc[1] += sg * dp[1];
                 acc[2] += sg * dp[2];
                 acc[3] += sg * dE;
+                acc[4] += sg * dm;
             }
             dpdt[i] = acc[0];
             dpdt[N + i] = acc[1];
             dpdt[2 * N + i] = acc[2];
             dEdt[i] = acc[3];
+            if (dmdt) dmdt[i] = acc[4];
         }
         scratch_free(&s);
     }
@@ -797,18 +879,20 @@ static double wrap1(double v) {
 }
 
 int gzo_update(int64_t N, double* x, double* y, double* z, double* vx, double* vy,
-               double* vz, const double* m, double* u, const double* dpdt,
-               const double* dEdt, double dt, const gzo_params* p, gzo_counters* cnt) {
+               double* vz, double* m, double* u, const double* dpdt, const double* dEdt,
+               const double* dmdt, double dt, const gzo_params* p, gzo_counters* cnt) {
+    /* with dmdt (MFV) m <- m + dt dm/dt and p, E are divided by the new m */
     double umed = 0.0;
     int need_floor = 0;
     for (int64_t i = 0; i < N && !need_floor; ++i) {
+        double mn = dmdt ? m[i] + dt * dmdt[i] : m[i];
         double px = m[i] * vx[i] + dt * dpdt[i];
         double py = m[i] * vy[i] + dt * dpdt[N + i];
         double pz = m[i] * vz[i] + dt * dpdt[2 * N + i];
         double v2 = (vx[i] * vx[i] + vy[i] * vy[i]) + vz[i] * vz[i];
         double E = m[i] * (u[i] + 0.5 * v2) + dt * dEdt[i];
-        double nx = px / m[i], ny = py / m[i], nz = pz / m[i];
-        double un = E / m[i] - 0.5 * ((nx * nx + ny * ny) + nz * nz);
+        double nx = px / mn, ny = py / mn, nz = pz / mn;
+        double un = E / mn - 0.5 * ((nx * nx + ny * ny) + nz * nz);
         if (!(un > 0.0)) need_floor = 1;
     }
     if (need_floor && N > 0) {
@@ -818,36 +902,42 @@ int gzo_update(int64_t N, double* x, double* y, double* z, double* vx, double* v
         umed = tmp[(N - 1) / 2];
         free(tmp);
     }
-    int64_t nfl = 0;
+    int64_t nfl = 0, nbad = 0;
     for (int64_t i = 0; i < N; ++i) {
+        double mn = dmdt ? m[i] + dt * dmdt[i] : m[i];
         double v2 = (vx[i] * vx[i] + vy[i] * vy[i]) + vz[i] * vz[i];
         double E = m[i] * (u[i] + 0.5 * v2) + dt * dEdt[i];
         double px = m[i] * vx[i] + dt * dpdt[i];
         double py = m[i] * vy[i] + dt * dpdt[N + i];
         double pz = m[i] * vz[i] + dt * dpdt[2 * N + i];
-        double nx = px / m[i], ny = py / m[i], nz = pz / m[i];
+        double nx = px / mn, ny = py / mn, nz = pz / mn;
         x[i] = wrap1(x[i] + dt * (0.5 * (vx[i] + nx)));
         y[i] = wrap1(y[i] + dt * (0.5 * (vy[i] + ny)));
         z[i] = wrap1(z[i] + dt * (0.5 * (vz[i] + nz)));
-        double un = E / m[i] - 0.5 * ((nx * nx + ny * ny) + nz * nz);
+        double un = E / mn - 0.5 * ((nx * nx + ny * ny) + nz * nz);
         if (!(un > 0.0)) {
             un = p->u_floor_frac * umed;
             nfl++;
         }
+        if (!(mn > 0.0)) nbad++;
         vx[i] = nx;
         vy[i] = ny;
         vz[i] = nz;
         u[i] = un;
+        if (dmdt) m[i] = mn;
     }
-    if (cnt) cnt->ufloor += nfl;
+    if (cnt) {
+        cnt->ufloor += nfl;
+        cnt->nonfinite += nbad;
+    }
     return 0;
 }
 
 /* ------------------------------------------------------------ step ------ */
 int gzo_step(int64_t N, double* x, double* y, double* z, double* vx, double* vy,
-             double* vz, const double* m, double* u, double* H, const int64_t* id,
+             double* vz, double* m, double* u, double* H, const int64_t* id,
              const gzo_params* p, double* dt_inout, double* n_out, double* dpdt,
-             double* dEdt, gzo_counters* cnt) {
+             double* dEdt, double* dmdt, gzo_counters* cnt) {
     size_t sz = sizeof(double) * (size_t)(N > 0 ? N : 1);
     double* Hn = (double*)malloc(sz);
     double* n = n_out ? n_out : (double*)malloc(sz);
@@ -856,14 +946,15 @@ int gzo_step(int64_t N, double* x, double* y, double* z, double* vx, double* vy,
     double* B = (double*)malloc(sz * 6);
     double* dp = dpdt ? dpdt : (double*)malloc(sz * 3);
     double* dE = dEdt ? dEdt : (double*)malloc(sz);
+    double* dm = p->scheme == 1 ? (dmdt ? dmdt : (double*)malloc(sz)) : NULL;
     gzo_density(N, x, y, z, id, H, NULL, p, Hn, n, it, NULL, cnt);
     memcpy(H, Hn, sz);
     gzo_gradients(N, x, y, z, id, m, H, n, vx, vy, vz, u, NULL, p, grad, B, NULL, NULL, NULL,
                   cnt);
     double dt = *dt_inout;
     if (!(dt > 0.0)) gzo_timestep(N, x, y, z, id, m, H, n, vx, vy, vz, u, NULL, p, NULL, &dt);
-    gzo_fluxes(N, x, y, z, id, m, H, n, vx, vy, vz, u, grad, B, dt, NULL, p, dp, dE, cnt);
-    gzo_update(N, x, y, z, vx, vy, vz, m, u, dp, dE, dt, p, cnt);
+    gzo_fluxes(N, x, y, z, id, m, H, n, vx, vy, vz, u, grad, B, dt, NULL, p, dp, dE, dm, cnt);
+    gzo_update(N, x, y, z, vx, vy, vz, m, u, dp, dE, dm, dt, p, cnt);
     *dt_inout = dt;
     free(Hn);
     if (!n_out) free(n);
@@ -872,6 +963,8 @@ int gzo_step(int64_t N, double* x, double* y, double* z, double* vx, double* vy,
     free(B);
     if (!dpdt) free(dp);
     if (!dEdt) free(dE);
+    if (dm && !dmdt) free(dm);
+    if (dmdt && p->scheme != 1) memset(dmdt, 0, sz);
     return 0;
 }
 

@@ -36,7 +36,9 @@ typedef struct {
     int32_t hancock;     /* 1: add the half-step predictor to face states     */
     int32_t max_iter;    /* cap on f-evaluations of the h-iteration           */
     int32_t use_cells;   /* 0: brute-force neighbours; 1: cell list           */
-    int32_t pad;
+    int32_t scheme;      /* 0: MFM (faces move with the contact, no mass      */
+                         /*    flux); 1: MFV (faces move with v_f, HLLC mass,  */
+                         /*    momentum and energy fluxes; masses evolve)      */
 } gzo_params;
 
 typedef struct {
@@ -94,36 +96,47 @@ int gzo_timestep(int64_t N, const double* x, const double* y, const double* z,
                  const double* vx, const double* vy, const double* vz, const double* u,
                  const uint8_t* mask, const gzo_params* p, double* dt_i, double* dt_min);
 
-/* O10-O12: MFM fluxes summed into dp/dt [3][N] and dE/dt [N]. */
+/* O10-O12: fluxes summed into dp/dt [3][N], dE/dt [N] and (MFV; may be
+ * NULL) dm/dt [N]. */
 int gzo_fluxes(int64_t N, const double* x, const double* y, const double* z,
                const int64_t* id, const double* m, const double* H, const double* n,
                const double* vx, const double* vy, const double* vz, const double* u,
                const double* grad, const double* B, double dt, const uint8_t* mask,
-               const gzo_params* p, double* dpdt, double* dEdt, gzo_counters* cnt);
+               const gzo_params* p, double* dpdt, double* dEdt, double* dmdt,
+               gzo_counters* cnt);
 
-/* O14: kick, trapezoid drift, periodic wrap, u floor. */
+/* O14: kick, trapezoid drift, periodic wrap, u floor; with dmdt (MFV) the
+ * masses are advanced too (m is then written). */
 int gzo_update(int64_t N, double* x, double* y, double* z, double* vx, double* vy,
-               double* vz, const double* m, double* u, const double* dpdt,
-               const double* dEdt, double dt, const gzo_params* p, gzo_counters* cnt);
+               double* vz, double* m, double* u, const double* dpdt, const double* dEdt,
+               const double* dmdt, double dt, const gzo_params* p, gzo_counters* cnt);
 
 /* Whole step O4..O14.  State arrays are updated in place (H becomes the
- * converged support radius used in this step).  *dt_inout <= 0 requests the
- * CFL step; the step used is written back.  n_out, dpdt, dEdt optional. */
+ * converged support radius used in this step; m changes under MFV).
+ * *dt_inout <= 0 requests the CFL step; the step used is written back.
+ * n_out, dpdt, dEdt, dmdt optional. */
 int gzo_step(int64_t N, double* x, double* y, double* z, double* vx, double* vy,
-             double* vz, const double* m, double* u, double* H, const int64_t* id,
+             double* vz, double* m, double* u, double* H, const int64_t* id,
              const gzo_params* p, double* dt_inout, double* n_out, double* dpdt,
-             double* dEdt, gzo_counters* cnt);
+             double* dEdt, double* dmdt, gzo_counters* cnt);
 
 /* One face evaluation in canonical (L, R) order for pins: inputs are the
  * two particles' positions, H, n, primitives (rho, vx, vy, vz, P), limited
  * gradients [15] and B [6].  Outputs the face area vector A[3], P*, S*,
  * the face-frame velocity vf[3], and the L-side rate contributions
- * dp[3], dE (R receives the negatives).  Returns 0 if |A| = 0. */
+ * dp[3], dE and dm (zero under MFM; R receives the negatives).  Returns 0 if
+ * |A| = 0. */
 int gzo_pair(const double* xL, double HL, double nL, const double* WL, const double* gL,
              const double* BL, const double* xR, double HR, double nR, const double* WR,
              const double* gR, const double* BR, double dt, const gzo_params* p,
              double* A, double* pstar, double* sstar, double* vf, double* dp, double* dE,
-             int* flags);
+             double* dm, int* flags);
+
+/* MFV face flux (HLLC, Davis speeds) for face states FL, FR (rho, v[3], P,
+ * lab frame) through a face moving with vf, unit normal nh from L to R:
+ * lab-frame mass, momentum [3] and energy flux densities. */
+void gzo_hllc_flux(const double* FL, const double* FR, const double* vf, const double* nh,
+                   double gamma, double* Fm, double* Fp, double* FE);
 
 /* O12 HLLC (Davis wave speeds) on 1-D states along the face normal. */
 void gzo_hllc(double rhoL, double uL, double PL, double rhoR, double uR, double PR,
