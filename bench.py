@@ -66,8 +66,9 @@ def parse():
     ap.add_argument("--cell-factor", type=float, default=None)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-path, adjoint and ensemble measurements")
-    ap.add_argument("--extras", default="all", choices=["all", "adjoint"],
-                    help="which extra measurements to run (adjoint: only the adjoint cost)")
+    ap.add_argument("--extras", default="all", choices=["all", "adjoint", "mfv"],
+                    help="which extra measurements to run (adjoint: only the adjoint cost; "
+                         "mfv: only the MFV-scheme throughput)")
     return ap.parse_args()
 
 
@@ -291,6 +292,8 @@ def run_ours(a, world, rank, local):
     line.update(extras)
     if "fp64_path" in line:
         line["fp64_path"]["fp32_over_fp64"] = round(value / world / line["fp64_path"]["value"], 2)
+    if "mfv" in line:
+        line["mfv"]["ms_over_mfm"] = round(line["mfv"]["ms_per_step"] / (tmax / a.steps), 3)
     if "adjoint" in line:
         adj = line["adjoint"]
         adj["forward_ms_per_step"] = round(tmax / a.steps, 4)
@@ -301,7 +304,8 @@ def run_ours(a, world, rank, local):
 
 
 def measure_extras(a, ctx, d, dtu, stream, prec, p):
-    """FP64-path throughput, adjoint cost and the batched ensemble (CUDA graph)."""
+    """Adjoint cost, MFV-scheme throughput, the evolved state, FP64-path throughput
+    and the batched ensemble (CUDA graph)."""
     import numpy as np
     import torch
 
@@ -311,62 +315,91 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p):
     out = {}
     ev = lambda: torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
-        # adjoint of one step (same workload, same precision), dt frozen, in the
-        # configuration MFMStep runs it: the forward fills the step checkpoint
-        # (gz_step_checkpoint: rates and the gradient pass's per-particle
-        # outputs) and returns the converged H; the backward recomputes the
-        # sort, density and pair-list passes and every pair quantity
-        rng = np.random.default_rng(0)
-        T = d["x"].dtype
-        start = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in d.items()}
-        level = gz.GZ_CKPT_GRADIENTS
-        ck = ctx.new_checkpoint(level)
-        K = max(2, a.steps // 2)
-        fwd = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in start.items()}
-        ctx.step(fwd, 0.0, dtu, ck, level)
-        e0, e1 = ev(), ev()
-        e0.record(stream)
-        for _ in range(K):
+        if a.extras in ("all", "adjoint"):
+            # adjoint of one step (same workload, same precision), dt frozen, in the
+            # configuration MFMStep runs it: the forward fills the step checkpoint
+            # (gz_step_checkpoint: rates and the gradient pass's per-particle
+            # outputs) and returns the converged H; the backward recomputes the
+            # sort, density and pair-list passes and every pair quantity
+            rng = np.random.default_rng(0)
+            T = d["x"].dtype
+            start = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in d.items()}
+            level = gz.GZ_CKPT_GRADIENTS
+            ck = ctx.new_checkpoint(level)
+            K = max(2, a.steps // 2)
+            fwd = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in start.items()}
             ctx.step(fwd, 0.0, dtu, ck, level)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_fwd_ckpt = e0.elapsed_time(e1) / K
-        fwd = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in start.items()}
-        ctx.step(fwd, 0.0, dtu, ck, level)
-        dt = float(dtu.item())
-        ckstate = dict(start)
-        ckstate["h"] = fwd["h"]
-        gend = {k: torch.as_tensor(rng.normal(size=p.N), dtype=T).cuda() for k in
-                ("x", "y", "z", "vx", "vy", "vz", "u")}
-        gstart = {k: torch.zeros(p.N, dtype=T, device="cuda") for k in
-                  ("x", "y", "z", "vx", "vy", "vz", "u", "m")}
-        ctx.step_backward(ckstate, dt, gend, gstart, ck, level)
-        e0, e1 = ev(), ev()
-        e0.record(stream)
-        for _ in range(K):
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            for _ in range(K):
+                ctx.step(fwd, 0.0, dtu, ck, level)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_fwd_ckpt = e0.elapsed_time(e1) / K
+            fwd = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in start.items()}
+            ctx.step(fwd, 0.0, dtu, ck, level)
+            dt = float(dtu.item())
+            ckstate = dict(start)
+            ckstate["h"] = fwd["h"]
+            gend = {k: torch.as_tensor(rng.normal(size=p.N), dtype=T).cuda() for k in
+                    ("x", "y", "z", "vx", "vy", "vz", "u")}
+            gstart = {k: torch.zeros(p.N, dtype=T, device="cuda") for k in
+                      ("x", "y", "z", "vx", "vy", "vz", "u", "m")}
             ctx.step_backward(ckstate, dt, gend, gstart, ck, level)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_bwd = e0.elapsed_time(e1) / K
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            for _ in range(K):
+                ctx.step_backward(ckstate, dt, gend, gstart, ck, level)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_bwd = e0.elapsed_time(e1) / K
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            for _ in range(K):
+                ctx.step_backward(start, dt, gend, gstart)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_bwd_full = e0.elapsed_time(e1) / K
+            st = ctx.status(reset=True)
+            out["adjoint"] = {"backward_ms_per_step": round(ms_bwd, 4),
+                              "forward_with_checkpoint_ms_per_step": round(ms_fwd_ckpt, 4),
+                              "checkpoint_bytes_per_particle": round(ctx.checkpoint_bytes(level) / p.N, 1),
+                              "backward_full_recompute_ms_per_step": round(ms_bwd_full, 4),
+                              "steps": K, "status_ok": st["ok"],
+                              "what": "gz_step_backward from the MFMStep checkpoint (start state, "
+                                      "converged H, rates and gradient-pass outputs): sort, density, "
+                                      "pair lists and all pair quantities recomputed, then the adjoint "
+                                      "passes"}
+            del ck
+        if a.extras == "adjoint":
+            return out
+        # the MFV scheme (mass fluxes through moving faces) on the same
+        # workload and precision: full steps, per-pass split
+        cm = gz.Context([p.N], gz.default_params(precision=prec, scheme=gz.GZ_MFV,
+                                                 **({"cell_factor": a.cell_factor} if a.cell_factor else {})),
+                        stream=stream)
+        dm_ = gz.to_device(p, prec)
+        for _ in range(3):
+            cm.step(dm_, 0.0, dtu)
+        cm.profile(True)
+        K = max(3, a.steps)
         e0, e1 = ev(), ev()
         e0.record(stream)
         for _ in range(K):
-            ctx.step_backward(start, dt, gend, gstart)
+            cm.step(dm_, 0.0, dtu)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms_bwd_full = e0.elapsed_time(e1) / K
-        st = ctx.status(reset=True)
-        out["adjoint"] = {"backward_ms_per_step": round(ms_bwd, 4),
-                          "forward_with_checkpoint_ms_per_step": round(ms_fwd_ckpt, 4),
-                          "checkpoint_bytes_per_particle": round(ctx.checkpoint_bytes(level) / p.N, 1),
-                          "backward_full_recompute_ms_per_step": round(ms_bwd_full, 4),
-                          "steps": K, "status_ok": st["ok"],
-                          "what": "gz_step_backward from the MFMStep checkpoint (start state, "
-                                  "converged H, rates and gradient-pass outputs): sort, density, "
-                                  "pair lists and all pair quantities recomputed, then the adjoint "
-                                  "passes"}
-        del ck
-        if a.extras == "adjoint":
+        prof_m = cm.profile_read(reset=True)
+        cm.profile(False)
+        ms_m = e0.elapsed_time(e1) / K
+        out["mfv"] = {"value": round(p.N / (ms_m / 1e3), 1), "unit": UNIT,
+                      "ms_per_step": round(ms_m, 4), "steps": K, "steps_before": 3,
+                      "status_ok": cm.status(reset=True)["ok"],
+                      "pass_ms_per_step": {k: round(v[0] / max(v[1], 1), 4)
+                                           for k, v in prof_m.items() if v[1]}}
+        cm.close()
+        del dm_
+        if a.extras == "mfv":
             return out
         # the same box further on: 20 more steps from the state the e2e loop
         # left (one step from the initial state), when the particles have left

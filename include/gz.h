@@ -26,6 +26,13 @@
  *   O13 dt = cfl * min_i 2 V_i^(1/3) / max_j v_sig,ij
  *   O14 kick, trapezoid drift, periodic wrap, u floor
  *
+ * gz_params.scheme selects GZ_MFM (above) or GZ_MFV, the paper's meshless
+ * finite-volume variant, where mass also moves across the faces:
+ *   O15 HLLC flux of mass, momentum and total energy through the face moving
+ *       with v_f (star states of the face frame, boosted back to the lab
+ *       frame); dm_i/dt = -sum F_m |A_ij|, dp_i/dt = -sum F_p |A_ij|,
+ *       dE_i/dt = -sum F_E |A_ij|; the update advances m too.
+ *
  * Conventions
  *   - Every call returns a gz_status; no exception or abort crosses the ABI.
  *     Calls are asynchronous on the context's CUDA stream; conditions found
@@ -87,6 +94,10 @@ typedef int32_t gz_status;
 #define GZ_C_KAPPA_FP64 7
 #define GZ_NCOUNTERS 8
 
+/* Schemes (gz_params.scheme). */
+#define GZ_MFM 0 /* meshless finite mass: particle masses fixed (O12)             */
+#define GZ_MFV 1 /* meshless finite volume: mass fluxes between particles (O15)   */
+
 /* Precision modes. */
 #define GZ_FP64 0    /* every step in double                                          */
 #define GZ_MIXED32 1 /* float state and pair math; double for the Newton update of H,
@@ -107,6 +118,8 @@ typedef struct {
     int32_t hancock;     /* 1: half-step predictor on face states (1)                */
     int32_t max_iter;    /* cap on f evaluations of the h-iteration (64)             */
     int32_t max_ngb;     /* capacity of each particle's neighbour list (128)         */
+    int32_t scheme;      /* GZ_MFM or GZ_MFV (GZ_MFM)                                 */
+    int32_t reserved;    /* must be 0                                                 */
 } gz_params;
 
 /* Structure-of-arrays particle set; every pointer is device memory with N
@@ -163,18 +176,22 @@ gz_status gz_gradients(gz_ctx* ctx, const gz_particles* p, const void* n, void* 
 gz_status gz_timestep(gz_ctx* ctx, const gz_particles* p, const void* n, double* dt_i_out,
                       double* dt_box_out);
 
-/* O10-O12 with the given H, n, limited gradients grad ([15][N]) and B
- * ([6][N]) and half-step time dt (the Hancock predictor uses dt/2): writes
- * dp/dt to dpdt ([3][N] doubles) and dE/dt to dEdt ([N] doubles). */
+/* O10-O12 (O15 under GZ_MFV) with the given H, n, limited gradients grad
+ * ([15][N]) and B ([6][N]) and half-step time dt (the Hancock predictor uses
+ * dt/2): writes dp/dt to dpdt ([3][N] doubles), dE/dt to dEdt ([N]
+ * doubles) and, if dmdt is non-NULL, dm/dt to dmdt ([N] doubles; zeros
+ * under GZ_MFM). */
 gz_status gz_hydro_fluxes(gz_ctx* ctx, const gz_particles* p, const void* n, const void* grad,
-                          const void* B, double dt, double* dpdt, double* dEdt);
+                          const void* B, double dt, double* dpdt, double* dEdt, double* dmdt);
 
 /* Adjoint of gz_hydro_fluxes with the same frozen inputs (H, n, grad, B,
  * dt; neighbour and pair sets of those H): given dpdt_bar ([3][N]) and
  * dEdt_bar ([N]) = dL/d(rates), writes dL/d(inputs) as double arrays:
  * x_bar [3][N] (positions), h_bar [N], n_bar [N], W_bar [5][N] (rho, vx,
  * vy, vz, P), grad_bar [15][N], B_bar [6][N].  Any output may be NULL.
- * min/max/clamp pass the adjoint to the branch the forward took. */
+ * min/max/clamp pass the adjoint to the branch the forward took.  The adjoint
+ * covers GZ_MFM only: under GZ_MFV this call, gz_step_checkpoint and
+ * gz_step_backward return GZ_E_INVAL. */
 gz_status gz_hydro_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const void* n,
                                    const void* grad, const void* B, double dt,
                                    const double* dpdt_bar, const double* dEdt_bar, double* x_bar,
@@ -182,7 +199,8 @@ gz_status gz_hydro_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const voi
                                    double* B_bar);
 
 /* One full step O4-O14 in place on p (x, y, z, vx, vy, vz, u, h updated;
- * m and id read only).  dt_fixed > 0 uses that step for every box;
+ * under GZ_MFV m too (O15), where a mass that is not positive after the
+ * update sets GZ_S_NONFINITE; id read only).  dt_fixed > 0 uses that step for every box;
  * otherwise each box takes its CFL step.  dt_used_dev (device, nboxes
  * doubles, may be NULL) receives the steps used.  No host synchronisation. */
 gz_status gz_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev);

@@ -17,7 +17,7 @@ import ctypes as C
 import os
 import threading
 
-__all__ = ["GZ_FP64", "GZ_MIXED32", "Params", "Context", "GZError", "load_library",
+__all__ = ["GZ_FP64", "GZ_MIXED32", "GZ_MFM", "GZ_MFV", "Params", "Context", "GZError", "load_library",
            "default_params", "status_names"]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(HERE, "libgz.so")
 
 GZ_OK, GZ_E_INVAL, GZ_E_NOMEM, GZ_E_CUDA, GZ_E_DEVICE = 0, 1, 2, 3, 4
 GZ_FP64, GZ_MIXED32 = 0, 1
+GZ_MFM, GZ_MFV = 0, 1
 GZ_CKPT_RATES, GZ_CKPT_GRADIENTS = 0, 1
 STATUS_BITS = {
     "hconv": 1 << 0, "singular": 1 << 1, "nonfinite": 1 << 2, "nbr_overflow": 1 << 3,
@@ -47,7 +48,8 @@ class Params(C.Structure):
                 ("cfl", C.c_double), ("kappa_max", C.c_double), ("beta", C.c_double),
                 ("u_floor_frac", C.c_double), ("h_lim", C.c_double),
                 ("cell_factor", C.c_double), ("precision", C.c_int32), ("hancock", C.c_int32),
-                ("max_iter", C.c_int32), ("max_ngb", C.c_int32)]
+                ("max_iter", C.c_int32), ("max_ngb", C.c_int32), ("scheme", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class _Particles(C.Structure):
@@ -80,7 +82,7 @@ def load_library(build_if_missing: bool = True):
             "gz_density": (st, [vp, P, vp, vp]),
             "gz_gradients": (st, [vp, P, vp, vp, vp]),
             "gz_timestep": (st, [vp, P, vp, vp, vp]),
-            "gz_hydro_fluxes": (st, [vp, P, vp, vp, vp, d, vp, vp]),
+            "gz_hydro_fluxes": (st, [vp, P, vp, vp, vp, d, vp, vp, vp]),
             "gz_step": (st, [vp, P, d, vp]),
             "gz_hydro_fluxes_backward": (st, [vp, P, vp, vp, vp, d, vp, vp, vp, vp, vp, vp, vp, vp]),
             "gz_graph_capture": (st, [vp, P, i32, d, vp]),
@@ -212,14 +214,17 @@ class Context:
                     "gz_timestep")
         return dti, dtb
 
-    def hydro_fluxes(self, p, n, grad, B, dt, dpdt=None, dEdt=None):
-        """gz_hydro_fluxes: returns (dpdt [3,N], dEdt [N]) in float64."""
+    def hydro_fluxes(self, p, n, grad, B, dt, dpdt=None, dEdt=None, with_mass=False):
+        """gz_hydro_fluxes: returns (dpdt [3,N], dEdt [N]) in float64, and dmdt [N]
+        third when with_mass (zeros under GZ_MFM)."""
         dpdt = self.empty(3, self.N, dtype=self.torch.float64) if dpdt is None else dpdt
         dEdt = self.empty(self.N, dtype=self.torch.float64) if dEdt is None else dEdt
+        dmdt = self.empty(self.N, dtype=self.torch.float64) if with_mass else None
         s = self._parts(p)
         self._check(self.lib.gz_hydro_fluxes(self.h, C.byref(s), _ptr(n), _ptr(grad), _ptr(B),
-                                             float(dt), _ptr(dpdt), _ptr(dEdt)), "gz_hydro_fluxes")
-        return dpdt, dEdt
+                                             float(dt), _ptr(dpdt), _ptr(dEdt), _ptr(dmdt)),
+                    "gz_hydro_fluxes")
+        return (dpdt, dEdt, dmdt) if with_mass else (dpdt, dEdt)
 
     def hydro_fluxes_backward(self, p, n, grad, B, dt, dpdt_bar, dEdt_bar):
         """gz_hydro_fluxes_backward: dict of float64 adjoints x [3,N], h, n, W [5,N],

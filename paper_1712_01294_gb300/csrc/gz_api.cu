@@ -44,6 +44,8 @@ bool params_ok(const gz_params* p, std::string& why) {
         return why = "precision must be GZ_FP64 or GZ_MIXED32", false;
     if (p->max_iter < 1) return why = "max_iter must be >= 1", false;
     if (p->max_ngb < 8 || p->max_ngb > 4096) return why = "max_ngb must be in [8, 4096]", false;
+    if (p->scheme != GZ_MFM && p->scheme != GZ_MFV) return why = "scheme must be GZ_MFM or GZ_MFV", false;
+    if (p->reserved != 0) return why = "reserved must be 0", false;
     return true;
 }
 
@@ -163,7 +165,7 @@ gz_status do_timestep(gz_ctx* ctx, const gz_particles* p, const void* n, double*
 
 template <typename T>
 gz_status do_fluxes(gz_ctx* ctx, const gz_particles* p, const void* n, const void* grad,
-                    const void* B, double dt, double* dpdt, double* dEdt) {
+                    const void* B, double dt, double* dpdt, double* dEdt, double* dmdt) {
     gz_status s = prepare_given<T>(ctx, p, n, true);
     if (s) return s;
     Ctx& c = ctx->c;
@@ -175,6 +177,12 @@ gz_status do_fluxes(gz_ctx* ctx, const gz_particles* p, const void* n, const voi
     }
     if (e == cudaSuccess) e = unpermute_d(c, c.dpdt, dpdt, 3);
     if (e == cudaSuccess) e = unpermute_d(c, c.dEdt, dEdt, 1);
+    if (e == cudaSuccess && dmdt) {
+        if (c.dmdt)
+            e = unpermute_d(c, c.dmdt, dmdt, 1);
+        else
+            e = cudaMemsetAsync(dmdt, 0, sizeof(double) * (size_t)c.N, c.stream);
+    }
     return cuda_check(ctx, e, "gz_hydro_fluxes");
 }
 
@@ -450,6 +458,7 @@ gz_status gz_create(const gz_params* params, int32_t nboxes, const int64_t* coun
         {(void**)&c.rcount, 4 * Nz},      {(void**)&c.rnbr, 4 * Nz * (size_t)c.rcap},
         {(void**)&c.rec, sz * Nz * kRecord},
         {(void**)&c.dpdt, 8 * 3 * Nz},    {(void**)&c.dEdt, 8 * Nz},
+        {(void**)&c.dmdt, params->scheme == GZ_MFV ? 8 * Nz : 0},
         {(void**)&c.dti, 8 * Nz},         {(void**)&c.dt_box, 8 * (size_t)nboxes},
         {(void**)&c.dt_use, 8 * (size_t)nboxes},
         {(void**)&c.box_hits, 4 * (size_t)nboxes},
@@ -466,7 +475,7 @@ gz_status gz_create(const gz_params* params, int32_t nboxes, const int64_t* coun
     }
     char* base = (char*)c.arena;
     for (auto& it : items) {
-        *it.ptr = base;
+        *it.ptr = it.bytes ? base : nullptr;
         base += (it.bytes + 255) & ~(size_t)255;
     }
     std::vector<int> box_of(Nz);
@@ -535,13 +544,13 @@ gz_status gz_timestep(gz_ctx* ctx, const gz_particles* p, const void* n, double*
 }
 
 gz_status gz_hydro_fluxes(gz_ctx* ctx, const gz_particles* p, const void* n, const void* grad,
-                          const void* B, double dt, double* dpdt, double* dEdt) {
+                          const void* B, double dt, double* dpdt, double* dEdt, double* dmdt) {
     if (!ctx) return GZ_E_INVAL;
     if (gz_status s = check_particles(ctx, p, true)) return s;
     if (!n || !grad || !B || !dpdt || !dEdt) return fail(ctx, GZ_E_INVAL, "null input/output");
     if (!(dt >= 0.0) || !isfinite(dt)) return fail(ctx, GZ_E_INVAL, "dt must be finite and >= 0");
-    return GZ_DISPATCH(do_fluxes<float>(ctx, p, n, grad, B, dt, dpdt, dEdt),
-                       do_fluxes<double>(ctx, p, n, grad, B, dt, dpdt, dEdt));
+    return GZ_DISPATCH(do_fluxes<float>(ctx, p, n, grad, B, dt, dpdt, dEdt, dmdt),
+                       do_fluxes<double>(ctx, p, n, grad, B, dt, dpdt, dEdt, dmdt));
 }
 
 gz_status gz_hydro_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const void* n,
@@ -552,6 +561,7 @@ gz_status gz_hydro_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const voi
     if (!ctx) return GZ_E_INVAL;
     if (gz_status s = check_particles(ctx, p, true)) return s;
     if (!n || !grad || !B || !dpdt_bar || !dEdt_bar) return fail(ctx, GZ_E_INVAL, "null input");
+    if (ctx->c.params.scheme != GZ_MFM) return fail(ctx, GZ_E_INVAL, "the adjoint covers GZ_MFM only");
     if (!(dt >= 0.0) || !isfinite(dt)) return fail(ctx, GZ_E_INVAL, "dt must be finite and >= 0");
     return GZ_DISPATCH(do_fluxes_backward<float>(ctx, p, n, grad, B, dt, dpdt_bar, dEdt_bar, x_bar, h_bar,
                                                  n_bar, W_bar, grad_bar, B_bar),
@@ -580,6 +590,7 @@ gz_status gz_step_checkpoint(gz_ctx* ctx, gz_particles* p, double dt_fixed, doub
     if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
     if (!ckpt || ((uintptr_t)ckpt & 255) || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS)
         return fail(ctx, GZ_E_INVAL, "checkpoint: need a 256-byte aligned buffer and a valid level");
+    if (ctx->c.params.scheme != GZ_MFM) return fail(ctx, GZ_E_INVAL, "the adjoint covers GZ_MFM only");
     const Ckpt ck = ckpt_view(ctx->c, ckpt, level);
     return GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev, ck),
                        do_step<double>(ctx, p, dt_fixed, dt_used_dev, ck));
@@ -641,6 +652,7 @@ gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt, 
     if (gz_status s = check_particles(ctx, p_start, true)) return s;
     if (!gbar_end || !gbar_start) return fail(ctx, GZ_E_INVAL, "null adjoint set");
     if (!(dt > 0.0) || !isfinite(dt)) return fail(ctx, GZ_E_INVAL, "dt must be finite and > 0");
+    if (ctx->c.params.scheme != GZ_MFM) return fail(ctx, GZ_E_INVAL, "the adjoint covers GZ_MFM only");
     if (ckpt && (((uintptr_t)ckpt & 255) || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS))
         return fail(ctx, GZ_E_INVAL, "checkpoint: need a 256-byte aligned buffer and a valid level");
     const Ckpt ck = ckpt_view(ctx->c, const_cast<void*>(ckpt), level);

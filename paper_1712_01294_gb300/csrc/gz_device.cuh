@@ -160,12 +160,63 @@ __device__ __forceinline__ void load4(const double* src, double (&v)[4]) {
     v[3] = w1.y;
 }
 
-// Contribution of the pair (a, b) to particle a's rates: dp (3) and dE.
-// Returns false when the face area vanishes.  flags: 1 fallback, 2 P* < 0.
+// O15: HLLC flux of mass, momentum and total energy through a face that
+// moves with vf (unit normal n from L to R), from the face states FL, FR
+// (rho, v, P) and the wave speeds the caller already formed in the face
+// frame (u_K = (v_K - vf) . n, S_L, S_R, S*).  In that frame w = v - vf,
+// U = (rho, rho w, E) with E = P/(gamma-1) + rho |w|^2/2 and the flux along n
+// is F(U) = (rho u, rho u w + P n, u (E + P)).  The flux at the face (xi = 0)
+// is F_K or F_K + S_K (U*_K - U_K) for the side K the waves leave it on, with
+// the star state U*_K = rho_K (S_K - u_K)/(S_K - S*) (1, w_K + (S* - u_K) n,
+// E_K/rho_K + (S* - u_K)(S* + P_K/(rho_K (S_K - u_K)))).  With q = 1/(S_K - S*),
+// g = rho_K q, f = g (S_K - u_K) and dS = S* - u_K the jump S_K (U*_K - U_K)
+// is S_K dS (g, g w_K + f n, q (E_K + P_K) + f S*), the same quantity without
+// the cancellation of U*_K - U_K for weak waves.  Back in the lab frame the
+// fluxes are F_m, F_w + vf F_m and F_E + vf . F_w + |vf|^2 F_m / 2.
 template <typename T>
+__device__ __forceinline__ void mfv_flux(const T (&FL)[5], const T (&FR)[5], T uL, T uR, T SL, T SR,
+                                         T ss, T vfx, T vfy, T vfz, T nx, T ny, T nz, T gam, T& Fm,
+                                         T (&Fp)[3], T& FE) {
+    // side: L when S_L >= 0 or S* >= 0; the star jump unless S_L >= 0 (L) or
+    // S_R <= 0 (R); a NaN speed takes R without the jump, like the oracle
+    const bool left = SL >= T(0) || ss >= T(0);
+    const bool star = left ? !(SL >= T(0)) : SR > T(0);
+    const T rho = left ? FL[0] : FR[0];
+    const T P = left ? FL[4] : FR[4];
+    const T un = left ? uL : uR;
+    const T wx = (left ? FL[1] : FR[1]) - vfx;
+    const T wy = (left ? FL[2] : FR[2]) - vfy;
+    const T wz = (left ? FL[3] : FR[3]) - vfz;
+    const T E = pdiv(P, gam - T(1)) + T(0.5) * rho * ((wx * wx + wy * wy) + wz * wz);
+    const T ru = rho * un;
+    T fr = ru;
+    T fx = ru * wx + P * nx, fy = ru * wy + P * ny, fz = ru * wz + P * nz;
+    T fe = un * (E + P);
+    if (star) {
+        const T SK = left ? SL : SR;
+        const T q = pdiv(T(1), SK - ss);
+        const T g = rho * q, f = g * (SK - un);
+        const T k = SK * (ss - un);
+        fr += k * g;
+        fx += k * (g * wx + f * nx);
+        fy += k * (g * wy + f * ny);
+        fz += k * (g * wz + f * nz);
+        fe += k * (q * (E + P) + f * ss);
+    }
+    Fm = fr;
+    Fp[0] = fx + vfx * fr;
+    Fp[1] = fy + vfy * fr;
+    Fp[2] = fz + vfz * fr;
+    FE = (fe + ((vfx * fx + vfy * fy) + vfz * fz)) + T(0.5) * ((vfx * vfx + vfy * vfy) + vfz * vfz) * fr;
+}
+
+// Contribution of the pair (a, b) to particle a's rates: dp (3), dE and,
+// under MFV (O15), dm.  Returns false when the face area vanishes.  flags:
+// 1 fallback, 2 P* < 0.
+template <typename T, bool kMFV>
 __device__ __forceinline__ bool pair_rates(const T (&a)[kRecord], const T (&b)[kRecord], bool aL,
                                            T hdt, T gam, bool hancock, const T (&inca)[5], T (&dp)[3],
-                                           T& dE, int& fl) {
+                                           T& dE, T& dm, int& fl) {
     const T dx = mi_diff(b[0], a[0], a[0] - T(1));
     const T dy = mi_diff(b[1], a[1], a[1] - T(1));
     const T dz = mi_diff(b[2], a[2], a[2] - T(1));
@@ -237,6 +288,21 @@ __device__ __forceinline__ bool pair_rates(const T (&a)[kRecord], const T (&b)[k
         ps = T(0);
         fl |= 2;
     }
+    if constexpr (kMFV) {
+        // both particles of the pair form the same canonical flux bits; L
+        // loses what R gains
+        T Fm, Fp[3], FE;
+        mfv_flux(FL, FR, uL, uR, SL, SR, ss, vfx, vfy, vfz, nx, ny, nz, gam, Fm, Fp, FE);
+        const T m = mul_rn(Fm, Am), px = mul_rn(Fp[0], Am), py = mul_rn(Fp[1], Am),
+                pz = mul_rn(Fp[2], Am), e = mul_rn(FE, Am);
+        dm = aL ? -m : m;
+        dp[0] = aL ? -px : px;
+        dp[1] = aL ? -py : py;
+        dp[2] = aL ? -pz : pz;
+        dE = aL ? -e : e;
+        return true;
+    }
+    dm = T(0);
     dp[0] = -mul_rn(ps, A0);
     dp[1] = -mul_rn(ps, A1);
     dp[2] = -mul_rn(ps, A2);
@@ -289,6 +355,49 @@ __device__ __forceinline__ void update_one(float m, float& x, float& y, float& z
     vx += dvx;
     vy += dvy;
     vz += dvz;
+}
+
+// MFV (O15): the mass advances too, m' = m + dt dm/dt, and momentum and
+// total energy are divided by m'.  FP64 state: the literal form, like the
+// oracle.
+__device__ __forceinline__ void update_one_mfv(double& m, double& x, double& y, double& z, double& vx,
+                                               double& vy, double& vz, double& u, double dpx, double dpy,
+                                               double dpz, double dE, double dm, double dt) {
+    const double mn = m + dt * dm;
+    const double v2 = (vx * vx + vy * vy) + vz * vz;
+    const double E = m * (u + 0.5 * v2) + dt * dE;
+    const double nx = (m * vx + dt * dpx) / mn, ny = (m * vy + dt * dpy) / mn, nz = (m * vz + dt * dpz) / mn;
+    x = wrap1(x + dt * (0.5 * (vx + nx)));
+    y = wrap1(y + dt * (0.5 * (vy + ny)));
+    z = wrap1(z + dt * (0.5 * (vz + nz)));
+    u = E / mn - 0.5 * ((nx * nx + ny * ny) + nz * nz);
+    vx = nx;
+    vy = ny;
+    vz = nz;
+    m = mn;
+}
+// FP32 state: with dM = dt dm/dt, m' = m + dM (formed in FP64) and the
+// increments dv = (dt dp/dt - dM v)/m' and
+// du = (dt dE/dt - dM (u + v^2/2))/m' - dv . (v + dv/2), which equal
+// p'/m' - v and E'/m' - v'^2/2 - u without the cancellation of the literal form.
+__device__ __forceinline__ void update_one_mfv(float& m, float& x, float& y, float& z, float& vx,
+                                               float& vy, float& vz, float& u, double dpx, double dpy,
+                                               double dpz, double dE, double dm, double dt) {
+    const float mn = (float)((double)m + dt * dm);
+    const float dtf = (float)dt, im = 1.f / mn, dM = dtf * (float)dm;
+    const float dvx = (dtf * (float)dpx - dM * vx) * im, dvy = (dtf * (float)dpy - dM * vy) * im,
+                dvz = (dtf * (float)dpz - dM * vz) * im;
+    const float hx = vx + 0.5f * dvx, hy = vy + 0.5f * dvy, hz = vz + 0.5f * dvz;
+    const float ek = u + 0.5f * ((vx * vx + vy * vy) + vz * vz);
+    const float du = (dtf * (float)dE - dM * ek) * im - ((dvx * hx + dvy * hy) + dvz * hz);
+    x = wrapf(x + dtf * hx);
+    y = wrapf(y + dtf * hy);
+    z = wrapf(z + dtf * hz);
+    u = u + du;
+    vx += dvx;
+    vy += dvy;
+    vz += dvz;
+    m = mn;
 }
 
 }  // namespace gz

@@ -625,16 +625,18 @@ __global__ void k_grad_out(int N, const unsigned* __restrict__ orig, const T* __
 // One thread per particle over its pairs N_i then R_i (both contiguous
 // lists, read four indices per 16-byte load).  Contributions are summed in
 // the working precision over runs of 8 pairs and each run is added to FP64
-// accumulators.
+// accumulators.  kMFV: the MFV fluxes (O15), which add dm/dt.
 constexpr int kFluxBlock = 128;
 
-template <typename T>
+template <typename T, bool kMFV>
 __global__ void __launch_bounds__(kFluxBlock)
     k_fluxes(int N, const T* __restrict__ rec, const long long* __restrict__ sid,
              const int* __restrict__ sbox, const unsigned* __restrict__ nbr,
              const int* __restrict__ ncount, const unsigned* __restrict__ rnbr,
              const int* __restrict__ rcount, KParams p, const double* __restrict__ dt_use,
-             double* __restrict__ dpdt, double* __restrict__ dEdt, DevStatus* st) {
+             double* __restrict__ dpdt, double* __restrict__ dEdt, double* __restrict__ dmdt,
+             DevStatus* st) {
+    constexpr int nq = kMFV ? 5 : 4;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     T a[kRecord];
@@ -645,8 +647,13 @@ __global__ void __launch_bounds__(kFluxBlock)
     const bool hancock = p.hancock != 0;
     T inca[5];
     hancock_inc(a, hdt, gam, hancock, inca);
-    T part[4] = {T(0), T(0), T(0), T(0)};
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    T part[nq];
+    double acc[nq];
+#pragma unroll
+    for (int q = 0; q < nq; ++q) {
+        part[q] = T(0);
+        acc[q] = 0.0;
+    }
     int np = 0, nfall = 0, nneg = 0;
 #pragma unroll 1
     for (int list = 0; list < 2; ++list) {
@@ -661,19 +668,20 @@ __global__ void __launch_bounds__(kFluxBlock)
                 const int j = (int)js[u];
                 T b[kRecord];
                 load_rec(rec + (size_t)j * kRecord, b);
-                T dp[3], dE;
+                T dp[3], dE, dm;
                 int fl = 0;
-                if (pair_rates(a, b, idi < sid[j], hdt, gam, hancock, inca, dp, dE, fl)) {
+                if (pair_rates<T, kMFV>(a, b, idi < sid[j], hdt, gam, hancock, inca, dp, dE, dm, fl)) {
                     part[0] += dp[0];
                     part[1] += dp[1];
                     part[2] += dp[2];
                     part[3] += dE;
+                    if constexpr (kMFV) part[4] += dm;
                 }
                 nfall += fl & 1;
                 nneg += (fl >> 1) & 1;
                 if (++np == 8) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                    for (int q = 0; q < nq; ++q) {
                         acc[q] += (double)part[q];
                         part[q] = T(0);
                     }
@@ -683,11 +691,12 @@ __global__ void __launch_bounds__(kFluxBlock)
         }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += (double)part[q];
+    for (int q = 0; q < nq; ++q) acc[q] += (double)part[q];
     dpdt[i] = acc[0];
     dpdt[(size_t)N + i] = acc[1];
     dpdt[2 * (size_t)N + i] = acc[2];
     dEdt[i] = acc[3];
+    if constexpr (kMFV) dmdt[i] = acc[4];
     if (nfall) {
         atomicOr(&st->bits, GZ_S_FALLBACK);
         atomicAdd(&st->counters[GZ_C_FALLBACK], (unsigned long long)nfall);
@@ -698,11 +707,12 @@ __global__ void __launch_bounds__(kFluxBlock)
     }
 }
 
+// dmdt (MFV, O15) non-null: the mass advances too and is written back.
 template <typename T>
 __global__ void k_update(int N, Sorted<T> s, const double* __restrict__ dpdt,
-                         const double* __restrict__ dEdt, const double* __restrict__ dt_use,
-                         gz_particles out, int* __restrict__ box_hits, DevStatus* st,
-                         double* __restrict__ rates_out) {
+                         const double* __restrict__ dEdt, const double* __restrict__ dmdt,
+                         const double* __restrict__ dt_use, gz_particles out,
+                         int* __restrict__ box_hits, DevStatus* st, double* __restrict__ rates_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const unsigned o = s.orig[i];
@@ -714,8 +724,17 @@ __global__ void k_update(int N, Sorted<T> s, const double* __restrict__ dpdt,
         rates_out[3 * (size_t)N + o] = dEdt[i];
     }
     T x = s.x[i], y = s.y[i], z = s.z[i], vx = s.vx[i], vy = s.vy[i], vz = s.vz[i], u = s.u[i];
-    update_one(s.m[i], x, y, z, vx, vy, vz, u, dpdt[i], dpdt[(size_t)N + i],
-               dpdt[2 * (size_t)N + i], dEdt[i], dt_use[b]);
+    bool mass_ok = true;
+    if (dmdt) {
+        T m = s.m[i];
+        update_one_mfv(m, x, y, z, vx, vy, vz, u, dpdt[i], dpdt[(size_t)N + i],
+                       dpdt[2 * (size_t)N + i], dEdt[i], dmdt[i], dt_use[b]);
+        ((T*)out.m)[o] = m;
+        mass_ok = m > T(0);
+    } else {
+        update_one(s.m[i], x, y, z, vx, vy, vz, u, dpdt[i], dpdt[(size_t)N + i],
+                   dpdt[2 * (size_t)N + i], dEdt[i], dt_use[b]);
+    }
     ((T*)out.x)[o] = x;
     ((T*)out.y)[o] = y;
     ((T*)out.z)[o] = z;
@@ -728,8 +747,8 @@ __global__ void k_update(int N, Sorted<T> s, const double* __restrict__ dpdt,
         atomicAdd(&box_hits[b], 1);
         set_status(st, GZ_S_UFLOOR, GZ_C_UFLOOR, -1);
     }
-    if (!(finite_(x) && finite_(y) && finite_(z) && finite_(vx) && finite_(vy) && finite_(vz) &&
-          finite_(u)))
+    if (!(mass_ok && finite_(x) && finite_(y) && finite_(z) && finite_(vx) && finite_(vy) &&
+          finite_(vz) && finite_(u)))
         set_status(st, GZ_S_NONFINITE, GZ_C_NONFINITE, s.id[i]);
 }
 
@@ -862,6 +881,7 @@ KParams kparams(const Ctx& c) {
     k.u_floor_frac = c.params.u_floor_frac;
     k.h_lim = c.params.h_lim;
     k.hancock = c.params.hancock;
+    k.scheme = c.params.scheme;
     k.max_iter = c.params.max_iter;
     k.cap = c.cap;
     k.rcap = c.rcap;
@@ -950,9 +970,14 @@ cudaError_t run_grad_out(Ctx& c, T* grad, T* B) {
 template <typename T>
 cudaError_t run_fluxes(Ctx& c) {
     c.launches += 1;
-    k_fluxes<T><<<blocks(c.N, kFluxBlock), kFluxBlock, 0, c.stream>>>(
-        c.N, (const T*)c.rec, c.sid, c.sbox, c.nbr, c.ncount, c.rnbr, c.rcount, kparams(c), c.dt_use,
-        c.dpdt, c.dEdt, c.status);
+    if (c.params.scheme == GZ_MFV)
+        k_fluxes<T, true><<<blocks(c.N, kFluxBlock), kFluxBlock, 0, c.stream>>>(
+            c.N, (const T*)c.rec, c.sid, c.sbox, c.nbr, c.ncount, c.rnbr, c.rcount, kparams(c), c.dt_use,
+            c.dpdt, c.dEdt, c.dmdt, c.status);
+    else
+        k_fluxes<T, false><<<blocks(c.N, kFluxBlock), kFluxBlock, 0, c.stream>>>(
+            c.N, (const T*)c.rec, c.sid, c.sbox, c.nbr, c.ncount, c.rnbr, c.rcount, kparams(c), c.dt_use,
+            c.dpdt, c.dEdt, nullptr, c.status);
     return cudaGetLastError();
 }
 
@@ -961,8 +986,9 @@ cudaError_t run_update(Ctx& c, gz_particles& p, double* rates_out) {
     c.launches += 2;
     int* hits = c.box_hits;
     cudaMemsetAsync(hits, 0, sizeof(int) * (size_t)c.nboxes, c.stream);
-    k_update<T><<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, sorted_view<T>(c), c.dpdt, c.dEdt,
-                                                         c.dt_use, p, hits, c.status, rates_out);
+    k_update<T><<<blocks(c.N, 256), 256, 0, c.stream>>>(
+        c.N, sorted_view<T>(c), c.dpdt, c.dEdt, c.params.scheme == GZ_MFV ? c.dmdt : nullptr, c.dt_use, p,
+        hits, c.status, rates_out);
     k_ufloor<T><<<c.nboxes, 1024, 0, c.stream>>>(sorted_view<T>(c), c.boxes, hits, p,
                                                   c.params.u_floor_frac);
     return cudaGetLastError();

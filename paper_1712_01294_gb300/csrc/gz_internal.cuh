@@ -39,7 +39,7 @@ struct BoxInfo {
 // Scalar parameters passed by value to kernels.
 struct KParams {
     double gamma, ngb, tol, cfl, kappa_max, beta, u_floor_frac, h_lim;
-    int hancock, max_iter, cap, rcap;
+    int hancock, max_iter, cap, rcap, scheme;
 };
 
 // Packed per-particle records (one 16-byte-aligned vector load each).
@@ -106,6 +106,7 @@ struct Ctx {
     void* rec;       // [N][kRecord] working precision
     double* dpdt;    // [3][N] sorted
     double* dEdt;    // [N] sorted
+    double* dmdt;    // [N] sorted (GZ_MFV only, else null)
     double* dti;     // [N] sorted
     double* dt_box;  // [nboxes] CFL minimum (before the cfl factor is applied: raw min)
     double* dt_use;  // [nboxes] step used

@@ -124,6 +124,7 @@ gz_status run(const gz_params* prm, int N, gz_particles* p, void* n_out, int32_t
     c.status = (DevStatus*)take(sizeof(DevStatus));
     // the density pass never touches these
     c.svx = c.svy = c.svz = c.sm = c.su = c.srho = c.sP = c.sc = c.ssd = nullptr;
+    c.dmdt = nullptr;
     c.sprim = c.sprim2 = nullptr;
     c.rcount = nullptr;
     c.rnbr = nullptr;
