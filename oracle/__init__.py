@@ -47,7 +47,7 @@ class Params(C.Structure):
                 ("cfl", C.c_double), ("kappa_max", C.c_double), ("beta", C.c_double),
                 ("u_floor_frac", C.c_double), ("h_lim", C.c_double),
                 ("hancock", C.c_int32), ("max_iter", C.c_int32), ("use_cells", C.c_int32),
-                ("scheme", C.c_int32)]
+                ("scheme", C.c_int32), ("riemann", C.c_int32), ("pad", C.c_int32)]
 
 
 class Counters(C.Structure):
@@ -60,13 +60,18 @@ class Counters(C.Structure):
 
 
 MFM, MFV = 0, 1
+HLLC, EXACT, EXACT_FALLBACK = 0, 1, 2  # MFM face solver (riemann)
 
 
 def params(gamma=5.0 / 3.0, ngb=32.0, tol=1e-6, cfl=0.2, kappa_max=100.0, beta=1.0,
            u_floor_frac=1e-10, h_lim=0.5, hancock=1, max_iter=64, use_cells=1,
-           scheme=MFM) -> Params:
+           scheme=MFM, riemann=HLLC) -> Params:
+    if riemann not in (HLLC, EXACT, EXACT_FALLBACK):
+        raise ValueError("riemann must be HLLC, EXACT or EXACT_FALLBACK")
+    if scheme == MFV and riemann != HLLC:
+        raise ValueError("the exact Riemann solver option covers the MFM face only")
     return Params(gamma, ngb, tol, cfl, kappa_max, beta, u_floor_frac, h_lim, hancock,
-                  max_iter, use_cells, scheme)
+                  max_iter, use_cells, scheme, riemann, 0)
 
 
 _D = C.POINTER(C.c_double)

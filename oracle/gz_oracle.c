@@ -699,7 +699,9 @@ static inline double clampd(double v, double lo, double hi) {
  * clamp each field to
  * [min(f_L, f_R), max(f_L, f_R)]; if rho or P <= 0 on a side use the
  * particle states.  O12: HLLC along n = A/|A| in the face frame; MFM rates
- * to L: dp = -P* A, dE = -P* (S* + v_f . n) |A|. */
+ * to L: dp = -P* A, dE = -P* (S* + v_f . n) |A|.  With riemann = 1 (every
+ * face) or 2 (faces where HLLC's P* < 0) the exact solver's star pressure and
+ * contact speed replace HLLC's P* and S*.  O15 (scheme = 1): the MFV fluxes. */
 int gzo_pair(const double* xL, double HL, double nL, const double* WL, const double* gL,
              const double* BL, const double* xR, double HR, double nR, const double* WR,
              const double* gR, const double* BR, double dt, const gzo_params* p,
@@ -770,10 +772,23 @@ int gzo_pair(const double* xL, double HL, double nL, const double* WL, const dou
     double uR = ((FR[1] - vf[0]) * nh[0] + (FR[2] - vf[1]) * nh[1]) + (FR[3] - vf[2]) * nh[2];
     double ss, ps;
     gzo_hllc(FL[0], uL, FL[4], FR[0], uR, FR[4], p->gamma, &ss, &ps);
-    if (ps < 0.0) {
-        ps = 0.0;
-        *flags |= 2;
+    int neg = ps < 0.0;
+    if (p->scheme == 0 && (p->riemann == 1 || (p->riemann == 2 && neg))) {
+        /* exact star state of the face-frame Riemann problem: P* and the contact
+         * speed u* take the places of HLLC's; a vacuum face carries P* = 0 */
+        double pe, ue;
+        if (gzo_riemann_star(FL[0], uL, FL[4], FR[0], uR, FR[4], p->gamma, &pe, &ue) == 0) {
+            ps = pe;
+            ss = ue;
+            if (p->riemann == 1) neg = 0;
+        } else {
+            ps = 0.0;
+            ss = 0.0;
+            neg = 1;
+        }
     }
+    if (neg) *flags |= 2;
+    if (ps < 0.0) ps = 0.0;
     *pstar = ps;
     *sstar = ss;
     if (p->scheme == 1) { /* MFV: full HLLC flux through the face moving with vf */

@@ -39,13 +39,19 @@ typedef struct {
     int32_t scheme;      /* 0: MFM (faces move with the contact, no mass      */
                          /*    flux); 1: MFV (faces move with v_f, HLLC mass,  */
                          /*    momentum and energy fluxes; masses evolve)      */
+    int32_t riemann;     /* MFM face solver: 0 HLLC; 1 exact (iterative star  */
+                         /*    pressure) on every face; 2 HLLC, exact where    */
+                         /*    HLLC's P* < 0                                   */
+    int32_t pad;
 } gzo_params;
 
 typedef struct {
     int64_t hconv;       /* particles whose h-iteration hit max_iter          */
     int64_t singular;    /* particles with det(E) <= 0 or kappa > 1e8         */
     int64_t fallback;    /* pair evaluations that fell back to first order    */
-    int64_t pstar_neg;   /* pair evaluations with P* < 0 clamped to 0         */
+    int64_t pstar_neg;   /* pair evaluations with HLLC P* < 0 (clamped to 0,  */
+                         /*    or replaced by the exact solver's under         */
+                         /*    riemann = 2) or a vacuum face (exact solver)    */
     int64_t ufloor;      /* particles whose u was floored in the update       */
     int64_t nonfinite;   /* non-finite inputs or outputs                      */
     int64_t kappa_big;   /* particles with kappa > kappa_max                  */

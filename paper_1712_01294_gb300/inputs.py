@@ -97,7 +97,10 @@ def _finish(x, y, z, vx, vy, vz, m, u, ngb=NGB, id0=0, meta=None) -> Particles:
 
 
 def sod(n: int = 32, seed: int = 1712, gamma: float = GAMMA, rho_l=1.0, p_l=1.0, rho_r=0.125,
-        p_r=0.1, jitter: float = 0.1) -> Particles:
+        p_r=0.1, jitter: float = 0.1, u_l: float = 0.0, u_r: float = 0.0) -> Particles:
+    """Shock tube along x: (rho_l, p_l, u_l) for x < 1/2, (rho_r, p_r, u_r) above
+    (u = x-velocity; u_l = -2, u_r = 2, rho = 1, p = 0.4 gives the strong double
+    rarefaction at x = 1/2 and, through the periodic wrap, a collision at x = 0)."""
     rng = np.random.default_rng(seed)
     x, y, z, _ = lattice(n, rng, jitter)
     N = x.size
@@ -107,9 +110,10 @@ def sod(n: int = 32, seed: int = 1712, gamma: float = GAMMA, rho_l=1.0, p_l=1.0,
     m = rho / N
     u = P / ((gamma - 1.0) * rho)
     zero = np.zeros(N)
-    return _finish(x, y, z, zero, zero.copy(), zero.copy(), m, u,
+    vx = np.where(left, u_l, u_r).astype(np.float64)
+    return _finish(x, y, z, vx, zero.copy(), zero.copy(), m, u,
                    meta=dict(kind="sod", n=n, seed=seed, rho_l=rho_l, p_l=p_l, rho_r=rho_r,
-                             p_r=p_r, gamma=gamma))
+                             p_r=p_r, gamma=gamma, u_l=u_l, u_r=u_r))
 
 
 def _deposit_weights(r: np.ndarray, R: float) -> np.ndarray:
