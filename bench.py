@@ -66,9 +66,9 @@ def parse():
     ap.add_argument("--cell-factor", type=float, default=None)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-path, adjoint and ensemble measurements")
-    ap.add_argument("--extras", default="all", choices=["all", "adjoint", "mfv"],
+    ap.add_argument("--extras", default="all", choices=["all", "adjoint", "variants"],
                     help="which extra measurements to run (adjoint: only the adjoint cost; "
-                         "mfv: only the MFV-scheme throughput)")
+                         "variants: only the MFV and exact-Riemann throughputs)")
     return ap.parse_args()
 
 
@@ -292,8 +292,9 @@ def run_ours(a, world, rank, local):
     line.update(extras)
     if "fp64_path" in line:
         line["fp64_path"]["fp32_over_fp64"] = round(value / world / line["fp64_path"]["value"], 2)
-    if "mfv" in line:
-        line["mfv"]["ms_over_mfm"] = round(line["mfv"]["ms_per_step"] / (tmax / a.steps), 3)
+    for key in ("mfv", "riemann_exact"):
+        if key in line:
+            line[key]["ms_over_mfm"] = round(line[key]["ms_per_step"] / (tmax / a.steps), 3)
     if "adjoint" in line:
         adj = line["adjoint"]
         adj["forward_ms_per_step"] = round(tmax / a.steps, 4)
@@ -304,7 +305,7 @@ def run_ours(a, world, rank, local):
 
 
 def measure_extras(a, ctx, d, dtu, stream, prec, p):
-    """Adjoint cost, MFV-scheme throughput, the evolved state, FP64-path throughput
+    """Adjoint cost, MFV and exact-Riemann throughputs, the evolved state, FP64-path throughput
     and the batched ensemble (CUDA graph)."""
     import numpy as np
     import torch
@@ -373,33 +374,36 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p):
             del ck
         if a.extras == "adjoint":
             return out
-        # the MFV scheme (mass fluxes through moving faces) on the same
-        # workload and precision: full steps, per-pass split
-        cm = gz.Context([p.N], gz.default_params(precision=prec, scheme=gz.GZ_MFV,
-                                                 **({"cell_factor": a.cell_factor} if a.cell_factor else {})),
-                        stream=stream)
-        dm_ = gz.to_device(p, prec)
-        for _ in range(3):
-            cm.step(dm_, 0.0, dtu)
-        cm.profile(True)
-        K = max(3, a.steps)
-        e0, e1 = ev(), ev()
-        e0.record(stream)
-        for _ in range(K):
-            cm.step(dm_, 0.0, dtu)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        prof_m = cm.profile_read(reset=True)
-        cm.profile(False)
-        ms_m = e0.elapsed_time(e1) / K
-        out["mfv"] = {"value": round(p.N / (ms_m / 1e3), 1), "unit": UNIT,
-                      "ms_per_step": round(ms_m, 4), "steps": K, "steps_before": 3,
-                      "status_ok": cm.status(reset=True)["ok"],
-                      "pass_ms_per_step": {k: round(v[0] / max(v[1], 1), 4)
-                                           for k, v in prof_m.items() if v[1]}}
-        cm.close()
-        del dm_
-        if a.extras == "mfv":
+        # the scheme variants on the same workload and precision: MFV (mass
+        # fluxes through moving faces) and the MFM face with the exact Riemann
+        # solver on every face; full steps, per-pass split
+        variants = (("mfv", {"scheme": gz.GZ_MFV}), ("riemann_exact", {"riemann": gz.GZ_RIEMANN_EXACT}))
+        for key, kw in variants:
+            if a.cell_factor:
+                kw = dict(kw, cell_factor=a.cell_factor)
+            cm = gz.Context([p.N], gz.default_params(precision=prec, **kw), stream=stream)
+            dv = gz.to_device(p, prec)
+            for _ in range(3):
+                cm.step(dv, 0.0, dtu)
+            cm.profile(True)
+            K = max(3, a.steps)
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            for _ in range(K):
+                cm.step(dv, 0.0, dtu)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            prof_m = cm.profile_read(reset=True)
+            cm.profile(False)
+            ms_m = e0.elapsed_time(e1) / K
+            out[key] = {"value": round(p.N / (ms_m / 1e3), 1), "unit": UNIT,
+                        "ms_per_step": round(ms_m, 4), "steps": K, "steps_before": 3,
+                        "status_ok": cm.status(reset=True)["ok"],
+                        "pass_ms_per_step": {k: round(v[0] / max(v[1], 1), 4)
+                                             for k, v in prof_m.items() if v[1]}}
+            cm.close()
+            del dv
+        if a.extras == "variants":
             return out
         # the same box further on: 20 more steps from the state the e2e loop
         # left (one step from the initial state), when the particles have left

@@ -78,7 +78,8 @@ typedef int32_t gz_status;
 #define GZ_S_HLIM (1u << 4)         /* support radius reached h_lim                 */
 /* Informational bits (counted, not errors): */
 #define GZ_S_FALLBACK (1u << 8)     /* first-order face states used (O11)           */
-#define GZ_S_PSTAR_NEG (1u << 9)    /* HLLC P* < 0 clamped to 0 (O12)               */
+#define GZ_S_PSTAR_NEG (1u << 9)    /* HLLC P* < 0 (O12; clamped to 0, or exact star
+                                       under GZ_RIEMANN_FALLBACK), or a vacuum face   */
 #define GZ_S_UFLOOR (1u << 10)      /* u floored after the update (O14)             */
 #define GZ_S_KAPPA_FP64 (1u << 11)  /* E re-inverted in FP64 (kappa > kappa_max)    */
 #define GZ_S_ERROR_MASK 0xFFu
@@ -97,6 +98,19 @@ typedef int32_t gz_status;
 /* Schemes (gz_params.scheme). */
 #define GZ_MFM 0 /* meshless finite mass: particle masses fixed (O12)             */
 #define GZ_MFV 1 /* meshless finite volume: mass fluxes between particles (O15)   */
+
+/* Riemann solvers of the MFM face (gz_params.riemann; O12).  EXACT: the
+ * exact star pressure and contact speed of the face-frame Riemann problem
+ * (safeguarded Newton iteration on the pressure function of each side:
+ * shock branch (p - P_K) sqrt(A_K/(p + B_K)), A_K = 2/((gamma+1) rho_K),
+ * B_K = (gamma-1)/(gamma+1) P_K; rarefaction branch
+ * 2 c_K/(gamma-1) ((p/P_K)^((gamma-1)/(2 gamma)) - 1)) replace HLLC's P* and
+ * S* on every face; a face whose fans open a vacuum carries P* = 0 and sets
+ * GZ_S_PSTAR_NEG.  FALLBACK: HLLC, and the exact star where HLLC's P* < 0
+ * (such faces still set GZ_S_PSTAR_NEG). */
+#define GZ_RIEMANN_HLLC 0
+#define GZ_RIEMANN_EXACT 1
+#define GZ_RIEMANN_FALLBACK 2
 
 /* Precision modes. */
 #define GZ_FP64 0    /* every step in double                                          */
@@ -119,7 +133,8 @@ typedef struct {
     int32_t max_iter;    /* cap on f evaluations of the h-iteration (64)             */
     int32_t max_ngb;     /* capacity of each particle's neighbour list (128)         */
     int32_t scheme;      /* GZ_MFM or GZ_MFV (GZ_MFM)                                 */
-    int32_t reserved;    /* must be 0                                                 */
+    int32_t riemann;     /* MFM face solver: GZ_RIEMANN_HLLC, _EXACT or _FALLBACK     */
+                         /* (GZ_RIEMANN_HLLC); GZ_MFV takes GZ_RIEMANN_HLLC only      */
 } gz_params;
 
 /* Structure-of-arrays particle set; every pointer is device memory with N
@@ -190,8 +205,8 @@ gz_status gz_hydro_fluxes(gz_ctx* ctx, const gz_particles* p, const void* n, con
  * x_bar [3][N] (positions), h_bar [N], n_bar [N], W_bar [5][N] (rho, vx,
  * vy, vz, P), grad_bar [15][N], B_bar [6][N].  Any output may be NULL.
  * min/max/clamp pass the adjoint to the branch the forward took.  The adjoint
- * covers GZ_MFM only: under GZ_MFV this call, gz_step_checkpoint and
- * gz_step_backward return GZ_E_INVAL. */
+ * covers GZ_MFM with GZ_RIEMANN_HLLC only: otherwise this call,
+ * gz_step_checkpoint and gz_step_backward return GZ_E_INVAL. */
 gz_status gz_hydro_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const void* n,
                                    const void* grad, const void* B, double dt,
                                    const double* dpdt_bar, const double* dEdt_bar, double* x_bar,

@@ -17,7 +17,8 @@ import ctypes as C
 import os
 import threading
 
-__all__ = ["GZ_FP64", "GZ_MIXED32", "GZ_MFM", "GZ_MFV", "Params", "Context", "GZError", "load_library",
+__all__ = ["GZ_FP64", "GZ_MIXED32", "GZ_MFM", "GZ_MFV", "GZ_RIEMANN_HLLC", "GZ_RIEMANN_EXACT",
+           "GZ_RIEMANN_FALLBACK", "Params", "Context", "GZError", "load_library",
            "default_params", "status_names"]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -26,6 +27,7 @@ LIB_PATH = os.path.join(HERE, "libgz.so")
 GZ_OK, GZ_E_INVAL, GZ_E_NOMEM, GZ_E_CUDA, GZ_E_DEVICE = 0, 1, 2, 3, 4
 GZ_FP64, GZ_MIXED32 = 0, 1
 GZ_MFM, GZ_MFV = 0, 1
+GZ_RIEMANN_HLLC, GZ_RIEMANN_EXACT, GZ_RIEMANN_FALLBACK = 0, 1, 2
 GZ_CKPT_RATES, GZ_CKPT_GRADIENTS = 0, 1
 STATUS_BITS = {
     "hconv": 1 << 0, "singular": 1 << 1, "nonfinite": 1 << 2, "nbr_overflow": 1 << 3,
@@ -49,7 +51,7 @@ class Params(C.Structure):
                 ("u_floor_frac", C.c_double), ("h_lim", C.c_double),
                 ("cell_factor", C.c_double), ("precision", C.c_int32), ("hancock", C.c_int32),
                 ("max_iter", C.c_int32), ("max_ngb", C.c_int32), ("scheme", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("riemann", C.c_int32)]
 
 
 class _Particles(C.Structure):

@@ -45,9 +45,15 @@ bool params_ok(const gz_params* p, std::string& why) {
     if (p->max_iter < 1) return why = "max_iter must be >= 1", false;
     if (p->max_ngb < 8 || p->max_ngb > 4096) return why = "max_ngb must be in [8, 4096]", false;
     if (p->scheme != GZ_MFM && p->scheme != GZ_MFV) return why = "scheme must be GZ_MFM or GZ_MFV", false;
-    if (p->reserved != 0) return why = "reserved must be 0", false;
+    if (p->riemann != GZ_RIEMANN_HLLC && p->riemann != GZ_RIEMANN_EXACT && p->riemann != GZ_RIEMANN_FALLBACK)
+        return why = "riemann must be GZ_RIEMANN_HLLC, _EXACT or _FALLBACK", false;
+    if (p->scheme == GZ_MFV && p->riemann != GZ_RIEMANN_HLLC)
+        return why = "GZ_MFV takes GZ_RIEMANN_HLLC only", false;
     return true;
 }
+
+// The hand-written adjoint differentiates the MFM face with the HLLC star.
+bool adjoint_covers(const gz_params& p) { return p.scheme == GZ_MFM && p.riemann == GZ_RIEMANN_HLLC; }
 
 int ceil_log2(long long v) {
     int b = 0;
@@ -561,7 +567,8 @@ gz_status gz_hydro_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const voi
     if (!ctx) return GZ_E_INVAL;
     if (gz_status s = check_particles(ctx, p, true)) return s;
     if (!n || !grad || !B || !dpdt_bar || !dEdt_bar) return fail(ctx, GZ_E_INVAL, "null input");
-    if (ctx->c.params.scheme != GZ_MFM) return fail(ctx, GZ_E_INVAL, "the adjoint covers GZ_MFM only");
+    if (!adjoint_covers(ctx->c.params))
+        return fail(ctx, GZ_E_INVAL, "the adjoint covers GZ_MFM with GZ_RIEMANN_HLLC only");
     if (!(dt >= 0.0) || !isfinite(dt)) return fail(ctx, GZ_E_INVAL, "dt must be finite and >= 0");
     return GZ_DISPATCH(do_fluxes_backward<float>(ctx, p, n, grad, B, dt, dpdt_bar, dEdt_bar, x_bar, h_bar,
                                                  n_bar, W_bar, grad_bar, B_bar),
@@ -590,7 +597,8 @@ gz_status gz_step_checkpoint(gz_ctx* ctx, gz_particles* p, double dt_fixed, doub
     if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
     if (!ckpt || ((uintptr_t)ckpt & 255) || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS)
         return fail(ctx, GZ_E_INVAL, "checkpoint: need a 256-byte aligned buffer and a valid level");
-    if (ctx->c.params.scheme != GZ_MFM) return fail(ctx, GZ_E_INVAL, "the adjoint covers GZ_MFM only");
+    if (!adjoint_covers(ctx->c.params))
+        return fail(ctx, GZ_E_INVAL, "the adjoint covers GZ_MFM with GZ_RIEMANN_HLLC only");
     const Ckpt ck = ckpt_view(ctx->c, ckpt, level);
     return GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev, ck),
                        do_step<double>(ctx, p, dt_fixed, dt_used_dev, ck));
@@ -652,7 +660,8 @@ gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt, 
     if (gz_status s = check_particles(ctx, p_start, true)) return s;
     if (!gbar_end || !gbar_start) return fail(ctx, GZ_E_INVAL, "null adjoint set");
     if (!(dt > 0.0) || !isfinite(dt)) return fail(ctx, GZ_E_INVAL, "dt must be finite and > 0");
-    if (ctx->c.params.scheme != GZ_MFM) return fail(ctx, GZ_E_INVAL, "the adjoint covers GZ_MFM only");
+    if (!adjoint_covers(ctx->c.params))
+        return fail(ctx, GZ_E_INVAL, "the adjoint covers GZ_MFM with GZ_RIEMANN_HLLC only");
     if (ckpt && (((uintptr_t)ckpt & 255) || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS))
         return fail(ctx, GZ_E_INVAL, "checkpoint: need a 256-byte aligned buffer and a valid level");
     const Ckpt ck = ckpt_view(ctx->c, const_cast<void*>(ckpt), level);

@@ -210,10 +210,107 @@ __device__ __forceinline__ void mfv_flux(const T (&FL)[5], const T (&FR)[5], T u
     FE = (fe + ((vfx * fx + vfy * fy) + vfz * fz)) + T(0.5) * ((vfx * vfx + vfy * vfy) + vfz * vfz) * fr;
 }
 
+// x^y for x > 0: FP32 as 2^(y log2 x) from the hardware base-2 logarithm
+// (relative error about 1e-7 (1 + |y log2 x|)); FP64 the library pow.
+__device__ __forceinline__ float ppow(float x, float y) { return exp2f(y * __log2f(x)); }
+__device__ __forceinline__ double ppow(double x, double y) { return pow(x, y); }
+
+// Exact Riemann problem of the face (option of O12).  Pressure function of one
+// side at the trial star pressure p: shock branch (p > P_K)
+// (p - P_K) sqrt(A_K/(p + B_K)) with A_K = 2/((gamma+1) rho_K),
+// B_K = (gamma-1)/(gamma+1) P_K; rarefaction branch
+// 2 c_K/(gamma-1) ((p/P_K)^e - 1), e = (gamma-1)/(2 gamma), whose derivative
+// (p/P_K)^(e-1)/(rho_K c_K) is formed from the same power.  f and df/dp.
+template <typename T>
+__device__ __forceinline__ void pres_side(T p, T rho, T P, T c, T gam, T& f, T& fd) {
+    if (p > P) {
+        const T A = pdiv(T(2), (gam + T(1)) * rho), Bk = pdiv(gam - T(1), gam + T(1)) * P;
+        const T q = psqrt(pdiv(A, p + Bk));
+        f = (p - P) * q;
+        fd = q * (T(1) - T(0.5) * pdiv(p - P, p + Bk));
+    } else {
+        const T r = pdiv(p, P);
+        const T pe = ppow(r, pdiv(gam - T(1), T(2) * gam));
+        f = pdiv(T(2) * c, gam - T(1)) * (pe - T(1));
+        fd = pdiv(pe, r * rho * c);
+    }
+}
+
+// Star pressure and contact speed of the exact solution: the root of
+// F(p) = f_L(p) + f_R(p) + u_R - u_L, an increasing concave function.
+// Starting point (Toro's adaptive choice): the primitive-variable estimate
+// p_PV = (P_L + P_R)/2 - (u_R - u_L)(rho_L + rho_R)(c_L + c_R)/8 when the
+// pressures differ by at most 2x and p_PV lies between them; below them the
+// two-rarefaction solution [(c_L + c_R - (gamma-1)(u_R - u_L)/2) /
+// (c_L P_L^-e + c_R P_R^-e)]^(1/e) (the root itself when both waves are
+// rarefactions); above them the two-shock estimate
+// (g_L P_L + g_R P_R - (u_R - u_L))/(g_L + g_R), g_K = sqrt(A_K/(p_PV + B_K));
+// at least 1e-12 (P_L + P_R).  Newton steps kept inside the bracket the signs
+// of F have established (bisection, or doubling while no upper end is known)
+// until two iterates agree to 1e-15 (FP64) or 1e-6 (FP32) relative, or F is at
+// the rounding level of its terms (FP32: 4e-7 of |f_L| + |f_R| + |u_R - u_L|,
+// where a strong rarefaction's F cannot resolve p to 1e-6); at most 200 (FP64)
+// or 20 (FP32) steps.  u* = (u_L + u_R)/2 + (f_R - f_L)/2.  Returns false when
+// the two fans open a vacuum (2 (c_L + c_R)/(gamma-1) <= u_R - u_L).
+template <typename T>
+__device__ __forceinline__ bool exact_star(T rL, T uL, T PL, T rR, T uR, T PR, T gam, T& ps, T& us) {
+    const T cL = psqrt(pdiv(gam * PL, rL)), cR = psqrt(pdiv(gam * PR, rR));
+    const T du = uR - uL;
+    if (pdiv(T(2) * (cL + cR), gam - T(1)) <= du) return false;
+    const T plo = min(PL, PR), phi = max(PL, PR);
+    T p = T(0.5) * (PL + PR) - T(0.125) * du * (rL + rR) * (cL + cR);
+    if (!(phi <= T(2) * plo && p >= plo && p <= phi)) {
+        if (p < plo) {
+            const T e = pdiv(gam - T(1), T(2) * gam);
+            const T num = (cL + cR) - T(0.5) * (gam - T(1)) * du;
+            const T den = cL * ppow(PL, -e) + cR * ppow(PR, -e);
+            p = ppow(pdiv(num, den), pdiv(T(1), e));
+        } else {
+            const T p0 = max(p, T(0));
+            const T gp1 = gam + T(1), gm1 = gam - T(1);
+            const T gL = psqrt(pdiv(pdiv(T(2), gp1 * rL), p0 + pdiv(gm1, gp1) * PL));
+            const T gR = psqrt(pdiv(pdiv(T(2), gp1 * rR), p0 + pdiv(gm1, gp1) * PR));
+            p = pdiv((gL * PL + gR * PR) - du, gL + gR);
+        }
+    }
+    const T pmin = T(1e-12) * (PL + PR);
+    if (!(p >= pmin)) p = pmin;
+    constexpr bool f32 = sizeof(T) == 4;
+    const T tol = f32 ? T(1e-6) : T(1e-15);
+    const int cap = f32 ? 20 : 200;
+    T lo = T(0), hi = T(0);
+    bool has_hi = false;
+    for (int it = 0; it < cap; ++it) {
+        T fL, dL, fR, dR;
+        pres_side(p, rL, PL, cL, gam, fL, dL);
+        pres_side(p, rR, PR, cR, gam, fR, dR);
+        const T F = (fL + fR) + du;
+        if (f32 && fabs(F) <= T(4e-7) * ((fabs(fL) + fabs(fR)) + fabs(du))) break;
+        if (F > T(0)) {
+            hi = p;
+            has_hi = true;
+        } else {
+            lo = p;
+        }
+        T pn = p - pdiv(F, dL + dR);
+        if (!(pn > lo) || (has_hi && !(pn < hi))) pn = has_hi ? T(0.5) * (lo + hi) : T(2) * p;
+        const bool done = fabs(pn - p) <= tol * (pn + p);
+        p = pn;
+        if (done) break;
+    }
+    T fL, dL, fR, dR;
+    pres_side(p, rL, PL, cL, gam, fL, dL);
+    pres_side(p, rR, PR, cR, gam, fR, dR);
+    ps = p;
+    us = T(0.5) * (uL + uR) + T(0.5) * (fR - fL);
+    return true;
+}
+
 // Contribution of the pair (a, b) to particle a's rates: dp (3), dE and,
-// under MFV (O15), dm.  Returns false when the face area vanishes.  flags:
-// 1 fallback, 2 P* < 0.
-template <typename T, bool kMFV>
+// under MFV (O15), dm.  kRiem: the MFM face's star from HLLC (0), the exact
+// solver (1), or HLLC with the exact star where HLLC's P* < 0 (2).  Returns
+// false when the face area vanishes.  flags: 1 fallback, 2 P* < 0 (or vacuum).
+template <typename T, bool kMFV, int kRiem>
 __device__ __forceinline__ bool pair_rates(const T (&a)[kRecord], const T (&b)[kRecord], bool aL,
                                            T hdt, T gam, bool hancock, const T (&inca)[5], T (&dp)[3],
                                            T& dE, T& dm, int& fl) {
@@ -284,10 +381,24 @@ __device__ __forceinline__ bool pair_rates(const T (&a)[kRecord], const T (&b)[k
     const T den = rL * (SL - uL) - rR * (SR - uR);
     const T ss = pdiv(num, den);
     T ps = PL + rL * (SL - uL) * (ss - uL);
-    if (ps < T(0)) {
-        ps = T(0);
-        fl |= 2;
+    T sm = ss;  // contact speed of the MFM energy rate
+    bool neg = ps < T(0);
+    if constexpr (!kMFV && kRiem != 0) {
+        if (kRiem == 1 || neg) {
+            T pe, ue;
+            if (exact_star(rL, uL, PL, rR, uR, PR, gam, pe, ue)) {
+                ps = pe;
+                sm = ue;
+                if (kRiem == 1) neg = false;
+            } else {
+                ps = T(0);
+                sm = T(0);
+                neg = true;
+            }
+        }
     }
+    if (neg) fl |= 2;
+    if (ps < T(0)) ps = T(0);
     if constexpr (kMFV) {
         // both particles of the pair form the same canonical flux bits; L
         // loses what R gains
@@ -306,7 +417,7 @@ __device__ __forceinline__ bool pair_rates(const T (&a)[kRecord], const T (&b)[k
     dp[0] = -mul_rn(ps, A0);
     dp[1] = -mul_rn(ps, A1);
     dp[2] = -mul_rn(ps, A2);
-    const T ef = ps * (ss + vfn) * Am;
+    const T ef = ps * (sm + vfn) * Am;
     dE = aL ? -ef : ef;
     return true;
 }

@@ -625,10 +625,11 @@ __global__ void k_grad_out(int N, const unsigned* __restrict__ orig, const T* __
 // One thread per particle over its pairs N_i then R_i (both contiguous
 // lists, read four indices per 16-byte load).  Contributions are summed in
 // the working precision over runs of 8 pairs and each run is added to FP64
-// accumulators.  kMFV: the MFV fluxes (O15), which add dm/dt.
+// accumulators.  kMFV: the MFV fluxes (O15), which add dm/dt.  kRiem: the
+// MFM face's Riemann solver (pair_rates).
 constexpr int kFluxBlock = 128;
 
-template <typename T, bool kMFV>
+template <typename T, bool kMFV, int kRiem>
 __global__ void __launch_bounds__(kFluxBlock)
     k_fluxes(int N, const T* __restrict__ rec, const long long* __restrict__ sid,
              const int* __restrict__ sbox, const unsigned* __restrict__ nbr,
@@ -670,7 +671,7 @@ __global__ void __launch_bounds__(kFluxBlock)
                 load_rec(rec + (size_t)j * kRecord, b);
                 T dp[3], dE, dm;
                 int fl = 0;
-                if (pair_rates<T, kMFV>(a, b, idi < sid[j], hdt, gam, hancock, inca, dp, dE, dm, fl)) {
+                if (pair_rates<T, kMFV, kRiem>(a, b, idi < sid[j], hdt, gam, hancock, inca, dp, dE, dm, fl)) {
                     part[0] += dp[0];
                     part[1] += dp[1];
                     part[2] += dp[2];
@@ -967,17 +968,24 @@ cudaError_t run_grad_out(Ctx& c, T* grad, T* B) {
     return cudaGetLastError();
 }
 
+template <typename T, bool kMFV, int kRiem>
+static void launch_fluxes(Ctx& c) {
+    k_fluxes<T, kMFV, kRiem><<<blocks(c.N, kFluxBlock), kFluxBlock, 0, c.stream>>>(
+        c.N, (const T*)c.rec, c.sid, c.sbox, c.nbr, c.ncount, c.rnbr, c.rcount, kparams(c), c.dt_use,
+        c.dpdt, c.dEdt, kMFV ? c.dmdt : nullptr, c.status);
+}
+
 template <typename T>
 cudaError_t run_fluxes(Ctx& c) {
     c.launches += 1;
     if (c.params.scheme == GZ_MFV)
-        k_fluxes<T, true><<<blocks(c.N, kFluxBlock), kFluxBlock, 0, c.stream>>>(
-            c.N, (const T*)c.rec, c.sid, c.sbox, c.nbr, c.ncount, c.rnbr, c.rcount, kparams(c), c.dt_use,
-            c.dpdt, c.dEdt, c.dmdt, c.status);
+        launch_fluxes<T, true, GZ_RIEMANN_HLLC>(c);
+    else if (c.params.riemann == GZ_RIEMANN_EXACT)
+        launch_fluxes<T, false, GZ_RIEMANN_EXACT>(c);
+    else if (c.params.riemann == GZ_RIEMANN_FALLBACK)
+        launch_fluxes<T, false, GZ_RIEMANN_FALLBACK>(c);
     else
-        k_fluxes<T, false><<<blocks(c.N, kFluxBlock), kFluxBlock, 0, c.stream>>>(
-            c.N, (const T*)c.rec, c.sid, c.sbox, c.nbr, c.ncount, c.rnbr, c.rcount, kparams(c), c.dt_use,
-            c.dpdt, c.dEdt, nullptr, c.status);
+        launch_fluxes<T, false, GZ_RIEMANN_HLLC>(c);
     return cudaGetLastError();
 }
 
