@@ -53,7 +53,7 @@ class Params(C.Structure):
 class Counters(C.Structure):
     _fields_ = [(k, C.c_int64) for k in
                 ("hconv", "singular", "fallback", "pstar_neg", "ufloor", "nonfinite",
-                 "kappa_big", "pairs")]
+                 "kappa_big", "pairs", "bin_clamp")]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -117,6 +117,12 @@ def _load():
             lib.gzo_step.restype = C.c_int
             lib.gzo_step.argtypes = [i64] + [vp] * 10 + [C.POINTER(Params), _D, vp, vp, vp, vp,
                                                        C.POINTER(Counters)]
+            lib.gzo_step_hier.restype = C.c_int
+            lib.gzo_step_hier.argtypes = [i64] + [vp] * 10 + [C.POINTER(Params), C.c_int32, _D, vp,
+                                                            C.POINTER(C.c_int64), C.POINTER(Counters)]
+            lib.gzo_exchange.restype = C.c_int
+            lib.gzo_exchange.argtypes = [i64] + [vp] * 15 + [d, C.POINTER(Params), vp, vp, vp,
+                                                           C.POINTER(Counters)]
             lib.gzo_pair.restype = C.c_int
             lib.gzo_pair.argtypes = [vp, d, d, vp, vp, vp, vp, d, d, vp, vp, vp, d,
                                      C.POINTER(Params), vp, _D, _D, vp, vp, _D, _D,
@@ -311,6 +317,46 @@ def step(s: State, p: Params, dt: float = 0.0, counters: Counters | None = None,
     if with_mass:
         return o, dtc.value, n, dp, dE, dm
     return o, dtc.value, n, dp, dE
+
+
+def step_hier(s: State, p: Params, K: int, dt: float = 0.0, counters: Counters | None = None):
+    """One sync interval of hierarchical (power-of-two) timesteps on a copy
+    (reading HT); returns (new_state, interval, bins [N] int32, active
+    particle-substeps).  K = 0 is step()."""
+    o = s.copy()
+    N = o.N
+    bins = np.zeros(N, dtype=np.int32)
+    act = C.c_int64()
+    dtc = C.c_double(float(dt))
+    cnt = counters if counters is not None else Counters()
+    rc = _load().gzo_step_hier(N, _p(o.x), _p(o.y), _p(o.z), _p(o.vx), _p(o.vy), _p(o.vz),
+                               _p(o.m), _p(o.u), _p(o.H), _p(o.id), C.byref(p), int(K),
+                               C.byref(dtc), _p(bins), C.byref(act), C.byref(cnt))
+    if rc != 0:
+        raise ValueError("step_hier: MFM only, 0 <= K <= 20, N >= 1")
+    return o, dtc.value, bins, int(act.value)
+
+
+def exchange(x, y, z, ids, m, H, n, vx, vy, vz, u, grad, B, bins, active, D, p: Params | None = None,
+             counters: Counters | None = None):
+    """One hierarchical substep's pair exchange (gzo_exchange): returns
+    (accp [3,N], accE [N], touched [N]) for the given per-particle arrays."""
+    p = p if p is not None else params()
+    a = [_f64(v) for v in (x, y, z, m, H, n, vx, vy, vz, u)]
+    N = a[0].size
+    g = np.ascontiguousarray(grad, dtype=np.float64).reshape(15, N)
+    Bm = np.ascontiguousarray(B, dtype=np.float64).reshape(6, N)
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    bins = np.ascontiguousarray(bins, dtype=np.int32)
+    act = np.ascontiguousarray(active, dtype=np.uint8)
+    accp = np.zeros((3, N))
+    accE = np.zeros(N)
+    tch = np.zeros(N, dtype=np.uint8)
+    cnt = counters if counters is not None else Counters()
+    _load().gzo_exchange(N, _p(a[0]), _p(a[1]), _p(a[2]), _p(ids), _p(a[3]), _p(a[4]), _p(a[5]),
+                         _p(a[6]), _p(a[7]), _p(a[8]), _p(a[9]), _p(g), _p(Bm), _p(bins), _p(act),
+                         float(D), C.byref(p), _p(accp), _p(accE), _p(tch), C.byref(cnt))
+    return accp, accE, tch
 
 
 def pair(L: dict, R: dict, dt: float, p: Params):

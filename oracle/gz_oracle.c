@@ -983,6 +983,259 @@ int gzo_step(int64_t N, double* x, double* y, double* z, double* vx, double* vy,
     return 0;
 }
 
+/* ------------------------------------------- hierarchical timesteps ---- */
+/* Reading HT (power-of-two timestep bins; the paper names hierarchical
+ * adaptive timesteps and gives no formula).  One call advances the box over a
+ * sync interval D split into 2^K substeps of D/2^K.  Particle i sits in bin
+ * k_i in [0, K] with step dt_i = D/2^k_i; it is active at substep s when
+ * s is a multiple of 2^(K - k_i), i.e. when a step of its own starts.
+ * Bins: at s = 0 every particle is active and, with its O13 criterion
+ * dtc_i = 2 V_i^(1/3)/max v_sig, takes the smallest k with D/2^k <= cfl dtc_i
+ * (K at most); D is dt_fixed when given, else
+ * min(cfl max_i dtc_i, 2^K cfl min_i dtc_i) (K = 0: the global CFL step).  At
+ * later active times a particle may only move to a smaller step (any smaller
+ * power of two starts there too); larger steps wait for the next interval.
+ * Positions: the caller's x holds each particle's position at the start of
+ * its current step (x_a, with velocity v_a then); at substep s every particle
+ * is placed at x_a + tau (v_a + v)/2, tau = (s - s_a) D/2^K and v its current
+ * velocity, and a step that ends moves x_a to x_a + dt_i (v_a + v)/2 (the
+ * trapezoid drift of O14).  Substep s: O4/O5 for the active particles (the
+ * others keep H and n of their last active time), O6-O9 and O13 for them
+ * (the others keep their gradients and B), re-binning, then every flux pair
+ * (O10) with at least one active particle exchanges the face fluxes of
+ * O11/O12 over dt_ij = min(dt_i, dt_j) = D/2^max(k_i, k_j) (Hancock with
+ * dt_ij/2): each particle accumulates rate * 2^(k_a - k_ij), and its momentum
+ * and energy change by dt_a times that sum (exact power-of-two scaling, so
+ * the pair's two shares are equal and opposite).  A particle's exchanges
+ * happen whenever the smaller-step particle of a pair is active, so every
+ * face is integrated over the whole interval exactly once.  u <= 0 after a
+ * kick is floored as in O14 with the median of u at the substep start.  K = 0
+ * is gzo_step. */
+static int32_t bin_for(double D, double cfl_dtc, int32_t K, int* clamped) {
+    for (int32_t k = 0; k <= K; ++k)
+        if (ldexp(D, -k) <= cfl_dtc) return k;
+    *clamped = 1;
+    return K;
+}
+
+int gzo_exchange(int64_t N, const double* x, const double* y, const double* z,
+                 const int64_t* id, const double* m, const double* H, const double* n,
+                 const double* vx, const double* vy, const double* vz, const double* u,
+                 const double* grad, const double* B, const int32_t* bin, const uint8_t* active,
+                 double D, const gzo_params* p, double* accp, double* accE, uint8_t* touched,
+                 gzo_counters* cnt) {
+    finder_t fd;
+    finder_init(&fd, N, x, y, z, id, p->use_cells, median_cell_len(H, N));
+    const double Hmax = max_of(H, N);
+    int64_t nfall = 0, nneg = 0, npairs = 0;
+#pragma omp parallel reduction(+ : nfall, nneg, npairs)
+    {
+        scratch_t s = {0};
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < N; ++i) {
+            const int64_t* list;
+            int64_t cntj = gather(&fd, &s, i, Hmax > H[i] ? Hmax : H[i], &list);
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            double d[3];
+            int any = 0;
+            for (int64_t k = 0; k < cntj; ++k) {
+                int64_t j = list[k];
+                if (!active[i] && !active[j]) continue;
+                double r2 = sep(x, y, z, i, j, d);
+                if (!(r2 < H[i] * H[i] || r2 < H[j] * H[j])) continue;
+                npairs++;
+                any = 1;
+                int64_t L = id[i] < id[j] ? i : j;
+                int64_t R = id[i] < id[j] ? j : i;
+                int32_t kij = bin[i] > bin[j] ? bin[i] : bin[j];
+                double dtij = ldexp(D, -kij);
+                double pL[3], pR[3], WL[5], WR[5], gL[15], gR[15], BL[6], BR[6];
+                load_side(L, x, y, z, m, n, vx, vy, vz, u, grad, B, N, p->gamma, pL, WL, gL, BL);
+                load_side(R, x, y, z, m, n, vx, vy, vz, u, grad, B, N, p->gamma, pR, WR, gR, BR);
+                double A[3], ps, ss, vf[3], dp[3], dE, dm;
+                int fl = 0;
+                gzo_pair(pL, H[L], n[L], WL, gL, BL, pR, H[R], n[R], WR, gR, BR, dtij, p, A, &ps,
+                         &ss, vf, dp, &dE, &dm, &fl);
+                if (fl & 1) nfall++;
+                if (fl & 2) nneg++;
+                double sg = ((i == L) ? 1.0 : -1.0) * ldexp(1.0, bin[i] - kij);
+                acc[0] += sg * dp[0];
+                acc[1] += sg * dp[1];
+                acc[2] += sg * dp[2];
+                acc[3] += sg * dE;
+            }
+            accp[i] = acc[0];
+            accp[N + i] = acc[1];
+            accp[2 * N + i] = acc[2];
+            accE[i] = acc[3];
+            touched[i] = (uint8_t)(any || active[i]);
+        }
+        scratch_free(&s);
+    }
+    finder_free(&fd);
+    if (cnt) {
+        cnt->fallback += nfall;
+        cnt->pstar_neg += nneg;
+        cnt->pairs += npairs;
+    }
+    return 0;
+}
+
+static double median_u(const double* u, int64_t N) {
+    double* tmp = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    memcpy(tmp, u, sizeof(double) * (size_t)N);
+    qsort(tmp, (size_t)N, sizeof(double), cmp_dbl);
+    double v = tmp[(N - 1) / 2];
+    free(tmp);
+    return v;
+}
+
+int gzo_step_hier(int64_t N, double* x, double* y, double* z, double* vx, double* vy,
+                  double* vz, double* m, double* u, double* H, const int64_t* id,
+                  const gzo_params* p, int32_t K, double* dt_inout, int32_t* bin_out,
+                  int64_t* active_out, gzo_counters* cnt) {
+    if (p->scheme != 0 || K < 0 || K > 20 || N < 1) return -1;
+    const size_t sz = sizeof(double) * (size_t)N;
+    double* xp = (double*)malloc(sz * 3);
+    double *yp = xp + N, *zp = xp + 2 * N;
+    double* va = (double*)malloc(sz * 3);
+    double* n = (double*)calloc((size_t)N, sizeof(double));
+    double* Hn = (double*)malloc(sz);
+    double* nn = (double*)malloc(sz);
+    double* grad = (double*)calloc((size_t)N * 15, sizeof(double));
+    double* B = (double*)calloc((size_t)N * 6, sizeof(double));
+    double* dtc = (double*)malloc(sz);
+    double* accp = (double*)malloc(sz * 3);
+    double* accE = (double*)malloc(sz);
+    int32_t* it = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
+    int32_t* bin = (int32_t*)calloc((size_t)N, sizeof(int32_t));
+    int32_t* sa = (int32_t*)calloc((size_t)N, sizeof(int32_t));
+    uint8_t* act = (uint8_t*)malloc((size_t)N);
+    uint8_t* tch = (uint8_t*)malloc((size_t)N);
+    for (int64_t i = 0; i < N; ++i) {
+        va[i] = vx[i];
+        va[N + i] = vy[i];
+        va[2 * N + i] = vz[i];
+    }
+    double D = *dt_inout;
+    const int32_t S = 1 << K;
+    int64_t nact = 0, nfl = 0, nclamp = 0;
+    for (int32_t s = 0; s < S; ++s) {
+        int64_t na = 0;
+        for (int64_t i = 0; i < N; ++i) {
+            act[i] = (uint8_t)(s % (1 << (K - bin[i])) == 0);
+            na += act[i];
+        }
+        nact += na;
+        if (na > 0) {
+            const double delta = ldexp(D > 0.0 ? D : 0.0, -K);
+            for (int64_t i = 0; i < N; ++i) {
+                const double tau = delta * (double)(s - sa[i]);
+                xp[i] = wrap1(x[i] + tau * (0.5 * (va[i] + vx[i])));
+                yp[i] = wrap1(y[i] + tau * (0.5 * (va[N + i] + vy[i])));
+                zp[i] = wrap1(z[i] + tau * (0.5 * (va[2 * N + i] + vz[i])));
+            }
+            gzo_density(N, xp, yp, zp, id, H, act, p, Hn, nn, it, NULL, cnt);
+            for (int64_t i = 0; i < N; ++i)
+                if (act[i]) {
+                    H[i] = Hn[i];
+                    n[i] = nn[i];
+                }
+            gzo_gradients(N, xp, yp, zp, id, m, H, n, vx, vy, vz, u, act, p, grad, B, NULL, NULL,
+                          NULL, cnt);
+            double dmin_unused;
+            gzo_timestep(N, xp, yp, zp, id, m, H, n, vx, vy, vz, u, act, p, dtc, &dmin_unused);
+            if (s == 0) {
+                if (!(D > 0.0)) {
+                    double lo = INFINITY, hi = 0.0;
+                    for (int64_t i = 0; i < N; ++i) {
+                        if (dtc[i] < lo) lo = dtc[i];
+                        if (isfinite(dtc[i]) && dtc[i] > hi) hi = dtc[i];
+                    }
+                    const double a = p->cfl * hi, b = ldexp(p->cfl * lo, K);
+                    D = a < b ? a : b;
+                }
+                for (int64_t i = 0; i < N; ++i) {
+                    int c = 0;
+                    bin[i] = bin_for(D, p->cfl * dtc[i], K, &c);
+                    nclamp += c;
+                }
+            } else {
+                for (int64_t i = 0; i < N; ++i)
+                    if (act[i]) {
+                        int c = 0;
+                        int32_t k = bin_for(D, p->cfl * dtc[i], K, &c);
+                        nclamp += c;
+                        if (k > bin[i]) bin[i] = k;
+                    }
+            }
+            double umed = 0.0;
+            int have_med = 0;
+            gzo_exchange(N, xp, yp, zp, id, m, H, n, vx, vy, vz, u, grad, B, bin, act, D, p, accp,
+                         accE, tch, cnt);
+            double* u0 = (double*)malloc(sz);
+            memcpy(u0, u, sz);
+            for (int64_t i = 0; i < N; ++i) {
+                if (!tch[i]) continue;
+                const double dt = ldexp(D, -bin[i]);
+                const double v2 = (vx[i] * vx[i] + vy[i] * vy[i]) + vz[i] * vz[i];
+                const double E = m[i] * (u[i] + 0.5 * v2) + dt * accE[i];
+                const double nx = (m[i] * vx[i] + dt * accp[i]) / m[i];
+                const double ny = (m[i] * vy[i] + dt * accp[N + i]) / m[i];
+                const double nz = (m[i] * vz[i] + dt * accp[2 * N + i]) / m[i];
+                double un = E / m[i] - 0.5 * ((nx * nx + ny * ny) + nz * nz);
+                if (!(un > 0.0)) {
+                    if (!have_med) {
+                        umed = median_u(u0, N);
+                        have_med = 1;
+                    }
+                    un = p->u_floor_frac * umed;
+                    nfl++;
+                }
+                vx[i] = nx;
+                vy[i] = ny;
+                vz[i] = nz;
+                u[i] = un;
+            }
+            free(u0);
+        }
+        for (int64_t i = 0; i < N; ++i) {
+            if ((s + 1) % (1 << (K - bin[i])) != 0) continue;
+            const double dt = ldexp(D, -bin[i]);
+            x[i] = wrap1(x[i] + dt * (0.5 * (va[i] + vx[i])));
+            y[i] = wrap1(y[i] + dt * (0.5 * (va[N + i] + vy[i])));
+            z[i] = wrap1(z[i] + dt * (0.5 * (va[2 * N + i] + vz[i])));
+            va[i] = vx[i];
+            va[N + i] = vy[i];
+            va[2 * N + i] = vz[i];
+            sa[i] = s + 1;
+        }
+    }
+    *dt_inout = D;
+    if (bin_out) memcpy(bin_out, bin, sizeof(int32_t) * (size_t)N);
+    if (active_out) *active_out = nact;
+    if (cnt) {
+        cnt->ufloor += nfl;
+        cnt->bin_clamp += nclamp;
+    }
+    free(xp);
+    free(va);
+    free(n);
+    free(Hn);
+    free(nn);
+    free(grad);
+    free(B);
+    free(dtc);
+    free(accp);
+    free(accE);
+    free(it);
+    free(bin);
+    free(sa);
+    free(act);
+    free(tch);
+    return 0;
+}
+
 /* ---------------------------------------------- exact Riemann solver ---- */
 /* Ideal-gas exact solution (pressure function of each side: shock branch
  * (p - p_K) sqrt(A_K / (p + B_K)) with A_K = 2 / ((g+1) rho_K),

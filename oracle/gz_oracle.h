@@ -56,6 +56,7 @@ typedef struct {
     int64_t nonfinite;   /* non-finite inputs or outputs                      */
     int64_t kappa_big;   /* particles with kappa > kappa_max                  */
     int64_t pairs;       /* ordered flux pairs visited                        */
+    int64_t bin_clamp;   /* hierarchical steps: bin assignments capped at K   */
 } gzo_counters;
 
 /* O2 */
@@ -125,6 +126,28 @@ int gzo_step(int64_t N, double* x, double* y, double* z, double* vx, double* vy,
              double* vz, double* m, double* u, double* H, const int64_t* id,
              const gzo_params* p, double* dt_inout, double* n_out, double* dpdt,
              double* dEdt, double* dmdt, gzo_counters* cnt);
+
+/* Hierarchical timesteps (reading HT, MFM only): one sync interval of 2^K
+ * substeps in place on the state; *dt_inout > 0 fixes the interval D, else
+ * the CFL rule sets it; the interval used is written back.  bin_out ([N],
+ * optional) receives every particle's final bin, active_out (optional) the
+ * number of active particle-substeps.  K = 0 is gzo_step.  Returns -1 for
+ * MFV, K outside [0, 20] or N < 1. */
+int gzo_step_hier(int64_t N, double* x, double* y, double* z, double* vx, double* vy,
+                  double* vz, double* m, double* u, double* H, const int64_t* id,
+                  const gzo_params* p, int32_t K, double* dt_inout, int32_t* bin_out,
+                  int64_t* active_out, gzo_counters* cnt);
+
+/* Pair exchange of one hierarchical substep: for every particle, the sum over
+ * its flux pairs with an active partner (or itself active) of
+ * rate * 2^(bin_i - max(bin_i, bin_j)), faces evaluated over
+ * D/2^max(bin_i, bin_j); touched[i] = 1 when i is active or has such a pair. */
+int gzo_exchange(int64_t N, const double* x, const double* y, const double* z,
+                 const int64_t* id, const double* m, const double* H, const double* n,
+                 const double* vx, const double* vy, const double* vz, const double* u,
+                 const double* grad, const double* B, const int32_t* bin, const uint8_t* active,
+                 double D, const gzo_params* p, double* accp, double* accE, uint8_t* touched,
+                 gzo_counters* cnt);
 
 /* One face evaluation in canonical (L, R) order for pins: inputs are the
  * two particles' positions, H, n, primitives (rho, vx, vy, vz, P), limited
