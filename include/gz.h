@@ -220,6 +220,35 @@ gz_status gz_hydro_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const voi
  * doubles, may be NULL) receives the steps used.  No host synchronisation. */
 gz_status gz_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev);
 
+/* Hierarchical (individual, power-of-two) timesteps: advances every box of p
+ * by one sync interval D split into 2^K substeps of D/2^K (K in [0, 20]).
+ * Reading of the paper's hierarchical adaptive timesteps (it gives no
+ * formula): particle i takes bin k_i (step D/2^k_i) and is active at the
+ * substeps that start a step of its own.  At substep 0 all particles are
+ * active; D = dt_fixed when dt_fixed > 0, else per box
+ * min(cfl max_i dtc_i, 2^K cfl min_i dtc_i) with dtc_i = 2 V_i^(1/3)/max v_sig
+ * (O13), and k_i is the smallest k with D/2^k <= cfl dtc_i (at most K; later
+ * active times may only deepen a bin).  At each substep the active particles
+ * run O4-O9 and O13 at positions predicted for all particles
+ * (x_start + elapsed * (v_start + v)/2); the others keep H, n, gradients and B
+ * of their last active time; every flux pair (O10) with an active particle
+ * exchanges the O11/O12 face fluxes over D/2^max(k_i, k_j) (Hancock with half
+ * of that), equal and opposite for its two particles; momentum and energy are
+ * kicked at once, and a step that ends drifts its particle by
+ * dt_i (v_start + v_end)/2.  K = 0 gives gz_step's result bitwise.  In place
+ * on p like gz_step (x, y, z, vx, vy, vz, u, h; m and id read only); h ends as
+ * each particle's H of its last active time.  dt_used_dev (device, nboxes
+ * doubles, may be NULL) receives D per box, bins_out (device, N int32, caller
+ * order, may be NULL) the final bins, *active_out (host, may be NULL) the
+ * number of active particle-substeps.  Host synchronisation: one per substep
+ * (the number of active particles sizes the launches; substeps without one
+ * only drift), so the call cannot be captured in a CUDA graph.  Scratch of
+ * about 150 bytes a particle (FP32) is allocated on the first call.  Errors:
+ * GZ_E_INVAL (K out of range, GZ_MFV or a Riemann option other than
+ * GZ_RIEMANN_HLLC), GZ_E_NOMEM. */
+gz_status gz_step_hier(gz_ctx* ctx, gz_particles* p, int32_t K, double dt_fixed, double* dt_used_dev,
+                       int32_t* bins_out, int64_t* active_out);
+
 /* Captures nsteps consecutive gz_step calls on p (same arguments as gz_step)
  * into a CUDA graph owned by the context, replacing any earlier one; nothing
  * is executed.  The context's stream must be a created (non-default) stream.

@@ -86,6 +86,7 @@ def load_library(build_if_missing: bool = True):
             "gz_timestep": (st, [vp, P, vp, vp, vp]),
             "gz_hydro_fluxes": (st, [vp, P, vp, vp, vp, d, vp, vp, vp]),
             "gz_step": (st, [vp, P, d, vp]),
+            "gz_step_hier": (st, [vp, P, i32, d, vp, vp, vp]),
             "gz_hydro_fluxes_backward": (st, [vp, P, vp, vp, vp, d, vp, vp, vp, vp, vp, vp, vp, vp]),
             "gz_graph_capture": (st, [vp, P, i32, d, vp]),
             "gz_graph_launch": (st, [vp]),
@@ -254,6 +255,17 @@ class Context:
             self._check(self.lib.gz_step_checkpoint(self.h, C.byref(s), float(dt_fixed), _ptr(dt_used),
                                                     _ptr(ckpt), int(level)), "gz_step_checkpoint")
         return dt_used
+
+    def step_hier(self, p, K: int, dt_fixed: float = 0.0, dt_used=None, bins=None):
+        """gz_step_hier: one sync interval of 2^K hierarchical substeps in place on
+        p; dt_used (device float64 [nboxes]) receives the interval, bins (device
+        int32 [N]) the final bins.  Returns the number of active
+        particle-substeps."""
+        s = self._parts(p)
+        act = C.c_int64()
+        self._check(self.lib.gz_step_hier(self.h, C.byref(s), int(K), float(dt_fixed), _ptr(dt_used),
+                                          _ptr(bins), C.byref(act)), "gz_step_hier")
+        return int(act.value)
 
     def checkpoint_bytes(self, level: int = 1) -> int:
         """gz_checkpoint_bytes: size of one step checkpoint at this level."""

@@ -92,6 +92,25 @@ struct Pass {
     }
 };
 
+}  // namespace
+
+void gz::PassTimer::begin(int pass) const {
+    if (!c->prof || pass < 0 || pass >= GZ_NPASSES) return;
+    cudaEvent_t a = take_event(*c);
+    cudaEventRecord(a, c->stream);
+    c->open_ev[pass] = a;
+}
+
+void gz::PassTimer::end(int pass) const {
+    if (!c->prof || pass < 0 || pass >= GZ_NPASSES || !c->open_ev[pass]) return;
+    cudaEvent_t b = take_event(*c);
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({pass, c->open_ev[pass], b});
+    c->open_ev[pass] = nullptr;
+}
+
+namespace {
+
 gz_status check_particles(gz_ctx* ctx, const gz_particles* p, bool need_vel) {
     if (!p) return fail(ctx, GZ_E_INVAL, "null particle set");
     if (!p->x || !p->y || !p->z || !p->h || !p->id)
@@ -516,6 +535,7 @@ gz_status gz_destroy(gz_ctx* ctx) {
     for (auto ev : ctx->c.ev_pool) cudaEventDestroy(ev);
     cudaFree(ctx->c.arena);
     if (ctx->c.adj_arena) cudaFree(ctx->c.adj_arena);
+    free_hier_scratch(ctx->c);
     if (ctx->c.graph_exec) cudaGraphExecDestroy(ctx->c.graph_exec);
     if (ctx->c.graph) cudaGraphDestroy(ctx->c.graph);
     delete ctx;
@@ -582,6 +602,25 @@ gz_status gz_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
     if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
     return GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev, Ckpt()),
                        do_step<double>(ctx, p, dt_fixed, dt_used_dev, Ckpt()));
+}
+
+gz_status gz_step_hier(gz_ctx* ctx, gz_particles* p, int32_t K, double dt_fixed, double* dt_used_dev,
+                       int32_t* bins_out, int64_t* active_out) {
+    if (!ctx) return GZ_E_INVAL;
+    if (gz_status s = check_particles(ctx, p, true)) return s;
+    if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
+    if (K < 0 || K > 20) return fail(ctx, GZ_E_INVAL, "K must be in [0, 20]");
+    Ctx& c = ctx->c;
+    if (c.params.scheme != GZ_MFM || c.params.riemann != GZ_RIEMANN_HLLC)
+        return fail(ctx, GZ_E_INVAL, "hierarchical steps cover GZ_MFM with GZ_RIEMANN_HLLC only");
+    const PassTimer timer{&c};
+    long long act = 0;
+    cudaError_t e = c.precision == GZ_FP64
+                        ? run_step_hier<double>(c, *p, K, dt_fixed, dt_used_dev, bins_out, &act, timer)
+                        : run_step_hier<float>(c, *p, K, dt_fixed, dt_used_dev, bins_out, &act, timer);
+    if (active_out) *active_out = (int64_t)act;
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, GZ_E_NOMEM, "gz_step_hier: scratch allocation failed");
+    return cuda_check(ctx, e, "gz_step_hier");
 }
 
 gz_status gz_checkpoint_bytes(gz_ctx* ctx, int32_t level, int64_t* bytes) {

@@ -429,43 +429,74 @@ __device__ __forceinline__ double wrap1(double v) {
     return v;
 }
 
-// FP64 state: the literal conserved update, like the oracle.
-__device__ __forceinline__ void update_one(double m, double& x, double& y, double& z, double& vx,
-                                           double& vy, double& vz, double& u, double dpx, double dpy,
-                                           double dpz, double dE, double dt) {
-    const double v2 = (vx * vx + vy * vy) + vz * vz;
-    const double E = m * (u + 0.5 * v2) + dt * dE;
-    const double nx = (m * vx + dt * dpx) / m, ny = (m * vy + dt * dpy) / m, nz = (m * vz + dt * dpz) / m;
-    x = wrap1(x + dt * (0.5 * (vx + nx)));
-    y = wrap1(y + dt * (0.5 * (vy + ny)));
-    z = wrap1(z + dt * (0.5 * (vz + nz)));
-    u = E / m - 0.5 * ((nx * nx + ny * ny) + nz * nz);
+// FP64 state: the literal conserved update, like the oracle, every operation
+// rounded explicitly (no contraction), so that each kernel that kicks or
+// drifts a particle (the step's update, the hierarchical kick and drift)
+// produces the same bits.  Kick: p += dt dp/dt, E += dt dE/dt, v = p/m,
+// u = E/m - v^2/2.
+__device__ __forceinline__ void kick_one(double m, double& vx, double& vy, double& vz, double& u, double dpx,
+                                         double dpy, double dpz, double dE, double dt) {
+    const double v2 = __dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz));
+    const double E = __dadd_rn(__dmul_rn(m, __dadd_rn(u, __dmul_rn(0.5, v2))), __dmul_rn(dt, dE));
+    const double nx = __ddiv_rn(__dadd_rn(__dmul_rn(m, vx), __dmul_rn(dt, dpx)), m);
+    const double ny = __ddiv_rn(__dadd_rn(__dmul_rn(m, vy), __dmul_rn(dt, dpy)), m);
+    const double nz = __ddiv_rn(__dadd_rn(__dmul_rn(m, vz), __dmul_rn(dt, dpz)), m);
+    const double n2 = __dadd_rn(__dadd_rn(__dmul_rn(nx, nx), __dmul_rn(ny, ny)), __dmul_rn(nz, nz));
+    u = __dsub_rn(__ddiv_rn(E, m), __dmul_rn(0.5, n2));
     vx = nx;
     vy = ny;
     vz = nz;
 }
+// Trapezoid drift of one coordinate: wrap(x + dt (v_old + v_new)/2).
+__device__ __forceinline__ double drift_one(double x, double v_old, double v_new, double dt) {
+    return wrap1(__dadd_rn(x, __dmul_rn(dt, __dmul_rn(0.5, __dadd_rn(v_old, v_new)))));
+}
+__device__ __forceinline__ void update_one(double m, double& x, double& y, double& z, double& vx,
+                                           double& vy, double& vz, double& u, double dpx, double dpy,
+                                           double dpz, double dE, double dt) {
+    const double ox = vx, oy = vy, oz = vz;
+    kick_one(m, vx, vy, vz, u, dpx, dpy, dpz, dE, dt);
+    x = drift_one(x, ox, vx, dt);
+    y = drift_one(y, oy, vy, dt);
+    z = drift_one(z, oz, vz, dt);
+}
 // FP32 state: the same update written with the increments dv = dt (dp/dt)/m
 // and du = dt (dE/dt)/m - dv . (v + dv/2), which is E/m - v_new^2/2 - u
-// without the cancellation of the literal form.
+// without the cancellation of the literal form; the drift is
+// x + dt (v_old + dv/2).  Explicit rounding as above.
 __device__ __forceinline__ float wrapf(float v) {
     if (v < 0.f) v += 1.f;
     if (v >= 1.f) v -= 1.f;
     return v;
 }
+__device__ __forceinline__ void kick_one(float m, float& vx, float& vy, float& vz, float& u, double dpx,
+                                         double dpy, double dpz, double dE, double dt, float& dvx,
+                                         float& dvy, float& dvz) {
+    const float dtf = (float)dt, im = __fdiv_rn(1.f, m);
+    dvx = __fmul_rn(__fmul_rn(dtf, (float)dpx), im);
+    dvy = __fmul_rn(__fmul_rn(dtf, (float)dpy), im);
+    dvz = __fmul_rn(__fmul_rn(dtf, (float)dpz), im);
+    const float hx = __fadd_rn(vx, __fmul_rn(0.5f, dvx)), hy = __fadd_rn(vy, __fmul_rn(0.5f, dvy)),
+                hz = __fadd_rn(vz, __fmul_rn(0.5f, dvz));
+    const float w = __fadd_rn(__fadd_rn(__fmul_rn(dvx, hx), __fmul_rn(dvy, hy)), __fmul_rn(dvz, hz));
+    const float du = __fsub_rn(__fmul_rn(__fmul_rn(dtf, (float)dE), im), w);
+    u = __fadd_rn(u, du);
+    vx = __fadd_rn(vx, dvx);
+    vy = __fadd_rn(vy, dvy);
+    vz = __fadd_rn(vz, dvz);
+}
+__device__ __forceinline__ float drift_onef(float x, float v_old, float dv, double dt) {
+    return wrapf(__fadd_rn(x, __fmul_rn((float)dt, __fadd_rn(v_old, __fmul_rn(0.5f, dv)))));
+}
 __device__ __forceinline__ void update_one(float m, float& x, float& y, float& z, float& vx,
                                            float& vy, float& vz, float& u, double dpx, double dpy,
                                            double dpz, double dE, double dt) {
-    const float dtf = (float)dt, im = 1.f / m;
-    const float dvx = dtf * (float)dpx * im, dvy = dtf * (float)dpy * im, dvz = dtf * (float)dpz * im;
-    const float hx = vx + 0.5f * dvx, hy = vy + 0.5f * dvy, hz = vz + 0.5f * dvz;
-    const float du = dtf * (float)dE * im - ((dvx * hx + dvy * hy) + dvz * hz);
-    x = wrapf(x + dtf * hx);
-    y = wrapf(y + dtf * hy);
-    z = wrapf(z + dtf * hz);
-    u = u + du;
-    vx += dvx;
-    vy += dvy;
-    vz += dvz;
+    const float ox = vx, oy = vy, oz = vz;
+    float dvx, dvy, dvz;
+    kick_one(m, vx, vy, vz, u, dpx, dpy, dpz, dE, dt, dvx, dvy, dvz);
+    x = drift_onef(x, ox, dvx, dt);
+    y = drift_onef(y, oy, dvy, dt);
+    z = drift_onef(z, oz, dvz, dt);
 }
 
 // MFV (O15): the mass advances too, m' = m + dt dm/dt, and momentum and

@@ -34,12 +34,18 @@ constexpr int kDensCacheLarge = 40, kDensCacheSmall = 48;
 template <typename T, int kDensCache>
 __global__ void __launch_bounds__(kDensBlock)
     k_density(int N, Sorted<T> s, Grid g, KParams p, unsigned* __restrict__ nbr,
-              int* __restrict__ ncount, int* __restrict__ iters, DevStatus* st) {
+              int* __restrict__ ncount, int* __restrict__ iters, DevStatus* st,
+              const int* __restrict__ list, const int* __restrict__ nlist) {
     __shared__ T c_r2[kDensCache][kDensBlock];
     __shared__ unsigned c_j[kDensCache][kDensBlock];
     const int t = threadIdx.x;
-    const int i = blockIdx.x * kDensBlock + t;
-    if (i >= N) return;
+    int i = blockIdx.x * kDensBlock + t;
+    if (list) {  // the particles of an index list only (hierarchical steps)
+        if (i >= *nlist) return;
+        i = list[i];
+    } else if (i >= N) {
+        return;
+    }
     const BoxInfo bx = g.boxes[s.box[i]];
     const P4<T> me = s.pos[i];
     const T xi = me.x, yi = me.y, zi = me.z;
@@ -339,9 +345,16 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
     k_gradients(int N, Sorted<T> s, const unsigned* __restrict__ nbr, const int* __restrict__ ncount,
                 const unsigned* __restrict__ rnbr, const int* __restrict__ rcount, KParams p,
                 T* __restrict__ rec, double* __restrict__ dti, unsigned long long* __restrict__ dtmin,
-                DevStatus* st, int want_dt, T* __restrict__ ginfo, int* __restrict__ lim) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = i < N;
+                DevStatus* st, int want_dt, T* __restrict__ ginfo, int* __restrict__ lim,
+                const int* __restrict__ list, const int* __restrict__ nlist) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool active;
+    if (list) {  // the particles of an index list only (hierarchical steps)
+        active = i < *nlist;
+        i = active ? list[i] : 0;
+    } else {
+        active = i < N;
+    }
     double dt_i = INFINITY;
     int mybox = 0;
     if (active) {
@@ -585,11 +598,21 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
 }
 
 // Builds flux records from caller-supplied gradients and B (caller order).
+// With a list: its particles only, skipping those flagged in skip (the
+// inactive partners of a hierarchical substep, whose gradients and B are
+// those of their last active time).
 template <typename T>
 __global__ void k_pack_given(int N, Sorted<T> s, const T* __restrict__ grad, const T* __restrict__ B,
-                             T* __restrict__ rec) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
+                             T* __restrict__ rec, const int* __restrict__ list,
+                             const int* __restrict__ nlist, const unsigned char* __restrict__ skip) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (list) {
+        if (i >= *nlist) return;
+        i = list[i];
+        if (skip && skip[i]) return;
+    } else if (i >= N) {
+        return;
+    }
     const unsigned o = s.orig[i];
     const T Hi = s.h[i], ni = s.n[i];
     const T iH = T(1) / Hi;
@@ -897,16 +920,20 @@ static Grid grid_of(const Ctx& c) {
 }
 
 template <typename T>
-cudaError_t run_density(Ctx& c) {
+cudaError_t run_density(Ctx& c, const int* list, const int* nlist, int n) {
     c.launches += 1;
+    if (!list) n = c.N;
+    if (n < 1) return cudaSuccess;
     int min_count = c.N;
     for (const BoxInfo& b : c.hboxes) min_count = std::min(min_count, b.count);
     if (min_count >= 32 * 32 * 32)
-        k_density<T, kDensCacheLarge><<<blocks(c.N, kDensBlock), kDensBlock, 0, c.stream>>>(
-            c.N, sorted_view<T>(c), grid_of(c), kparams(c), c.nbr, c.ncount, c.iters, c.status);
+        k_density<T, kDensCacheLarge><<<blocks(n, kDensBlock), kDensBlock, 0, c.stream>>>(
+            c.N, sorted_view<T>(c), grid_of(c), kparams(c), c.nbr, c.ncount, c.iters, c.status, list,
+            nlist);
     else
-        k_density<T, kDensCacheSmall><<<blocks(c.N, kDensBlock), kDensBlock, 0, c.stream>>>(
-            c.N, sorted_view<T>(c), grid_of(c), kparams(c), c.nbr, c.ncount, c.iters, c.status);
+        k_density<T, kDensCacheSmall><<<blocks(n, kDensBlock), kDensBlock, 0, c.stream>>>(
+            c.N, sorted_view<T>(c), grid_of(c), kparams(c), c.nbr, c.ncount, c.iters, c.status, list,
+            nlist);
     return cudaGetLastError();
 }
 
@@ -944,20 +971,25 @@ cudaError_t run_prim(Ctx& c) {
 }
 
 template <typename T>
-cudaError_t run_gradients(Ctx& c, bool want_dt, bool with_info) {
+cudaError_t run_gradients(Ctx& c, bool want_dt, bool with_info, const int* list, const int* nlist, int n) {
     c.launches += want_dt ? 2 : 1;
+    if (!list) n = c.N;
     if (want_dt) k_dt_init<<<blocks(c.nboxes, 256), 256, 0, c.stream>>>(c.nboxes, (unsigned long long*)c.dt_box);
-    k_gradients<T><<<blocks(c.N, 128), 128, 0, c.stream>>>(
+    if (n < 1) return cudaGetLastError();
+    k_gradients<T><<<blocks(n, 128), 128, 0, c.stream>>>(
         c.N, sorted_view<T>(c), c.nbr, c.ncount, c.rnbr, c.rcount, kparams(c), (T*)c.rec, c.dti,
         (unsigned long long*)c.dt_box, c.status, want_dt ? 1 : 0, with_info ? (T*)c.ginfo : nullptr,
-        with_info ? c.lim : nullptr);
+        with_info ? c.lim : nullptr, list, nlist);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t run_pack_given(Ctx& c, const T* grad, const T* B) {
+cudaError_t run_pack_given(Ctx& c, const T* grad, const T* B, const int* list, const int* nlist, int n,
+                           const unsigned char* skip) {
     c.launches += 1;
-    k_pack_given<T><<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, sorted_view<T>(c), grad, B, (T*)c.rec);
+    if (list && n < 1) return cudaSuccess;
+    k_pack_given<T><<<blocks(list ? n : c.N, 256), 256, 0, c.stream>>>(c.N, sorted_view<T>(c), grad, B,
+                                                                     (T*)c.rec, list, nlist, skip);
     return cudaGetLastError();
 }
 
@@ -998,6 +1030,15 @@ cudaError_t run_update(Ctx& c, gz_particles& p, double* rates_out) {
         c.N, sorted_view<T>(c), c.dpdt, c.dEdt, c.params.scheme == GZ_MFV ? c.dmdt : nullptr, c.dt_use, p,
         hits, c.status, rates_out);
     k_ufloor<T><<<c.nboxes, 1024, 0, c.stream>>>(sorted_view<T>(c), c.boxes, hits, p,
+                                                  c.params.u_floor_frac);
+    return cudaGetLastError();
+}
+
+// The u floor of O14 alone (after a kick that flagged box_hits).
+template <typename T>
+cudaError_t run_ufloor(Ctx& c, gz_particles& p) {
+    c.launches += 1;
+    k_ufloor<T><<<c.nboxes, 1024, 0, c.stream>>>(sorted_view<T>(c), c.boxes, c.box_hits, p,
                                                   c.params.u_floor_frac);
     return cudaGetLastError();
 }
@@ -1054,16 +1095,18 @@ cudaError_t run_get_neighbours(Ctx& c, int32_t* count_out, int64_t* ids_out, int
 }
 
 #define GZ_INST(T)                                                   \
-    template cudaError_t run_density<T>(Ctx&);                       \
-    template cudaError_t run_density_given<T>(Ctx&);                 \
-    template cudaError_t run_build_lists<T>(Ctx&);                   \
-    template cudaError_t run_reverse<T>(Ctx&);                       \
-    template cudaError_t run_prim<T>(Ctx&);                          \
-    template cudaError_t run_gradients<T>(Ctx&, bool, bool);         \
-    template cudaError_t run_pack_given<T>(Ctx&, const T*, const T*); \
-    template cudaError_t run_grad_out<T>(Ctx&, T*, T*);              \
-    template cudaError_t run_fluxes<T>(Ctx&);                        \
-    template cudaError_t run_update<T>(Ctx&, gz_particles&, double*);
+    template cudaError_t run_density<T>(Ctx&, const int*, const int*, int);                    \
+    template cudaError_t run_density_given<T>(Ctx&);                                            \
+    template cudaError_t run_build_lists<T>(Ctx&);                                              \
+    template cudaError_t run_reverse<T>(Ctx&);                                                  \
+    template cudaError_t run_prim<T>(Ctx&);                                                     \
+    template cudaError_t run_gradients<T>(Ctx&, bool, bool, const int*, const int*, int);      \
+    template cudaError_t run_pack_given<T>(Ctx&, const T*, const T*, const int*, const int*, int, \
+                                           const unsigned char*);                               \
+    template cudaError_t run_grad_out<T>(Ctx&, T*, T*);                                         \
+    template cudaError_t run_fluxes<T>(Ctx&);                                                   \
+    template cudaError_t run_update<T>(Ctx&, gz_particles&, double*);                          \
+    template cudaError_t run_ufloor<T>(Ctx&, gz_particles&);
 GZ_INST(float)
 GZ_INST(double)
 #undef GZ_INST

@@ -123,6 +123,7 @@ struct Ctx {
         cudaEvent_t a, b;
     };
     std::vector<Pending> pending;
+    cudaEvent_t open_ev[GZ_NPASSES] = {};  // PassTimer::begin events awaiting their end
     double prof_ms[GZ_NPASSES];
     long long prof_calls[GZ_NPASSES];
     long long* pairs_dev;  // scratch for gz_pair_count
@@ -138,6 +139,26 @@ struct Ctx {
     unsigned long long* lbloom = nullptr;  // [N] bit (j & 63) set for each limiter target j
     int* lim = nullptr;       // [N][10] limiter: active neighbour, extreme particle per field
     void* ginfo = nullptr;    // [N][kGInfo] working precision
+    // hierarchical-step scratch, allocated on the first gz_step_hier call
+    void* hier_arena = nullptr;
+    void* hxp = nullptr;      // [3][N] predicted positions (caller order)
+    void* hva = nullptr;      // [3][N] velocity at the start of each particle's step
+    void* hdvs = nullptr;     // [3][N] velocity change since then
+    void* hn = nullptr;       // [N] n of each particle's last active time
+    void* hgrad = nullptr;    // [15][N] limited gradients of that time
+    void* hB = nullptr;       // [6][N] E^-1 of that time
+    int* hsa = nullptr;       // [N] substep its current step started at
+    int* hbin = nullptr;      // [N] bin (caller order)
+    int* sbin = nullptr;      // [N] bin (sorted order)
+    int* alist = nullptr;     // [N] active particles (sorted indices)
+    int* tlist = nullptr;     // [N] particles with an exchange this substep
+    int* hcount = nullptr;    // [4] device counters (predicted actives, |alist|, |tlist|)
+    int* bcount = nullptr;    // per-block counts of the list compaction
+    unsigned char* aflag = nullptr;  // [N] active (sorted order)
+    unsigned char* tflag = nullptr;  // [N] touched (sorted order)
+    unsigned long long* hmax = nullptr;   // [nboxes] largest H (bits)
+    unsigned long long* dtmax = nullptr;  // [nboxes] largest finite criterion (bits)
+    int* hcount_host = nullptr;           // pinned copy of hcount
 };
 
 // ------------------------------------------------------------------ status

@@ -21,8 +21,10 @@ cudaError_t unpermute_d(Ctx& c, const double* src, double* dst, int rows);
 cudaError_t unpermute_i(Ctx& c, const int* src, int* dst);
 
 // Hydro passes (sorted order).
+// list (device, sorted indices) and nlist (device count, at most n): run on
+// those particles only.
 template <typename T>
-cudaError_t run_density(Ctx& c);
+cudaError_t run_density(Ctx& c, const int* list = nullptr, const int* nlist = nullptr, int n = 0);
 template <typename T>
 cudaError_t run_density_given(Ctx& c);
 template <typename T>
@@ -32,16 +34,20 @@ cudaError_t run_reverse(Ctx& c);
 template <typename T>
 cudaError_t run_prim(Ctx& c);
 template <typename T>
-cudaError_t run_gradients(Ctx& c, bool want_dt, bool with_info = false);
+cudaError_t run_gradients(Ctx& c, bool want_dt, bool with_info = false, const int* list = nullptr,
+                          const int* nlist = nullptr, int n = 0);
 template <typename T>
 cudaError_t run_timestep_only(Ctx& c);
 template <typename T>
-cudaError_t run_pack_given(Ctx& c, const T* grad, const T* B);
+cudaError_t run_pack_given(Ctx& c, const T* grad, const T* B, const int* list = nullptr,
+                           const int* nlist = nullptr, int n = 0, const unsigned char* skip = nullptr);
 template <typename T>
 cudaError_t run_fluxes(Ctx& c);
 template <typename T>
 cudaError_t run_update(Ctx& c, gz_particles& p, double* rates_out = nullptr);
 cudaError_t run_rates_in(Ctx& c, const double* rates);
+template <typename T>
+cudaError_t run_ufloor(Ctx& c, gz_particles& p);
 template <typename T>
 cudaError_t run_grad_out(Ctx& c, T* grad_out, T* B_out);
 
@@ -63,5 +69,23 @@ cudaError_t run_adj_out_flux(Ctx& c, double* xbar, double* hbar, double* nbar, d
                              double* Bbar);
 
 KParams kparams(const Ctx& c);
+
+// Per-pass CUDA-event profile (gz_profile_*) for passes launched outside the
+// API layer: begin/end record events on the context stream when profiling is
+// on (implemented with the API layer's event pool).
+struct PassTimer {
+    Ctx* c;
+    void begin(int pass) const;
+    void end(int pass) const;
+};
+
+// Hierarchical timesteps: one sync interval of 2^K substeps in place on p
+// (one host synchronisation per substep to read the number of active
+// particles).  active_out (host) receives the active particle-substeps.
+cudaError_t ensure_hier_scratch(Ctx& c);
+void free_hier_scratch(Ctx& c);
+template <typename T>
+cudaError_t run_step_hier(Ctx& c, gz_particles& p, int K, double dt_fixed, double* dt_used_dev,
+                          int32_t* bins_out, long long* active_out, const PassTimer& timer);
 
 }  // namespace gz
