@@ -66,9 +66,10 @@ def parse():
     ap.add_argument("--cell-factor", type=float, default=None)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-path, adjoint and ensemble measurements")
-    ap.add_argument("--extras", default="all", choices=["all", "adjoint", "variants"],
+    ap.add_argument("--extras", default="all", choices=["all", "adjoint", "variants", "hier"],
                     help="which extra measurements to run (adjoint: only the adjoint cost; "
-                         "variants: only the MFV and exact-Riemann throughputs)")
+                         "variants: only the MFV and exact-Riemann throughputs; hier: only the "
+                         "hierarchical-timestep Sedov comparison)")
     return ap.parse_args()
 
 
@@ -292,7 +293,7 @@ def run_ours(a, world, rank, local):
     line.update(extras)
     if "fp64_path" in line:
         line["fp64_path"]["fp32_over_fp64"] = round(value / world / line["fp64_path"]["value"], 2)
-    for key in ("mfv", "riemann_exact"):
+    for key in ("mfv", "riemann_exact", "riemann_fallback"):
         if key in line:
             line[key]["ms_over_mfm"] = round(line[key]["ms_per_step"] / (tmax / a.steps), 3)
     if "adjoint" in line:
@@ -377,8 +378,9 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p):
         # the scheme variants on the same workload and precision: MFV (mass
         # fluxes through moving faces) and the MFM face with the exact Riemann
         # solver on every face; full steps, per-pass split
-        variants = (("mfv", {"scheme": gz.GZ_MFV}), ("riemann_exact", {"riemann": gz.GZ_RIEMANN_EXACT}))
-        for key, kw in variants:
+        variants = (("mfv", {"scheme": gz.GZ_MFV}), ("riemann_exact", {"riemann": gz.GZ_RIEMANN_EXACT}),
+                    ("riemann_fallback", {"riemann": gz.GZ_RIEMANN_FALLBACK}))
+        for key, kw in (variants if a.extras in ("all", "variants") else ()):
             if a.cell_factor:
                 kw = dict(kw, cell_factor=a.cell_factor)
             cm = gz.Context([p.N], gz.default_params(precision=prec, **kw), stream=stream)
@@ -404,6 +406,10 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p):
             cm.close()
             del dv
         if a.extras == "variants":
+            return out
+        if a.extras in ("all", "hier"):
+            out["hierarchical"] = measure_hier(a, stream, prec)
+        if a.extras == "hier":
             return out
         # the same box further on: 20 more steps from the state the e2e loop
         # left (one step from the initial state), when the particles have left
@@ -476,6 +482,68 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p):
                            "status_ok": ce.status(reset=True)["ok"]}
         ce.close()
     return out
+
+
+def measure_hier(a, stream, prec, K=5, intervals=3):
+    """Sedov blast at the workload's particle count: time to advance the same
+    physical time with hierarchical power-of-two steps (gz_step_hier, K bins,
+    `intervals` sync intervals) and with global CFL steps (gz_step)."""
+    import torch
+
+    import paper_1712_01294_gb300 as gz
+    from paper_1712_01294_gb300 import inputs as I
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    sed = I.sedov(a.n)
+    N = sed.N
+    kw = {"cell_factor": a.cell_factor} if a.cell_factor else {}
+    with torch.cuda.stream(stream):
+        ch = gz.Context([N], gz.default_params(precision=prec, **kw), stream=stream)
+        D = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dw = gz.to_device(sed, prec)
+        ch.step_hier(dw, K, 0.0, D)  # warm-up (allocates the scratch)
+        dh = gz.to_device(sed, prec)
+        ch.profile_read(reset=True)
+        ch.profile(True)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        t_h, active = 0.0, 0
+        for _ in range(intervals):
+            active += ch.step_hier(dh, K, 0.0, D)
+            t_h += float(D.item())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_h = e0.elapsed_time(e1)
+        prof = ch.profile_read(reset=True)
+        ch.profile(False)
+        st_h = ch.status(reset=True)["ok"]
+        cg = gz.Context([N], gz.default_params(precision=prec, **kw), stream=stream)
+        dg = gz.to_device(sed, prec)
+        dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        cg.step(dg, 0.0, dt)  # warm-up on a copy
+        dg = gz.to_device(sed, prec)
+        steps, t_g = 0, 0.0
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        while t_g < t_h and steps < 2000:
+            cg.step(dg, 0.0, dt)
+            t_g += float(dt.item())
+            steps += 1
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_g = e0.elapsed_time(e1)
+        st_g = cg.status(reset=True)["ok"]
+        ch.close()
+        cg.close()
+    return {"workload": f"Sedov blast {a.n}^3 = {N} particles, E = 1 in the 32 central particles",
+            "K": K, "intervals": intervals, "physical_time": round(t_h, 8),
+            "hier_ms": round(ms_h, 3), "global_steps": steps, "global_time": round(t_g, 8),
+            "global_ms": round(ms_g, 3), "speedup": round(ms_g / ms_h, 2),
+            "active_particle_substeps": active,
+            "active_fraction": round(active / (N * intervals * (1 << K)), 4),
+            "hier_pass_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
+            "status_ok": st_h and st_g,
+            "what": "wall time (CUDA events) to advance the same physical time; the hierarchical "
+                    "call synchronises the host once per substep"}
 
 
 def cpu_sample_rate(p, threads=None, sample_frac=1.0 / 8):

@@ -17,11 +17,11 @@
 //     (Hancock with dt_ij/2): each side accumulates rate * 2^(k_a - k_ij)
 //     (exact power-of-two scaling, so the two shares stay equal and opposite)
 //     and kicks momentum and energy by dt_a times that sum.
-// K = 0 is gz_step bitwise.  Pair lists: N_i from the density pass, the pairs
-// with r >= H_i but r < H_j from a scan of radius max(H_i, max H of the box),
-// both for active particles only; an inactive particle's list holds its
-// active partners, written by them (atomic slot counter, then sorted by
-// index, so every sum runs in a fixed order).
+// K = 0 is gz_step bitwise.  Pair lists of an active particle: N_i from the
+// density pass and the pairs with r >= H_i (r < H_j), written by the partner
+// j from a scan of its own support; an inactive particle's list holds its
+// active partners, written by them (atomic slot counters, then every such
+// list sorted by index, so every sum runs in a fixed order).
 #include <math.h>
 
 #include <algorithm>
@@ -169,59 +169,50 @@ __global__ void __launch_bounds__(kCmpBlock)
 }
 
 // --------------------------------------------------------- pair lists
-template <typename T>
-__device__ __forceinline__ unsigned long long hbits(T v) {
-    if constexpr (std::is_same<T, float>::value)
-        return (unsigned long long)__float_as_uint(v);
-    else
-        return (unsigned long long)__double_as_longlong(v);
-}
-template <typename T>
-__device__ __forceinline__ T hval(unsigned long long b) {
-    if constexpr (std::is_same<T, float>::value)
-        return __uint_as_float((unsigned)b);
-    else
-        return __longlong_as_double((long long)b);
+// Cells holding at least one active particle (sorted ranges).
+__global__ void k_h_cellact(int ncells, const int2* __restrict__ cells, const unsigned char* __restrict__ aflag,
+                            unsigned char* __restrict__ cellact) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    const int2 se = cells[c];
+    unsigned char any = 0;
+    for (int i = se.x; i < se.y && !any; ++i) any = aflag[i];
+    cellact[c] = any;
 }
 
-// Largest H of every box (positive values: bit patterns order like values).
-template <typename T>
-__global__ void k_h_hmax(int N, const T* __restrict__ h, const int* __restrict__ box,
-                         unsigned long long* __restrict__ hmax) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const T H = h[i];
-    if (H > T(0)) atomicMax(&hmax[box[i]], hbits<T>(H));
-}
-
-// Active i: the flux pairs j with r >= H_i and r < H_j (O10), in index order
-// after k_h_sort.
+// The flux pairs of active i with r >= H_i (so r < H_j, O10), found from the
+// partner's side: every particle j scans its own support (cells without an
+// active particle skipped) and appends itself to the list of each active i
+// there with r >= H_i; the lists are put in index order by k_h_sort.  r^2 is
+// the bit pattern the density pass forms for the pair, so these lists and
+// N_i split the flux pairs exactly.
 template <typename T>
 __global__ void __launch_bounds__(128)
-    k_h_rlist(const int* __restrict__ alist, const int* __restrict__ nA, Sorted<T> s, Grid g,
-              KParams p, const unsigned long long* __restrict__ hmax, unsigned* __restrict__ rnbr,
-              int* __restrict__ rcount, DevStatus* st) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= *nA) return;
-    const int i = alist[t];
-    const int b = s.box[i];
-    const BoxInfo bx = g.boxes[b];
-    const P4<T> me = s.pos[i];
-    const T Hi = me.w;
-    const T H2 = Hi * Hi;
-    const T R = max(Hi, hval<T>(hmax[b]));
-    int c = 0;
-    for_candidates<T>(g, bx, s.pos, i, me.x, me.y, me.z, R, [&](int j, T, T, T, T r2) {
-        if (!(r2 < H2)) {
-            const T Hj = s.pos[j].w;
-            if (r2 < Hj * Hj) {
-                if (c < p.rcap) rnbr[(size_t)i * p.rcap + c] = (unsigned)j;
-                ++c;
+    k_h_rscatter(int N, Sorted<T> s, Grid g, KParams p, const unsigned char* __restrict__ aflag,
+                 const unsigned char* __restrict__ cellact, unsigned* __restrict__ rnbr,
+                 int* __restrict__ rcount, DevStatus* st) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const BoxInfo bx = g.boxes[s.box[j]];
+    const P4<T> me = s.pos[j];
+    const T Hj = me.w;
+    const T H2 = Hj * Hj;
+    const unsigned char* ca = cellact + bx.cell_off;
+    for_candidates<T>(
+        g, bx, s.pos, j, me.x, me.y, me.z, Hj,
+        [&](int i, T, T, T, T r2) {
+            if (r2 < H2 && aflag[i]) {
+                const T Hi = s.pos[i].w;
+                if (!(r2 < Hi * Hi)) {
+                    const int slot = atomicAdd(&rcount[i], 1);
+                    if (slot < p.rcap)
+                        rnbr[(size_t)i * p.rcap + slot] = (unsigned)j;
+                    else
+                        set_status(st, GZ_S_NBR_OVERFLOW, GZ_C_NBR_OVERFLOW, s.id[i]);
+                }
             }
-        }
-    });
-    rcount[i] = min(c, p.rcap);
-    if (c > p.rcap) set_status(st, GZ_S_NBR_OVERFLOW, GZ_C_NBR_OVERFLOW, s.id[i]);
+        },
+        [&](int lc) { return ca[lc] != 0; });
 }
 
 // Active i appends itself to the list of each inactive partner.
@@ -507,7 +498,7 @@ cudaError_t ensure_hier_scratch(Ctx& c) {
         {(void**)&c.hsa, 4 * Nz},      {(void**)&c.hbin, 4 * Nz},    {(void**)&c.sbin, 4 * Nz},
         {(void**)&c.alist, 4 * Nz},    {(void**)&c.tlist, 4 * Nz},   {(void**)&c.hcount, 4 * 4},
         {(void**)&c.bcount, 4 * nb},   {(void**)&c.aflag, Nz},       {(void**)&c.tflag, Nz},
-        {(void**)&c.hmax, 8 * (size_t)c.nboxes}, {(void**)&c.dtmax, 8 * (size_t)c.nboxes},
+        {(void**)&c.cellact, (size_t)c.total_cells}, {(void**)&c.dtmax, 8 * (size_t)c.nboxes},
     };
     size_t total = 0;
     for (auto& it : items) total += (it.bytes + 255) & ~(size_t)255;
@@ -584,11 +575,10 @@ cudaError_t run_step_hier(Ctx& c, gz_particles& p, int K, double dt_fixed, doubl
             if (e == cudaSuccess) e = run_prim<T>(c);
             timer.end(GZ_PASS_PRIM);
             timer.begin(GZ_PASS_REVERSE);
-            cudaMemsetAsync(c.hmax, 0, 8 * (size_t)c.nboxes, st);
             c.launches += 6;
-            k_h_hmax<T><<<nblk(N, 256), 256, 0, st>>>(N, sv.h, c.sbox, c.hmax);
-            k_h_rlist<T><<<nblk(nA, 128), 128, 0, st>>>(c.alist, c.hcount + 1, sv, g, kp, c.hmax, c.rnbr,
-                                                         c.rcount, c.status);
+            k_h_cellact<<<nblk(c.total_cells, 256), 256, 0, st>>>(c.total_cells, c.cells, c.aflag, c.cellact);
+            k_h_rscatter<T><<<nblk(N, 128), 128, 0, st>>>(N, sv, g, kp, c.aflag, c.cellact, c.rnbr, c.rcount,
+                                                           c.status);
             k_h_inlist<<<nblk(nA, 128), 128, 0, st>>>(c.alist, c.hcount + 1, c.aflag, c.nbr, c.ncount, c.rnbr,
                                                        c.rcount, c.cap, c.rcap, c.sid, c.status);
             k_h_sort<<<nblk(N, 128), 128, 0, st>>>(N, c.aflag, c.ncount, c.nbr, c.cap, c.rcount, c.rnbr,

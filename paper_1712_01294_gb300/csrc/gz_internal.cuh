@@ -156,7 +156,7 @@ struct Ctx {
     int* bcount = nullptr;    // per-block counts of the list compaction
     unsigned char* aflag = nullptr;  // [N] active (sorted order)
     unsigned char* tflag = nullptr;  // [N] touched (sorted order)
-    unsigned long long* hmax = nullptr;   // [nboxes] largest H (bits)
+    unsigned char* cellact = nullptr;     // [cells] cell holds an active particle
     unsigned long long* dtmax = nullptr;  // [nboxes] largest finite criterion (bits)
     int* hcount_host = nullptr;           // pinned copy of hcount
 };
@@ -231,10 +231,13 @@ __device__ __forceinline__ unsigned long long dbits(double v) {
 // (a, b) = (0, x_i), (-1, x_i) for cells wrapped below 0 (x_j - 1 is exact
 // there) or (0, x_i - 1) for cells wrapped above 1 (x_i - 1 is exact): the
 // same correctly rounded offsets mi_diff gives, at a third of the cost.
-template <typename T, typename F>
+struct AllCells {
+    __device__ __forceinline__ bool operator()(int) const { return true; }
+};
+template <typename T, typename F, typename CellOk = AllCells>
 __device__ __forceinline__ void for_candidates(const Grid& g, const BoxInfo& bx,
                                                const P4<T>* __restrict__ pos, int self, T xi, T yi,
-                                               T zi, T R, F&& fn) {
+                                               T zi, T R, F&& fn, CellOk cell_ok = CellOk()) {
     const int nc = bx.nc;
     const int2* __restrict__ cells = g.cells + bx.cell_off;
     // positions outside [0, 1] (flagged by the binning pass) see no candidates
@@ -267,6 +270,7 @@ __device__ __forceinline__ void for_candidates(const Grid& g, const BoxInfo& bx,
             for (int cx = lo[0]; cx <= hi[0]; ++cx) {
                 const int wx = cx < 0 ? cx + nc : (cx >= nc ? cx - nc : cx);
                 const T ax = cx < 0 ? T(-1) : T(0), bxx = cx >= nc ? xim1 : xi;
+                if (!cell_ok(row + wx)) continue;  // (cell index within the box)
                 const int2 se = cells[row + wx];
                 if (percell) {
                     // four candidates' positions in flight at a time
