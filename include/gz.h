@@ -354,6 +354,15 @@ gz_status gz_profile_read(gz_ctx* ctx, double* ms, int64_t* calls, int32_t reset
 gz_status gz_density_noalloc(const gz_params* params, int64_t n, gz_particles* p, void* n_out,
                              int32_t* iters_out, void* cuda_stream);
 
+/* Measured throughput of one SM pipe on the current device (a measurement
+ * aid for the ALU roofline, not part of the method): which = 0 FP32 fused
+ * multiply-add (FLOP/s, 2 per FMA), 1 FP64 fused multiply-add (FLOP/s), 2 FP32
+ * reciprocal square root of the special-function unit (operations/s).
+ * Independent dependency chains over 8 blocks of 256 threads per SM, best of
+ * three timed launches (CUDA events) on cuda_stream; a few milliseconds.
+ * Synchronises the stream.  Errors: GZ_E_INVAL, GZ_E_NOMEM, GZ_E_CUDA. */
+gz_status gz_measure_alu(int32_t which, double* ops_per_s, void* cuda_stream);
+
 /* Text of the last host-side error of this context ("" if none). */
 const char* gz_last_error(gz_ctx* ctx);
 

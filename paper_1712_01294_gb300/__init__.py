@@ -101,6 +101,7 @@ def load_library(build_if_missing: bool = True):
             "gz_pair_count": (st, [vp, vp]),
             "gz_profile_enable": (st, [vp, i32]),
             "gz_profile_read": (st, [vp, vp, vp, i32]),
+            "gz_measure_alu": (st, [i32, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -118,6 +119,23 @@ def default_params(**kw) -> Params:
             raise KeyError(k)
         setattr(p, k, v)
     return p
+
+
+def measure_alu(stream=None):
+    """gz_measure_alu on the current device: measured FP32 and FP64 fused
+    multiply-add throughput (TFLOP/s) and FP32 reciprocal-square-root
+    throughput (T operations/s)."""
+    import torch
+    lib = load_library()
+    st = C.c_void_p((stream if stream is not None else torch.cuda.current_stream()).cuda_stream)
+    out = {}
+    for which, key in ((0, "fp32_fma_tflops"), (1, "fp64_fma_tflops"), (2, "mufu_rsqrt_tops")):
+        v = C.c_double()
+        rc = lib.gz_measure_alu(which, C.byref(v), st)
+        if rc != GZ_OK:
+            raise GZError(rc, "gz_measure_alu failed")
+        out[key] = round(v.value / 1e12, 3)
+    return out
 
 
 def status_names(bits: int):

@@ -77,3 +77,10 @@ def test_autotuner_picks_a_measured_factor(tmp_path):
     best2, ms2 = autotune.tune(q, m.GZ_MIXED32, candidates=(0.8, 1.0, 1.3), steps=1,
                                cache=str(tmp_path / "tune.json"))
     assert best2 == best and ms2 == ms  # served from the cache
+
+
+def test_measured_alu_pipes_are_ordered():
+    m = gz()
+    alu = m.measure_alu()
+    assert alu["fp32_fma_tflops"] > 10 * alu["fp64_fma_tflops"] > 0
+    assert alu["mufu_rsqrt_tops"] > 0
