@@ -239,7 +239,8 @@ def run_ours(a, world, rank, local):
         # measured throughput of the ALU pipes (outside every timed region):
         # context for the derived FP32 peak the roofline divides by
         alu = gz.measure_alu(stream)
-        extras = {} if a.no_extras else measure_extras(a, ctx, d, dtu, stream, prec, p)
+        extras = {} if a.no_extras else measure_extras(a, ctx, d, dtu, stream, prec, p,
+                                                       alu["fp64_fma_tflops"])
     tmax = ms
     if dist:
         tmax, ms_e2e = replica_aggregate([ms, ms_e2e], dist, "cuda")
@@ -318,7 +319,7 @@ def run_ours(a, world, rank, local):
     return line, p
 
 
-def measure_extras(a, ctx, d, dtu, stream, prec, p):
+def measure_extras(a, ctx, d, dtu, stream, prec, p, fp64_peak=None):
     """Adjoint cost, MFV and exact-Riemann throughputs, the evolved state, FP64-path throughput
     and the batched ensemble (CUDA graph)."""
     import numpy as np
@@ -453,6 +454,7 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p):
             c64 = gz.Context([p.N], gz.default_params(precision=gz.GZ_FP64), stream=stream)
             d64 = gz.to_device(p, gz.GZ_FP64)
             c64.step(d64)
+            c64.profile(True)
             e0, e1 = ev(), ev()
             e0.record(stream)
             for _ in range(3):
@@ -460,8 +462,18 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p):
             e1.record(stream)
             torch.cuda.synchronize()
             ms64 = e0.elapsed_time(e1) / 3
+            prof64 = c64.profile_read(reset=True)
+            c64.profile(False)
+            pass64 = {k: round(v[0] / max(v[1], 1), 3) for k, v in prof64.items() if v[1]}
+            # the flux pass against the measured FP64 FMA rate, by the same
+            # algorithmic FLOP as the FP32 roofline
+            pairs64 = c64.pair_count() // 2
+            ach64 = pairs64 * FLOPS_PER_PAIR / (pass64["fluxes"] / 1e3) / 1e12
             out["fp64_path"] = {"value": round(p.N / (ms64 / 1e3), 1), "unit": UNIT,
-                                "ms_per_step": round(ms64, 3), "steps": 3,
+                                "ms_per_step": round(ms64, 3), "steps": 3, "pass_ms_per_step": pass64,
+                                "fluxes_roofline": {"bound": "alu (FP64)", "achieved": round(ach64, 4),
+                                                    "peak_measured": fp64_peak, "unit": "TFLOP/s",
+                                                    "frac": round(ach64 / fp64_peak, 4) if fp64_peak else None},
                                 "status_ok": c64.status(reset=True)["ok"]}
             c64.close()
             del d64
@@ -646,6 +658,14 @@ def main():
                                     "sample": f"one full oracle step of the same {ns}-particle state "
                                               f"(density, gradients, timestep, fluxes, update), "
                                               f"{secs:.1f} s of CPU wall time"}
+            # the same oracle on one host core, on a cubic sub-box of 1/64 of
+            # the state (each pass on the particles it needs there)
+            import oracle as O
+            r1, secs1, ns1, _ = cpu_sample_rate(p, threads=1, sample_frac=1.0 / 64)
+            O.set_threads(cores)
+            line["cpu_baseline_1thread"] = {"value": round(r1, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                            "sample": f"one oracle step of a cubic sub-box of {ns1} particles "
+                                                      f"of the same state, {secs1:.1f} s"}
         print(json.dumps(line), flush=True)
     return 0
 
