@@ -1,0 +1,92 @@
+"""The benchmark's own launch at full size: one gz_step of the 128^3
+turbulence box (2,097,152 particles, FP32 mixed path, one box, default cell
+size), checked against the FP64 oracle on sampled outputs it can compute one
+by one: every particle of four cubic sub-boxes (one of them around the
+particle that sets the CFL step), each oracle pass run on the particles it
+needs there (sub-box plus halos of 2.2 and 4.4 times the largest support).
+Tolerances as in the per-pass parity tests.  FP32: H within 2e-6, per-particle
+timesteps within 1e-5, the step's changes of v and u within 50 x 2e-5 of
+their RMS (RMS error).  FP64 (the same launch in double): h-iteration counts
+equal, H and timesteps within 1e-12, the changes within 1e-10 of their RMS
+(max error)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1712_01294_gb300 import inputs as I
+
+from gpu_common import cast_state, device, field_err, min_image, ostate
+
+pytestmark = pytest.mark.gpu
+
+
+def around(s, centres, half):
+    """Particles within `half` (per axis, periodic) of any centre."""
+    ok = np.zeros(s.N, dtype=bool)
+    for c in centres:
+        m = np.ones(s.N, dtype=bool)
+        for k, ck in zip(("x", "y", "z"), c):
+            m &= np.abs(min_image(getattr(s, k) - ck)) < half
+        ok |= m
+    return ok
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_128cubed_step_matches_oracle_on_sampled_sub_boxes(prec):
+    import torch
+
+    import paper_1712_01294_gb300 as m
+    f64 = prec == m.GZ_FP64
+    q = cast_state(I.turbulence(128, seed=1714), prec)
+    s = ostate(q)
+    ctx = m.Context([q.N], m.default_params(precision=prec))
+    # per-pass view of the step's first passes: converged H, n, per-particle dt
+    dc = device(q, prec)
+    n_g, it_g = ctx.density(dc)
+    it_g = it_g.cpu().numpy()
+    dti, dtb = ctx.timestep(dc, n_g)
+    H_g = dc["h"].cpu().numpy().astype(np.float64)
+    dti = dti.cpu().numpy()
+    kmin = int(np.argmin(dti))
+    # the step itself, as the benchmark launches it
+    d = device(q, prec)
+    dtu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.step(d, 0.0, dtu)
+    st = ctx.status(reset=True)
+    assert st["ok"], st
+    dt = float(dtu.item())
+    assert dt == float(dtb[0].item())
+
+    rng = np.random.default_rng(128)
+    centres = [rng.uniform(0, 1, 3) for _ in range(3)] + [np.array([s.x[kmin], s.y[kmin], s.z[kmin]])]
+    half = 0.02
+    Hm = 1.3 * float(np.max(s.H))
+    m_f, m_g, m_d = around(s, centres, half), around(s, centres, half + 2.2 * Hm), \
+        around(s, centres, half + 4.4 * Hm)
+    assert m_f.sum() > 300 and m_f[kmin]
+    p = O.params()
+    H, n, it_o, _ = O.density(s, p, mask=m_d)
+    H = np.where(m_d, H, s.H)
+    n = np.where(m_d, n, 1.0)
+    assert np.max(np.abs(H_g[m_f] - H[m_f]) / H[m_f]) <= (1e-12 if f64 else 2e-6)
+    if f64:
+        assert np.array_equal(it_g[m_f], it_o[m_f])
+    g = O.gradients(s, H, n, p, mask=m_g)
+    dti_o, _ = O.timestep(s, H, n, p, mask=m_f)
+    tol_dt = 1e-12 if f64 else 1e-5
+    assert np.max(np.abs(dti[m_f] - dti_o[m_f]) / dti_o[m_f]) <= tol_dt
+    assert abs(dt - p.cfl * dti_o[kmin]) <= tol_dt * dt  # the box's CFL step
+    dp, dE = O.fluxes(s, H, n, g["grad"], g["B"], dt, p, mask=m_f)
+    o = O.update(s, dp, dE, dt, p)
+    for k in ("vx", "vy", "vz", "u"):
+        got = d[k].cpu().numpy().astype(np.float64)[m_f] - getattr(s, k)[m_f]
+        ref = getattr(o, k)[m_f] - getattr(s, k)[m_f]
+        mx, rm = field_err(got, ref)
+        assert (mx <= 1e-10) if f64 else (rm <= 50 * 2e-5), (k, mx, rm)
+    for k in ("x", "y", "z"):
+        got = min_image(d[k].cpu().numpy().astype(np.float64)[m_f] - getattr(s, k)[m_f])
+        ref = min_image(getattr(o, k)[m_f] - getattr(s, k)[m_f])
+        mx, rm = field_err(got, ref)
+        assert (mx <= 1e-10) if f64 else (rm <= 50 * 2e-5), (k, mx, rm)
+    assert np.max(np.abs(d["h"].cpu().numpy().astype(np.float64)[m_f] - H[m_f]) / H[m_f]) <= \
+        (1e-12 if f64 else 2e-6)
