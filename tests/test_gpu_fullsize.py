@@ -90,3 +90,62 @@ def test_128cubed_step_matches_oracle_on_sampled_sub_boxes(prec):
         assert (mx <= 1e-10) if f64 else (rm <= 50 * 2e-5), (k, mx, rm)
     assert np.max(np.abs(d["h"].cpu().numpy().astype(np.float64)[m_f] - H[m_f]) / H[m_f]) <= \
         (1e-12 if f64 else 2e-6)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_128cubed_adjoint_of_conserved_totals(prec):
+    """Total momentum and total energy after a step do not depend on the
+    positions and equal their values before it, whatever the state (pairwise
+    equal and opposite fluxes), so the adjoint of the step, seeded with their
+    derivatives (m and m v; m), must return m for the velocities, m v and m
+    for velocities and u, and zero for the positions.  A property of the full
+    launch that holds at any size; checked at the benchmark's 128^3."""
+    import torch
+
+    import paper_1712_01294_gb300 as m
+    q = cast_state(I.turbulence(128, seed=1714), prec)
+    ctx = m.Context([q.N], m.default_params(precision=prec))
+    T = torch.float64 if prec == 0 else torch.float32
+    start = device(q, prec)
+    fwd = device(q, prec)
+    lvl = m.GZ_CKPT_GRADIENTS
+    ck = ctx.new_checkpoint(lvl)
+    dtu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.step(fwd, 0.0, dtu, ck, lvl)
+    dt = float(dtu.item())
+    start["h"] = fwd["h"]
+    mass = start["m"]
+    zeros = lambda: torch.zeros(q.N, dtype=T, device="cuda")
+    tol = 1e-10 if prec == 0 else 2e-4
+    rms = lambda a: float(a.double().pow(2).mean().sqrt())
+    # scale of the position and energy adjoints: a functional with no
+    # conservation law, L = sum r_i vx_i' with random weights r
+    gend = {k: zeros() for k in ("x", "y", "z", "vx", "vy", "vz", "u")}
+    gend["vx"] = (mass * torch.randn(q.N, generator=torch.Generator(device="cuda").manual_seed(3),
+                                     device="cuda", dtype=torch.float64).to(T))
+    ref = {k: zeros() for k in ("x", "y", "z", "vx", "vy", "vz", "u", "m")}
+    ctx.step_backward(start, dt, gend, ref, ck, lvl)
+    assert rms(ref["x"]) > 0 and rms(ref["u"]) > 0
+    # momentum (x component): L = sum m vx'
+    gend = {k: zeros() for k in ("x", "y", "z", "vx", "vy", "vz", "u")}
+    gend["vx"] = mass.clone()
+    gs = {k: zeros() for k in ("x", "y", "z", "vx", "vy", "vz", "u", "m")}
+    ctx.step_backward(start, dt, gend, gs, ck, lvl)
+    assert ctx.status(reset=True)["ok"]
+    rel = lambda a, b: float((a.double() - b.double()).norm() / b.double().norm())
+    assert rel(gs["vx"], mass) <= tol
+    for k in ("x", "y", "z", "vy", "vz", "u"):
+        assert rms(gs[k]) <= tol * rms(ref[k] if k in ("x", "y", "z", "u") else ref["vx"]), k
+    # total energy: L = sum m (u' + |v'|^2 / 2)
+    gend = {k: zeros() for k in ("x", "y", "z")}
+    for k in ("vx", "vy", "vz"):
+        gend[k] = mass * fwd[k]
+    gend["u"] = mass.clone()
+    gs = {k: zeros() for k in ("x", "y", "z", "vx", "vy", "vz", "u", "m")}
+    ctx.step_backward(start, dt, gend, gs, ck, lvl)
+    assert ctx.status(reset=True)["ok"]
+    for k in ("vx", "vy", "vz"):
+        assert rel(gs[k], mass * start[k]) <= 10 * tol, k
+    assert rel(gs["u"], mass) <= tol
+    for k in ("x", "y", "z"):
+        assert rms(gs[k]) <= 10 * tol * rms(ref[k]) * rms(fwd["vx"]), k  # seeds m v against m r
