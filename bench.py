@@ -313,9 +313,11 @@ def run_ours(a, world, rank, local):
     if "adjoint" in line:
         adj = line["adjoint"]
         adj["forward_ms_per_step"] = round(tmax / a.steps, 4)
-        # (forward that saves the checkpoint + backward) / plain forward
+        # (forward that saves the checkpoint + backward) / plain forward, the
+        # plain forward timed on the same states (those after the timed steps)
         adj["total_over_forward"] = round(
-            (adj["forward_with_checkpoint_ms_per_step"] + adj["backward_ms_per_step"]) / (tmax / a.steps), 3)
+            (adj["forward_with_checkpoint_ms_per_step"] + adj["backward_ms_per_step"])
+            / adj["forward_same_states_ms_per_step"], 3)
     return line, p
 
 
@@ -343,6 +345,17 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p, fp64_peak=None):
             level = gz.GZ_CKPT_GRADIENTS
             ck = ctx.new_checkpoint(level)
             K = max(2, a.steps // 2)
+            # the plain forward over the same K steps (the denominator of the
+            # cost ratio: the same states as the checkpointing forward below)
+            fwd = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in start.items()}
+            ctx.step(fwd, 0.0, dtu)
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            for _ in range(K):
+                ctx.step(fwd, 0.0, dtu)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_fwd_plain = e0.elapsed_time(e1) / K
             fwd = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in start.items()}
             ctx.step(fwd, 0.0, dtu, ck, level)
             e0, e1 = ev(), ev()
@@ -379,6 +392,7 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p, fp64_peak=None):
             st = ctx.status(reset=True)
             out["adjoint"] = {"backward_ms_per_step": round(ms_bwd, 4),
                               "forward_with_checkpoint_ms_per_step": round(ms_fwd_ckpt, 4),
+                              "forward_same_states_ms_per_step": round(ms_fwd_plain, 4),
                               "checkpoint_bytes_per_particle": round(ctx.checkpoint_bytes(level) / p.N, 1),
                               "backward_full_recompute_ms_per_step": round(ms_bwd_full, 4),
                               "steps": K, "status_ok": st["ok"],
@@ -425,10 +439,9 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p, fp64_peak=None):
             out["hierarchical"] = measure_hier(a, stream, prec)
         if a.extras == "hier":
             return out
-        # the same box further on: 20 more steps from the state the e2e loop
-        # left (one step from the initial state), when the particles have left
-        # the initial lattice (whose regular cell occupancy the density scan
-        # profits from), then 10 timed
+        # the same box further on: 20 more steps from the state the timed loop
+        # left, when the particles have left the initial lattice (whose regular
+        # cell occupancy the density scan profits from), then 10 timed
         ev_state = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in d.items()}
         for _ in range(20):
             ctx.step(ev_state, 0.0, dtu)
@@ -444,7 +457,7 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p, fp64_peak=None):
         ctx.profile(False)
         ms_ev = e0.elapsed_time(e1) / 10
         out["evolved_state"] = {"value": round(p.N / (ms_ev / 1e3), 1), "unit": UNIT,
-                                "ms_per_step": round(ms_ev, 4), "steps_before": 21,
+                                "ms_per_step": round(ms_ev, 4), "steps_before": a.warmup + a.steps + 20,
                                 "steps": 10, "status_ok": ctx.status(reset=True)["ok"],
                                 "pass_ms_per_step": {k: round(v[0] / max(v[1], 1), 4)
                                                      for k, v in prof_ev.items() if v[1]}}
