@@ -78,19 +78,22 @@ def test_one_bin_interval_is_one_fixed_step_bitwise(prec):
         assert np.array_equal(sa[k], sb[k]), k
 
 
-@pytest.mark.parametrize("kind,n,K", [("turb", 14, 2), ("sedov", 15, 4)])
-def test_fp64_interval_follows_the_oracle(kind, n, K):
+@pytest.mark.parametrize("kind,n,K,fixed", [("turb", 14, 2, 0.0), ("sedov", 15, 4, 0.0),
+                                            ("turb", 13, 3, 0.02)])
+def test_fp64_interval_follows_the_oracle(kind, n, K, fixed):
+    """fixed > 0: the interval is given (0.02 is about four CFL steps of this
+    box, so its particles spread over the deeper bins)."""
     import torch
     m = gz()
     q = cast_state(make(kind, n), m.GZ_FP64)
     s = ostate(q)
-    o, D_o, bins_o, na_o = O.step_hier(s, O.params(), K)
+    o, D_o, bins_o, na_o = O.step_hier(s, O.params(), K, dt=fixed)
     assert len(np.unique(bins_o)) > 1
     ctx = ctx_for(q.N, m.GZ_FP64)
     d = device(q, m.GZ_FP64)
     D = torch.zeros(1, dtype=torch.float64, device="cuda")
     bins = torch.zeros(q.N, dtype=torch.int32, device="cuda")
-    na = ctx.step_hier(d, K, 0.0, D, bins)
+    na = ctx.step_hier(d, K, fixed, D, bins)
     st = ctx.status(reset=True)
     assert st["ok"], st
     assert abs(float(D.item()) - D_o) <= 1e-12 * D_o
