@@ -482,6 +482,7 @@ gz_status gz_create(const gz_params* params, int32_t nboxes, const int64_t* coun
         {(void**)&c.ncount, 4 * Nz},      {(void**)&c.nbr, 4 * Nz * (size_t)c.cap},
         {(void**)&c.rcount, 4 * Nz},      {(void**)&c.rnbr, 4 * Nz * (size_t)c.rcap},
         {(void**)&c.rec, sz * Nz * kRecord},
+        {(void**)&c.defer, 4 * Nz},       {(void**)&c.ndefer, 4},
         {(void**)&c.dpdt, 8 * 3 * Nz},    {(void**)&c.dEdt, 8 * Nz},
         {(void**)&c.dmdt, params->scheme == GZ_MFV ? 8 * Nz : 0},
         {(void**)&c.dti, 8 * Nz},         {(void**)&c.dt_box, 8 * (size_t)nboxes},

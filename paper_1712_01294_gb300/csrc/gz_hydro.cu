@@ -35,7 +35,8 @@ template <typename T, int kDensCache>
 __global__ void __launch_bounds__(kDensBlock)
     k_density(int N, Sorted<T> s, Grid g, KParams p, unsigned* __restrict__ nbr,
               int* __restrict__ ncount, int* __restrict__ iters, DevStatus* st,
-              const int* __restrict__ list, const int* __restrict__ nlist) {
+              const int* __restrict__ list, const int* __restrict__ nlist, int* __restrict__ defer,
+              int* __restrict__ ndefer) {
     __shared__ T c_r2[kDensCache][kDensBlock];
     __shared__ unsigned c_j[kDensCache][kDensBlock];
     const int t = threadIdx.x;
@@ -82,6 +83,13 @@ __global__ void __launch_bounds__(kDensBlock)
             Rc = R;
             ncache = n;
             cached = n <= kDensCache;
+            if (!cached && defer) {
+                // more candidates than the cache holds (a support spanning many
+                // cells): left to k_density_warp, where a whole warp scans for
+                // it and runs the iteration again from the starting H
+                defer[atomicAdd(ndefer, 1)] = i;
+                return;
+            }
         }
         Acc<T> sw;
         T sd = T(0);
@@ -190,6 +198,148 @@ __global__ void __launch_bounds__(kDensBlock)
         if (clamped) atomicOr(&st->bits, GZ_S_HLIM);
     }
     if (cnt > p.cap) set_status(st, GZ_S_NBR_OVERFLOW, GZ_C_NBR_OVERFLOW, s.id[i]);
+}
+
+// The particles k_density deferred (more candidates within 1.05 H than its
+// cache holds): one warp per particle, the same bracketed Newton iteration,
+// each evaluation a warp-cooperative scan of the cells (lanes over the
+// candidates of a cell, sums reduced across the warp in FP64, so every lane
+// holds the same totals and takes the same steps); the neighbour list of the
+// returned H in scan order (ballot-compacted).  Grid-stride over the deferred
+// list, whose length only the device knows.
+constexpr int kWarpDensBlock = 128;
+
+template <typename T>
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kWarpDensBlock)
+    k_density_warp(int N, Sorted<T> s, Grid g, KParams p, unsigned* __restrict__ nbr,
+                   int* __restrict__ ncount, int* __restrict__ iters, DevStatus* st,
+                   const int* __restrict__ defer, const int* __restrict__ ndefer) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (kWarpDensBlock / 32);
+    const int nd = *ndefer;
+    for (int w = blockIdx.x * (kWarpDensBlock / 32) + (threadIdx.x >> 5); w < nd; w += warps) {
+        const int i = defer[w];
+        const BoxInfo bx = g.boxes[s.box[i]];
+        const P4<T> me = s.pos[i];
+        const T xi = me.x, yi = me.y, zi = me.z;
+        double H = (double)s.h[i];
+        if (!(H > 0.0) || !(H < p.h_lim)) {  // (flagged by k_density)
+            H = cbrt(3.0 * p.ngb / (4.0 * kPi * (double)bx.count));
+            if (!(H < p.h_lim)) H = 0.5 * p.h_lim;
+        }
+        const double C = 32.0 / 3.0;
+        double lo = 0.0, hi = 0.0, S = 0.0, Hev = H;
+        bool has_lo = false, has_hi = false, conv = false, clamped = false;
+        T sd_last = T(0);
+        int it, cnt = 0;
+        for (it = 1; it <= p.max_iter; ++it) {
+            const T Ht = (T)H;
+            const T H2 = Ht * Ht;
+            const T iH = T(1) / Ht;
+            Acc<T> sw;
+            T sd = T(0);
+            int c = 0;
+            for_candidates_warp<T>(g, bx, s.pos, i, xi, yi, zi, Ht, lane,
+                                   [&](int, bool valid, T, T, T, T r2) {
+                                       if (valid && r2 < H2) {
+                                           const T q = sqrt(r2) * iH;
+                                           sw.add(kern_w(q));
+                                           sd += -kern_dw(q) * q;
+                                           ++c;
+                                       }
+                                   });
+            const double Sw = warp_sum<T>(sw.value());
+            const T sdw = (T)warp_sum<T>((double)sd);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+            cnt = c;
+            sd_last = sdw;
+            Hev = (double)Ht;
+            double f;
+            if constexpr (std::is_same<T, float>::value) {
+                const float Sf = (float)Sw;
+                S = (double)Sf;
+                f = (double)((32.f / 3.f) * (1.f + Sf) - (float)p.ngb);
+            } else {
+                S = Sw;
+                f = C * (1.0 + S) - p.ngb;
+            }
+            if (fabs(f) <= p.tol * p.ngb) {
+                conv = true;
+                break;
+            }
+            if (it == p.max_iter) break;
+            if (f < 0.0) {
+                lo = Hev;
+                has_lo = true;
+            } else {
+                hi = Hev;
+                has_hi = true;
+            }
+            const double lo_eff = has_lo ? lo : 0.5 * Hev;
+            const double hi_eff = has_hi ? hi : 2.0 * Hev;
+            double Hn = 0.0;
+            bool ok = false;
+            if (std::is_same<T, float>::value) {
+                const float fpf = (float)C * (float)sdw / Ht;
+                if (fpf > 0.f) {
+                    Hn = Hev - (double)((float)f / fpf);
+                    ok = (Hn > lo_eff) && (Hn < hi_eff);
+                }
+            } else {
+                const double fp = C * (double)sdw / Hev;
+                if (fp > 0.0) {
+                    Hn = Hev - f / fp;
+                    ok = (Hn > lo_eff) && (Hn < hi_eff);
+                }
+            }
+            if (!ok) Hn = (has_lo && has_hi) ? 0.5 * (lo + hi) : (f < 0.0 ? 2.0 * Hev : 0.5 * Hev);
+            if (Hn >= p.h_lim) {
+                Hn = 0.5 * (Hev + p.h_lim);
+                clamped = true;
+            }
+            H = Hn;
+        }
+        if (it > p.max_iter) it = p.max_iter;
+        {  // list of the returned H, in scan order
+            const T Ht = (T)Hev;
+            const T H2 = Ht * Ht;
+            int c = 0;
+            for_candidates_warp<T>(g, bx, s.pos, i, xi, yi, zi, Ht, lane,
+                                   [&](int j, bool valid, T, T, T, T r2) {
+                                       const bool in = valid && r2 < H2;
+                                       const unsigned b = __ballot_sync(0xffffffffu, in);
+                                       const int slot = c + __popc(b & ((1u << lane) - 1u));
+                                       if (in && slot < p.cap) nbr[(size_t)i * p.cap + slot] = (unsigned)j;
+                                       c += __popc(b);
+                                   });
+        }
+        if (lane == 0) {
+            s.h[i] = (T)Hev;
+            if (std::is_same<T, float>::value) {
+                const float Hf = (float)Hev;
+                s.n[i] = (T)(8.f * (float)(1.0 + S) / ((float)kPi * Hf * Hf * Hf));
+            } else {
+                s.n[i] = (T)(8.0 * (1.0 + S) / (kPi * Hev * Hev * Hev));
+            }
+            if (s.sd) s.sd[i] = sd_last;
+            iters[i] = it;
+            ncount[i] = cnt;
+            if (!conv) {
+                set_status(st, GZ_S_HCONV, GZ_C_HCONV, s.id[i]);
+                if (clamped) atomicOr(&st->bits, GZ_S_HLIM);
+            }
+            if (cnt > p.cap) set_status(st, GZ_S_NBR_OVERFLOW, GZ_C_NBR_OVERFLOW, s.id[i]);
+        }
+        __syncwarp();
+    }
 }
 
 // Neighbour lists N_i = {j : r_ij < H_i} for given H (O3).
@@ -921,19 +1071,26 @@ static Grid grid_of(const Ctx& c) {
 
 template <typename T>
 cudaError_t run_density(Ctx& c, const int* list, const int* nlist, int n) {
-    c.launches += 1;
     if (!list) n = c.N;
     if (n < 1) return cudaSuccess;
     int min_count = c.N;
     for (const BoxInfo& b : c.hboxes) min_count = std::min(min_count, b.count);
+    const Sorted<T> sv = sorted_view<T>(c);
+    c.launches += c.defer ? 2 : 1;
+    if (c.defer) cudaMemsetAsync(c.ndefer, 0, sizeof(int), c.stream);
     if (min_count >= 32 * 32 * 32)
         k_density<T, kDensCacheLarge><<<blocks(n, kDensBlock), kDensBlock, 0, c.stream>>>(
-            c.N, sorted_view<T>(c), grid_of(c), kparams(c), c.nbr, c.ncount, c.iters, c.status, list,
-            nlist);
+            c.N, sv, grid_of(c), kparams(c), c.nbr, c.ncount, c.iters, c.status, list, nlist, c.defer,
+            c.ndefer);
     else
         k_density<T, kDensCacheSmall><<<blocks(n, kDensBlock), kDensBlock, 0, c.stream>>>(
-            c.N, sorted_view<T>(c), grid_of(c), kparams(c), c.nbr, c.ncount, c.iters, c.status, list,
-            nlist);
+            c.N, sv, grid_of(c), kparams(c), c.nbr, c.ncount, c.iters, c.status, list, nlist, c.defer,
+            c.ndefer);
+    if (c.defer) {
+        const int wb = std::max(1, std::min(blocks(n, kWarpDensBlock / 32), 152 * 16));
+        k_density_warp<T><<<wb, kWarpDensBlock, 0, c.stream>>>(c.N, sv, grid_of(c), kparams(c), c.nbr, c.ncount,
+                                                                c.iters, c.status, c.defer, c.ndefer);
+    }
     return cudaGetLastError();
 }
 

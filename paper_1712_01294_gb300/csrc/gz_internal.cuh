@@ -104,6 +104,8 @@ struct Ctx {
     int* rcount;
     unsigned* rnbr;  // [N][rcap]
     void* rec;       // [N][kRecord] working precision
+    int* defer = nullptr;   // [N] particles the density pass leaves to its warp-per-particle kernel
+    int* ndefer = nullptr;  // [1] their number
     double* dpdt;    // [3][N] sorted
     double* dEdt;    // [N] sorted
     double* dmdt;    // [N] sorted (GZ_MFV only, else null)
@@ -307,6 +309,60 @@ __device__ __forceinline__ void for_candidates(const Grid& g, const BoxInfo& bx,
                             fn(j, dx, dy, dz, sep2(dx, dy, dz));
                         }
                     }
+                }
+            }
+        }
+    }
+}
+
+// Warp-cooperative for_candidates for one particle per warp (every lane
+// passes the same particle): the same cells in the same order; within a cell
+// the lanes take the candidates start + lane, start + 32 + lane, ... in rounds
+// that every lane runs, calling fn(j, valid, dx, dy, dz, r2) each round
+// (valid = false past the cell's end and for the particle itself).  Offsets
+// as in for_candidates (mi_diff; every offset is correctly rounded).
+template <typename T, typename F>
+__device__ __forceinline__ void for_candidates_warp(const Grid& g, const BoxInfo& bx,
+                                                    const P4<T>* __restrict__ pos, int self, T xi, T yi,
+                                                    T zi, T R, int lane, F&& fn) {
+    const int nc = bx.nc;
+    const int2* __restrict__ cells = g.cells + bx.cell_off;
+    if (!(xi >= T(0) && xi <= T(1) && yi >= T(0) && yi <= T(1) && zi >= T(0) && zi <= T(1) &&
+          R >= T(0)))
+        return;
+    const bool full = !(R < T(0.5));
+    const T c3[3] = {xi, yi, zi};
+    int lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = full ? 0 : (int)floor((c3[a] - R) * (T)nc - T(1e-3));
+        hi[a] = full ? nc - 1 : (int)floor((c3[a] + R) * (T)nc + T(1e-3));
+        if (hi[a] - lo[a] + 1 >= nc) {
+            lo[a] = 0;
+            hi[a] = nc - 1;
+        }
+    }
+    const T xim1 = xi - T(1), yim1 = yi - T(1), zim1 = zi - T(1);
+    for (int cz = lo[2]; cz <= hi[2]; ++cz) {
+        const int wz = cz < 0 ? cz + nc : (cz >= nc ? cz - nc : cz);
+        for (int cy = lo[1]; cy <= hi[1]; ++cy) {
+            const int wy = cy < 0 ? cy + nc : (cy >= nc ? cy - nc : cy);
+            const int row = (wz * nc + wy) * nc;
+            for (int cx = lo[0]; cx <= hi[0]; ++cx) {
+                const int wx = cx < 0 ? cx + nc : (cx >= nc ? cx - nc : cx);
+                const int2 se = cells[row + wx];
+                for (int j0 = se.x; j0 < se.y; j0 += 32) {
+                    const int j = j0 + lane;
+                    const bool valid = j < se.y && j != self;
+                    T dx = T(0), dy = T(0), dz = T(0), r2 = T(0);
+                    if (valid) {
+                        const P4<T> q = pos[j];
+                        dx = mi_diff(q.x, xi, xim1);
+                        dy = mi_diff(q.y, yi, yim1);
+                        dz = mi_diff(q.z, zi, zim1);
+                        r2 = sep2(dx, dy, dz);
+                    }
+                    fn(j, valid, dx, dy, dz, r2);
                 }
             }
         }
