@@ -262,16 +262,28 @@ __device__ __forceinline__ void for_candidates(const Grid& g, const BoxInfo& bx,
     }
     const T xim1 = xi - T(1), yim1 = yi - T(1), zim1 = zi - T(1);
     const bool percell = sizeof(T) == 4 && !wraps_all && (T(2) * R + T(2) / (T)nc < T(0.5));
+    // cells whose nearest point lies beyond R hold no candidate: skipped (the
+    // gap of each axis from the cell's unwrapped extent; the margin covers the
+    // rounding of the cell bounds; no pruning when the range wraps the box)
+    const T cl = T(1) / (T)nc, R2m = R * R * T(1.0001);
     for (int cz = lo[2]; cz <= hi[2]; ++cz) {
         const int wz = cz < 0 ? cz + nc : (cz >= nc ? cz - nc : cz);
         const T az = cz < 0 ? T(-1) : T(0), bz = cz >= nc ? zim1 : zi;
+        const T gz = wraps_all ? T(0) : max(max((T)cz * cl - zi, zi - (T)(cz + 1) * cl), T(0));
+        const T gz2 = gz * gz;
+        if (gz2 > R2m) continue;
         for (int cy = lo[1]; cy <= hi[1]; ++cy) {
             const int wy = cy < 0 ? cy + nc : (cy >= nc ? cy - nc : cy);
             const T ay = cy < 0 ? T(-1) : T(0), by = cy >= nc ? yim1 : yi;
+            const T gy = wraps_all ? T(0) : max(max((T)cy * cl - yi, yi - (T)(cy + 1) * cl), T(0));
+            const T gzy2 = gz2 + gy * gy;
+            if (gzy2 > R2m) continue;
             const int row = (wz * nc + wy) * nc;
             for (int cx = lo[0]; cx <= hi[0]; ++cx) {
                 const int wx = cx < 0 ? cx + nc : (cx >= nc ? cx - nc : cx);
                 const T ax = cx < 0 ? T(-1) : T(0), bxx = cx >= nc ? xim1 : xi;
+                const T gx = wraps_all ? T(0) : max(max((T)cx * cl - xi, xi - (T)(cx + 1) * cl), T(0));
+                if (gzy2 + gx * gx > R2m) continue;
                 if (!cell_ok(row + wx)) continue;  // (cell index within the box)
                 const int2 se = cells[row + wx];
                 if (percell) {
