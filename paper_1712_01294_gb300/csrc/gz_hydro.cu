@@ -1087,7 +1087,7 @@ cudaError_t run_density(Ctx& c, const int* list, const int* nlist, int n) {
             c.N, sv, grid_of(c), kparams(c), c.nbr, c.ncount, c.iters, c.status, list, nlist, c.defer,
             c.ndefer);
     if (c.defer) {
-        const int wb = std::max(1, std::min(blocks(n, kWarpDensBlock / 32), 152 * 16));
+        const int wb = std::max(1, std::min(blocks(n, kWarpDensBlock / 32), 152 * 4));
         k_density_warp<T><<<wb, kWarpDensBlock, 0, c.stream>>>(c.N, sv, grid_of(c), kparams(c), c.nbr, c.ncount,
                                                                 c.iters, c.status, c.defer, c.ndefer);
     }
