@@ -243,9 +243,9 @@ gz_status gz_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
  * number of active particle-substeps.  Host synchronisation: one per substep
  * (the number of active particles sizes the launches; substeps without one
  * only drift), so the call cannot be captured in a CUDA graph.  Scratch of
- * about 150 bytes a particle (FP32) is allocated on the first call.  Errors:
- * GZ_E_INVAL (K out of range, GZ_MFV or a Riemann option other than
- * GZ_RIEMANN_HLLC), GZ_E_NOMEM. */
+ * about 150 bytes a particle (FP32) is allocated on the first call.  Every
+ * Riemann option of the MFM face applies.  Errors: GZ_E_INVAL (K out of
+ * range, GZ_MFV), GZ_E_NOMEM. */
 gz_status gz_step_hier(gz_ctx* ctx, gz_particles* p, int32_t K, double dt_fixed, double* dt_used_dev,
                        int32_t* bins_out, int64_t* active_out);
 

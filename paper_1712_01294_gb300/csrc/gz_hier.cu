@@ -17,6 +17,7 @@
 //     (Hancock with dt_ij/2): each side accumulates rate * 2^(k_a - k_ij)
 //     (exact power-of-two scaling, so the two shares stay equal and opposite)
 //     and kicks momentum and energy by dt_a times that sum.
+// Any Riemann option of the MFM face (the exchange uses pair_rates with it).
 // K = 0 is gz_step bitwise.  Pair lists of an active particle: N_i from the
 // density pass and the pairs with r >= H_i (r < H_j), written by the partner
 // j from a scan of its own support; an inactive particle's list holds its
@@ -342,8 +343,8 @@ constexpr int kXBlock = 128;
 // r >= H_i pairs; an inactive one: its active partners): the pair's face
 // fluxes with the Hancock half step of dt_ij, scaled by 2^(k_i - k_ij),
 // summed like the flux pass (working precision over runs of 8 pairs, then
-// FP64).
-template <typename T>
+// FP64).  kRiem: the MFM face's Riemann solver (pair_rates).
+template <typename T, int kRiem>
 __global__ void __launch_bounds__(kXBlock)
     k_h_exchange(const int* __restrict__ tlist, const int* __restrict__ nT, const T* __restrict__ rec,
                  const long long* __restrict__ sid, const int* __restrict__ sbox,
@@ -378,7 +379,7 @@ __global__ void __launch_bounds__(kXBlock)
             hancock_inc(a, hdt, gam, hancock, inca);
             T dp[3], dE, dm;
             int fl = 0;
-            if (pair_rates<T, false, GZ_RIEMANN_HLLC>(a, b, idi < sid[j], hdt, gam, hancock, inca, dp, dE,
+            if (pair_rates<T, false, kRiem>(a, b, idi < sid[j], hdt, gam, hancock, inca, dp, dE,
                                                       dm, fl)) {
                 const T sc = (T)ldexp(1.0, ka - kab);
                 part[0] += dp[0] * sc;
@@ -481,6 +482,22 @@ __global__ void k_h_finalize(int N, int s, int K, gz_particles p, T* __restrict_
     }
     hsa[o] = s + 1;
     if (!ok) set_status(st, GZ_S_NONFINITE, GZ_C_NONFINITE, (long long)p.id[o]);
+}
+
+template <typename T>
+void launch_exchange(Ctx& c, const KParams& kp, int N) {
+    const int r = c.params.riemann;
+    auto go = [&](auto kernel) {
+        kernel<<<nblk(N, kXBlock), kXBlock, 0, c.stream>>>(c.tlist, c.hcount + 2, (const T*)c.rec, c.sid, c.sbox,
+                                                           c.sbin, c.nbr, c.ncount, c.rnbr, c.rcount, kp, c.dt_use,
+                                                           c.dpdt, c.dEdt, N, c.status);
+    };
+    if (r == GZ_RIEMANN_EXACT)
+        go(k_h_exchange<T, GZ_RIEMANN_EXACT>);
+    else if (r == GZ_RIEMANN_FALLBACK)
+        go(k_h_exchange<T, GZ_RIEMANN_FALLBACK>);
+    else
+        go(k_h_exchange<T, GZ_RIEMANN_HLLC>);
 }
 
 }  // namespace
@@ -610,9 +627,7 @@ cudaError_t run_step_hier(Ctx& c, gz_particles& p, int K, double dt_fixed, doubl
             timer.end(GZ_PASS_GRAD);
             timer.begin(GZ_PASS_FLUX);
             c.launches += 1;
-            k_h_exchange<T><<<nblk(N, kXBlock), kXBlock, 0, st>>>(
-                c.tlist, c.hcount + 2, (const T*)c.rec, c.sid, c.sbox, c.sbin, c.nbr, c.ncount, c.rnbr,
-                c.rcount, kp, c.dt_use, c.dpdt, c.dEdt, N, c.status);
+            launch_exchange<T>(c, kp, N);
             timer.end(GZ_PASS_FLUX);
             timer.begin(GZ_PASS_UPDATE);
             cudaMemsetAsync(c.box_hits, 0, sizeof(int) * (size_t)c.nboxes, st);

@@ -109,6 +109,26 @@ def test_fp64_interval_follows_the_oracle(kind, n, K, fixed):
     assert np.max(np.abs(d["h"].cpu().numpy() - o.H) / o.H) <= 1e-12
 
 
+@pytest.mark.parametrize("riemann", [1, 2])
+def test_fp64_interval_with_the_exact_riemann_options_follows_the_oracle(riemann):
+    import torch
+    m = gz()
+    q = cast_state(I.sod(12, rho_l=1.0, p_l=0.4, rho_r=1.0, p_r=0.4, u_l=-2.0, u_r=2.0), m.GZ_FP64)
+    s = ostate(q)
+    o, D_o, bins_o, na_o = O.step_hier(s, O.params(riemann=riemann), 2)
+    ctx = ctx_for(q.N, m.GZ_FP64, riemann=riemann)
+    d = device(q, m.GZ_FP64)
+    D = torch.zeros(1, dtype=torch.float64, device="cuda")
+    bins = torch.zeros(q.N, dtype=torch.int32, device="cuda")
+    na = ctx.step_hier(d, 2, 0.0, D, bins)
+    assert ctx.status(reset=True)["ok"]
+    assert abs(float(D.item()) - D_o) <= 1e-12 * D_o and na == na_o
+    assert np.array_equal(bins.cpu().numpy(), bins_o)
+    for k in ("vx", "vy", "vz", "u"):
+        mx, _ = field_err(d[k].cpu().numpy() - getattr(s, k), getattr(o, k) - getattr(s, k))
+        assert mx <= 1e-9, (k, mx)
+
+
 def test_fp32_interval_within_tolerance_of_the_oracle():
     import torch
     m = gz()
