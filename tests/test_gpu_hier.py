@@ -223,3 +223,35 @@ def test_batched_boxes_equal_single_boxes():
         for k in FIELDS:
             assert np.array_equal(d[k].cpu().numpy()[off:off + qb.N], singles[b][k]), (b, k)
         off += qb.N
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_lone_particle_box_beside_a_normal_box_without_fault(scheme):
+    """A one-particle box (no neighbours: the h-iteration cannot converge, no
+    flux pair, an infinite criterion) batched with a normal box: the flags
+    are reported and the normal box steps as it does alone."""
+    import torch
+    m = gz()
+    q = cast_state(I.turbulence(10, seed=12), m.GZ_MIXED32)
+    lone = {k: torch.full((1,), v, dtype=torch.float32, device="cuda") for k, v in
+            (("x", 0.5), ("y", 0.5), ("z", 0.5), ("vx", 0.0), ("vy", 0.0), ("vz", 0.0), ("m", 1.0),
+             ("u", 1.0), ("h", 0.1))}
+    alone = device(q, m.GZ_MIXED32)
+    ctx1 = ctx_for(q.N, m.GZ_MIXED32, scheme=scheme, max_iter=20)
+    if scheme == 0:
+        ctx1.step_hier(alone, 2)
+    else:
+        ctx1.step(alone)
+    assert ctx1.status(reset=True)["ok"]
+    d = device(q, m.GZ_MIXED32)
+    both = {k: torch.cat([d[k], lone[k]]) for k in lone}
+    both["id"] = torch.cat([d["id"], torch.tensor([10 ** 6], dtype=torch.int64, device="cuda")])
+    ctx = ctx_for([q.N, 1], m.GZ_MIXED32, scheme=scheme, max_iter=20)
+    if scheme == 0:
+        ctx.step_hier(both, 2)
+    else:
+        ctx.step(both)
+    st = ctx.status(reset=True)
+    assert "hconv" in st["bits"]
+    for k in ("x", "vx", "u", "h"):
+        assert torch.equal(both[k][:q.N], alone[k]), k
