@@ -121,7 +121,7 @@ def _load():
             lib.gzo_step_hier.argtypes = [i64] + [vp] * 10 + [C.POINTER(Params), C.c_int32, _D, vp,
                                                             C.POINTER(C.c_int64), C.POINTER(Counters)]
             lib.gzo_exchange.restype = C.c_int
-            lib.gzo_exchange.argtypes = [i64] + [vp] * 15 + [d, C.POINTER(Params), vp, vp, vp,
+            lib.gzo_exchange.argtypes = [i64] + [vp] * 15 + [d, C.POINTER(Params), vp, vp, vp, vp,
                                                            C.POINTER(Counters)]
             lib.gzo_pair.restype = C.c_int
             lib.gzo_pair.argtypes = [vp, d, d, vp, vp, vp, vp, d, d, vp, vp, vp, d,
@@ -333,12 +333,12 @@ def step_hier(s: State, p: Params, K: int, dt: float = 0.0, counters: Counters |
                                _p(o.m), _p(o.u), _p(o.H), _p(o.id), C.byref(p), int(K),
                                C.byref(dtc), _p(bins), C.byref(act), C.byref(cnt))
     if rc != 0:
-        raise ValueError("step_hier: MFM only, 0 <= K <= 20, N >= 1")
+        raise ValueError("step_hier: 0 <= K <= 20, N >= 1")
     return o, dtc.value, bins, int(act.value)
 
 
 def exchange(x, y, z, ids, m, H, n, vx, vy, vz, u, grad, B, bins, active, D, p: Params | None = None,
-             counters: Counters | None = None):
+             counters: Counters | None = None, with_mass: bool = False):
     """One hierarchical substep's pair exchange (gzo_exchange): returns
     (accp [3,N], accE [N], touched [N]) for the given per-particle arrays."""
     p = p if p is not None else params()
@@ -353,10 +353,11 @@ def exchange(x, y, z, ids, m, H, n, vx, vy, vz, u, grad, B, bins, active, D, p: 
     accE = np.zeros(N)
     tch = np.zeros(N, dtype=np.uint8)
     cnt = counters if counters is not None else Counters()
+    accm = np.zeros(N)
     _load().gzo_exchange(N, _p(a[0]), _p(a[1]), _p(a[2]), _p(ids), _p(a[3]), _p(a[4]), _p(a[5]),
                          _p(a[6]), _p(a[7]), _p(a[8]), _p(a[9]), _p(g), _p(Bm), _p(bins), _p(act),
-                         float(D), C.byref(p), _p(accp), _p(accE), _p(tch), C.byref(cnt))
-    return accp, accE, tch
+                         float(D), C.byref(p), _p(accp), _p(accE), _p(accm), _p(tch), C.byref(cnt))
+    return (accp, accE, tch, accm) if with_mass else (accp, accE, tch)
 
 
 def pair(L: dict, R: dict, dt: float, p: Params):

@@ -1009,7 +1009,9 @@ int gzo_step(int64_t N, double* x, double* y, double* z, double* vx, double* vy,
  * the pair's two shares are equal and opposite).  A particle's exchanges
  * happen whenever the smaller-step particle of a pair is active, so every
  * face is integrated over the whole interval exactly once.  u <= 0 after a
- * kick is floored as in O14 with the median of u at the substep start.  K = 0
+ * kick is floored as in O14 with the median of u at the substep start.  Under
+ * MFV (O15) the mass share rides along: m += dt_a x (its sum of
+ * dm * 2^(k_a - k_ij)), momentum and energy divided by the new mass.  K = 0
  * is gzo_step. */
 static int32_t bin_for(double D, double cfl_dtc, int32_t K, int* clamped) {
     for (int32_t k = 0; k <= K; ++k)
@@ -1022,8 +1024,8 @@ int gzo_exchange(int64_t N, const double* x, const double* y, const double* z,
                  const int64_t* id, const double* m, const double* H, const double* n,
                  const double* vx, const double* vy, const double* vz, const double* u,
                  const double* grad, const double* B, const int32_t* bin, const uint8_t* active,
-                 double D, const gzo_params* p, double* accp, double* accE, uint8_t* touched,
-                 gzo_counters* cnt) {
+                 double D, const gzo_params* p, double* accp, double* accE, double* accm,
+                 uint8_t* touched, gzo_counters* cnt) {
     finder_t fd;
     finder_init(&fd, N, x, y, z, id, p->use_cells, median_cell_len(H, N));
     const double Hmax = max_of(H, N);
@@ -1035,7 +1037,7 @@ int gzo_exchange(int64_t N, const double* x, const double* y, const double* z,
         for (int64_t i = 0; i < N; ++i) {
             const int64_t* list;
             int64_t cntj = gather(&fd, &s, i, Hmax > H[i] ? Hmax : H[i], &list);
-            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
             double d[3];
             int any = 0;
             for (int64_t k = 0; k < cntj; ++k) {
@@ -1063,11 +1065,13 @@ int gzo_exchange(int64_t N, const double* x, const double* y, const double* z,
                 acc[1] += sg * dp[1];
                 acc[2] += sg * dp[2];
                 acc[3] += sg * dE;
+                acc[4] += sg * dm;
             }
             accp[i] = acc[0];
             accp[N + i] = acc[1];
             accp[2 * N + i] = acc[2];
             accE[i] = acc[3];
+            if (accm) accm[i] = acc[4];
             touched[i] = (uint8_t)(any || active[i]);
         }
         scratch_free(&s);
@@ -1094,7 +1098,8 @@ int gzo_step_hier(int64_t N, double* x, double* y, double* z, double* vx, double
                   double* vz, double* m, double* u, double* H, const int64_t* id,
                   const gzo_params* p, int32_t K, double* dt_inout, int32_t* bin_out,
                   int64_t* active_out, gzo_counters* cnt) {
-    if (p->scheme != 0 || K < 0 || K > 20 || N < 1) return -1;
+    if (K < 0 || K > 20 || N < 1) return -1;
+    const int mfv = p->scheme == 1;
     const size_t sz = sizeof(double) * (size_t)N;
     double* xp = (double*)malloc(sz * 3);
     double *yp = xp + N, *zp = xp + 2 * N;
@@ -1107,6 +1112,7 @@ int gzo_step_hier(int64_t N, double* x, double* y, double* z, double* vx, double
     double* dtc = (double*)malloc(sz);
     double* accp = (double*)malloc(sz * 3);
     double* accE = (double*)malloc(sz);
+    double* accm = mfv ? (double*)malloc(sz) : NULL;
     int32_t* it = (int32_t*)malloc(sizeof(int32_t) * (size_t)N);
     int32_t* bin = (int32_t*)calloc((size_t)N, sizeof(int32_t));
     int32_t* sa = (int32_t*)calloc((size_t)N, sizeof(int32_t));
@@ -1119,7 +1125,7 @@ int gzo_step_hier(int64_t N, double* x, double* y, double* z, double* vx, double
     }
     double D = *dt_inout;
     const int32_t S = 1 << K;
-    int64_t nact = 0, nfl = 0, nclamp = 0;
+    int64_t nact = 0, nfl = 0, nclamp = 0, nbad = 0;
     for (int32_t s = 0; s < S; ++s) {
         int64_t na = 0;
         for (int64_t i = 0; i < N; ++i) {
@@ -1172,18 +1178,19 @@ int gzo_step_hier(int64_t N, double* x, double* y, double* z, double* vx, double
             double umed = 0.0;
             int have_med = 0;
             gzo_exchange(N, xp, yp, zp, id, m, H, n, vx, vy, vz, u, grad, B, bin, act, D, p, accp,
-                         accE, tch, cnt);
+                         accE, accm, tch, cnt);
             double* u0 = (double*)malloc(sz);
             memcpy(u0, u, sz);
             for (int64_t i = 0; i < N; ++i) {
                 if (!tch[i]) continue;
                 const double dt = ldexp(D, -bin[i]);
+                const double mn = mfv ? m[i] + dt * accm[i] : m[i];
                 const double v2 = (vx[i] * vx[i] + vy[i] * vy[i]) + vz[i] * vz[i];
                 const double E = m[i] * (u[i] + 0.5 * v2) + dt * accE[i];
-                const double nx = (m[i] * vx[i] + dt * accp[i]) / m[i];
-                const double ny = (m[i] * vy[i] + dt * accp[N + i]) / m[i];
-                const double nz = (m[i] * vz[i] + dt * accp[2 * N + i]) / m[i];
-                double un = E / m[i] - 0.5 * ((nx * nx + ny * ny) + nz * nz);
+                const double nx = (m[i] * vx[i] + dt * accp[i]) / mn;
+                const double ny = (m[i] * vy[i] + dt * accp[N + i]) / mn;
+                const double nz = (m[i] * vz[i] + dt * accp[2 * N + i]) / mn;
+                double un = E / mn - 0.5 * ((nx * nx + ny * ny) + nz * nz);
                 if (!(un > 0.0)) {
                     if (!have_med) {
                         umed = median_u(u0, N);
@@ -1192,10 +1199,12 @@ int gzo_step_hier(int64_t N, double* x, double* y, double* z, double* vx, double
                     un = p->u_floor_frac * umed;
                     nfl++;
                 }
+                if (!(mn > 0.0)) nbad++;
                 vx[i] = nx;
                 vy[i] = ny;
                 vz[i] = nz;
                 u[i] = un;
+                m[i] = mn;
             }
             free(u0);
         }
@@ -1217,6 +1226,7 @@ int gzo_step_hier(int64_t N, double* x, double* y, double* z, double* vx, double
     if (cnt) {
         cnt->ufloor += nfl;
         cnt->bin_clamp += nclamp;
+        cnt->nonfinite += nbad;
     }
     free(xp);
     free(va);
@@ -1228,6 +1238,7 @@ int gzo_step_hier(int64_t N, double* x, double* y, double* z, double* vx, double
     free(dtc);
     free(accp);
     free(accE);
+    free(accm);
     free(it);
     free(bin);
     free(sa);

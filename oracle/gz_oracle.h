@@ -127,12 +127,12 @@ int gzo_step(int64_t N, double* x, double* y, double* z, double* vx, double* vy,
              const gzo_params* p, double* dt_inout, double* n_out, double* dpdt,
              double* dEdt, double* dmdt, gzo_counters* cnt);
 
-/* Hierarchical timesteps (reading HT, MFM only): one sync interval of 2^K
+/* Hierarchical timesteps (reading HT; MFV too): one sync interval of 2^K
  * substeps in place on the state; *dt_inout > 0 fixes the interval D, else
  * the CFL rule sets it; the interval used is written back.  bin_out ([N],
  * optional) receives every particle's final bin, active_out (optional) the
  * number of active particle-substeps.  K = 0 is gzo_step.  Returns -1 for
- * MFV, K outside [0, 20] or N < 1. */
+ * K outside [0, 20] or N < 1. */
 int gzo_step_hier(int64_t N, double* x, double* y, double* z, double* vx, double* vy,
                   double* vz, double* m, double* u, double* H, const int64_t* id,
                   const gzo_params* p, int32_t K, double* dt_inout, int32_t* bin_out,
@@ -141,13 +141,14 @@ int gzo_step_hier(int64_t N, double* x, double* y, double* z, double* vx, double
 /* Pair exchange of one hierarchical substep: for every particle, the sum over
  * its flux pairs with an active partner (or itself active) of
  * rate * 2^(bin_i - max(bin_i, bin_j)), faces evaluated over
- * D/2^max(bin_i, bin_j); touched[i] = 1 when i is active or has such a pair. */
+ * D/2^max(bin_i, bin_j) (accm, optional: the mass rates of MFV);
+ * touched[i] = 1 when i is active or has such a pair. */
 int gzo_exchange(int64_t N, const double* x, const double* y, const double* z,
                  const int64_t* id, const double* m, const double* H, const double* n,
                  const double* vx, const double* vy, const double* vz, const double* u,
                  const double* grad, const double* B, const int32_t* bin, const uint8_t* active,
-                 double D, const gzo_params* p, double* accp, double* accE, uint8_t* touched,
-                 gzo_counters* cnt);
+                 double D, const gzo_params* p, double* accp, double* accE, double* accm,
+                 uint8_t* touched, gzo_counters* cnt);
 
 /* One face evaluation in canonical (L, R) order for pins: inputs are the
  * two particles' positions, H, n, primitives (rho, vx, vy, vz, P), limited

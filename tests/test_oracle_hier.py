@@ -109,3 +109,27 @@ def test_sedov_blast_keeps_global_step_accuracy_with_fewer_updates():
     assert abs(res[0][0] - 1.0) < 0.1
     assert abs(res[3][0] - res[0][0]) < 0.03
     assert res[3][1] < 0.5 * res[0][1]
+
+
+def test_mfv_k0_is_the_global_mfv_step_bitwise():
+    s = state(I.turbulence(10, seed=9))
+    p = O.params(scheme=O.MFV)
+    a, dta, _, _, _ = O.step(s, p)
+    b, D, bins, na = O.step_hier(s, p, 0)
+    assert D == dta
+    for k in FIELDS + ("m",):
+        assert np.array_equal(getattr(a, k), getattr(b, k)), k
+
+
+def test_mfv_interval_conserves_mass_momentum_energy():
+    s = state(I.sedov(12))
+    P0, E0 = totals(s)
+    M0 = s.m.sum()
+    o, D, bins, na = O.step_hier(s, O.params(scheme=O.MFV), 3)
+    assert len(np.unique(bins)) > 1
+    assert np.abs(o.m - s.m).max() > 0.0  # mass moved
+    assert o.m.sum() == pytest.approx(M0, rel=1e-14)
+    P1, E1 = totals(o)
+    scale = (s.m * np.sqrt(s.vx ** 2 + s.vy ** 2 + s.vz ** 2)).sum() + (s.m * np.sqrt(s.u)).sum()
+    assert np.all(np.abs(P1 - P0) <= 1e-13 * scale)
+    assert E1 == pytest.approx(E0, rel=1e-13)
