@@ -236,7 +236,7 @@ gz_status gz_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
  * of that), equal and opposite for its two particles; momentum and energy are
  * kicked at once, and a step that ends drifts its particle by
  * dt_i (v_start + v_end)/2.  K = 0 gives gz_step's result bitwise.  In place
- * on p like gz_step (x, y, z, vx, vy, vz, u, h; m and id read only); h ends as
+ * on p like gz_step (x, y, z, vx, vy, vz, u, h, and m under GZ_MFV; id read only); h ends as
  * each particle's H of its last active time.  dt_used_dev (device, nboxes
  * doubles, may be NULL) receives D per box, bins_out (device, N int32, caller
  * order, may be NULL) the final bins, *active_out (host, may be NULL) the
@@ -244,8 +244,9 @@ gz_status gz_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
  * (the number of active particles sizes the launches; substeps without one
  * only drift), so the call cannot be captured in a CUDA graph.  Scratch of
  * about 150 bytes a particle (FP32) is allocated on the first call.  Every
- * Riemann option of the MFM face applies.  Errors: GZ_E_INVAL (K out of
- * range, GZ_MFV), GZ_E_NOMEM. */
+ * Riemann option of the MFM face applies, and GZ_MFV (O15: the mass shares are
+ * exchanged with momentum and energy, m is updated too).  Errors: GZ_E_INVAL
+ * (K out of range), GZ_E_NOMEM. */
 gz_status gz_step_hier(gz_ctx* ctx, gz_particles* p, int32_t K, double dt_fixed, double* dt_used_dev,
                        int32_t* bins_out, int64_t* active_out);
 

@@ -612,7 +612,6 @@ gz_status gz_step_hier(gz_ctx* ctx, gz_particles* p, int32_t K, double dt_fixed,
     if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
     if (K < 0 || K > 20) return fail(ctx, GZ_E_INVAL, "K must be in [0, 20]");
     Ctx& c = ctx->c;
-    if (c.params.scheme != GZ_MFM) return fail(ctx, GZ_E_INVAL, "hierarchical steps cover GZ_MFM only");
     const PassTimer timer{&c};
     long long act = 0;
     cudaError_t e = c.precision == GZ_FP64

@@ -501,45 +501,66 @@ __device__ __forceinline__ void update_one(float m, float& x, float& y, float& z
 
 // MFV (O15): the mass advances too, m' = m + dt dm/dt, and momentum and
 // total energy are divided by m'.  FP64 state: the literal form, like the
-// oracle.
-__device__ __forceinline__ void update_one_mfv(double& m, double& x, double& y, double& z, double& vx,
-                                               double& vy, double& vz, double& u, double dpx, double dpy,
-                                               double dpz, double dE, double dm, double dt) {
-    const double mn = m + dt * dm;
-    const double v2 = (vx * vx + vy * vy) + vz * vz;
-    const double E = m * (u + 0.5 * v2) + dt * dE;
-    const double nx = (m * vx + dt * dpx) / mn, ny = (m * vy + dt * dpy) / mn, nz = (m * vz + dt * dpz) / mn;
-    x = wrap1(x + dt * (0.5 * (vx + nx)));
-    y = wrap1(y + dt * (0.5 * (vy + ny)));
-    z = wrap1(z + dt * (0.5 * (vz + nz)));
-    u = E / mn - 0.5 * ((nx * nx + ny * ny) + nz * nz);
+// oracle, explicitly rounded like kick_one.
+__device__ __forceinline__ void kick_one_mfv(double& m, double& vx, double& vy, double& vz, double& u,
+                                             double dpx, double dpy, double dpz, double dE, double dm,
+                                             double dt) {
+    const double mn = __dadd_rn(m, __dmul_rn(dt, dm));
+    const double v2 = __dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz));
+    const double E = __dadd_rn(__dmul_rn(m, __dadd_rn(u, __dmul_rn(0.5, v2))), __dmul_rn(dt, dE));
+    const double nx = __ddiv_rn(__dadd_rn(__dmul_rn(m, vx), __dmul_rn(dt, dpx)), mn);
+    const double ny = __ddiv_rn(__dadd_rn(__dmul_rn(m, vy), __dmul_rn(dt, dpy)), mn);
+    const double nz = __ddiv_rn(__dadd_rn(__dmul_rn(m, vz), __dmul_rn(dt, dpz)), mn);
+    const double n2 = __dadd_rn(__dadd_rn(__dmul_rn(nx, nx), __dmul_rn(ny, ny)), __dmul_rn(nz, nz));
+    u = __dsub_rn(__ddiv_rn(E, mn), __dmul_rn(0.5, n2));
     vx = nx;
     vy = ny;
     vz = nz;
     m = mn;
 }
+__device__ __forceinline__ void update_one_mfv(double& m, double& x, double& y, double& z, double& vx,
+                                               double& vy, double& vz, double& u, double dpx, double dpy,
+                                               double dpz, double dE, double dm, double dt) {
+    const double ox = vx, oy = vy, oz = vz;
+    kick_one_mfv(m, vx, vy, vz, u, dpx, dpy, dpz, dE, dm, dt);
+    x = drift_one(x, ox, vx, dt);
+    y = drift_one(y, oy, vy, dt);
+    z = drift_one(z, oz, vz, dt);
+}
 // FP32 state: with dM = dt dm/dt, m' = m + dM (formed in FP64) and the
 // increments dv = (dt dp/dt - dM v)/m' and
 // du = (dt dE/dt - dM (u + v^2/2))/m' - dv . (v + dv/2), which equal
-// p'/m' - v and E'/m' - v'^2/2 - u without the cancellation of the literal form.
+// p'/m' - v and E'/m' - v'^2/2 - u without the cancellation of the literal
+// form; explicitly rounded like kick_one.
+__device__ __forceinline__ void kick_one_mfv(float& m, float& vx, float& vy, float& vz, float& u, double dpx,
+                                             double dpy, double dpz, double dE, double dm, double dt,
+                                             float& dvx, float& dvy, float& dvz) {
+    const float mn = (float)__dadd_rn((double)m, __dmul_rn(dt, dm));
+    const float dtf = (float)dt, im = __fdiv_rn(1.f, mn), dM = __fmul_rn(dtf, (float)dm);
+    dvx = __fmul_rn(__fsub_rn(__fmul_rn(dtf, (float)dpx), __fmul_rn(dM, vx)), im);
+    dvy = __fmul_rn(__fsub_rn(__fmul_rn(dtf, (float)dpy), __fmul_rn(dM, vy)), im);
+    dvz = __fmul_rn(__fsub_rn(__fmul_rn(dtf, (float)dpz), __fmul_rn(dM, vz)), im);
+    const float hx = __fadd_rn(vx, __fmul_rn(0.5f, dvx)), hy = __fadd_rn(vy, __fmul_rn(0.5f, dvy)),
+                hz = __fadd_rn(vz, __fmul_rn(0.5f, dvz));
+    const float v2 = __fadd_rn(__fadd_rn(__fmul_rn(vx, vx), __fmul_rn(vy, vy)), __fmul_rn(vz, vz));
+    const float ek = __fadd_rn(u, __fmul_rn(0.5f, v2));
+    const float w = __fadd_rn(__fadd_rn(__fmul_rn(dvx, hx), __fmul_rn(dvy, hy)), __fmul_rn(dvz, hz));
+    const float du = __fsub_rn(__fmul_rn(__fsub_rn(__fmul_rn(dtf, (float)dE), __fmul_rn(dM, ek)), im), w);
+    u = __fadd_rn(u, du);
+    vx = __fadd_rn(vx, dvx);
+    vy = __fadd_rn(vy, dvy);
+    vz = __fadd_rn(vz, dvz);
+    m = mn;
+}
 __device__ __forceinline__ void update_one_mfv(float& m, float& x, float& y, float& z, float& vx,
                                                float& vy, float& vz, float& u, double dpx, double dpy,
                                                double dpz, double dE, double dm, double dt) {
-    const float mn = (float)((double)m + dt * dm);
-    const float dtf = (float)dt, im = 1.f / mn, dM = dtf * (float)dm;
-    const float dvx = (dtf * (float)dpx - dM * vx) * im, dvy = (dtf * (float)dpy - dM * vy) * im,
-                dvz = (dtf * (float)dpz - dM * vz) * im;
-    const float hx = vx + 0.5f * dvx, hy = vy + 0.5f * dvy, hz = vz + 0.5f * dvz;
-    const float ek = u + 0.5f * ((vx * vx + vy * vy) + vz * vz);
-    const float du = (dtf * (float)dE - dM * ek) * im - ((dvx * hx + dvy * hy) + dvz * hz);
-    x = wrapf(x + dtf * hx);
-    y = wrapf(y + dtf * hy);
-    z = wrapf(z + dtf * hz);
-    u = u + du;
-    vx += dvx;
-    vy += dvy;
-    vz += dvz;
-    m = mn;
+    const float ox = vx, oy = vy, oz = vz;
+    float dvx, dvy, dvz;
+    kick_one_mfv(m, vx, vy, vz, u, dpx, dpy, dpz, dE, dm, dt, dvx, dvy, dvz);
+    x = drift_onef(x, ox, dvx, dt);
+    y = drift_onef(y, oy, dvy, dt);
+    z = drift_onef(z, oz, dvz, dt);
 }
 
 }  // namespace gz

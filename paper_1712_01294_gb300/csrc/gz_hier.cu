@@ -17,7 +17,8 @@
 //     (Hancock with dt_ij/2): each side accumulates rate * 2^(k_a - k_ij)
 //     (exact power-of-two scaling, so the two shares stay equal and opposite)
 //     and kicks momentum and energy by dt_a times that sum.
-// Any Riemann option of the MFM face (the exchange uses pair_rates with it).
+// Any Riemann option of the MFM face, and MFV (the exchange uses pair_rates
+// with them; under MFV the mass shares ride along and the kick advances m).
 // K = 0 is gz_step bitwise.  Pair lists of an active particle: N_i from the
 // density pass and the pairs with r >= H_i (r < H_j), written by the partner
 // j from a scan of its own support; an inactive particle's list holds its
@@ -343,15 +344,18 @@ constexpr int kXBlock = 128;
 // r >= H_i pairs; an inactive one: its active partners): the pair's face
 // fluxes with the Hancock half step of dt_ij, scaled by 2^(k_i - k_ij),
 // summed like the flux pass (working precision over runs of 8 pairs, then
-// FP64).  kRiem: the MFM face's Riemann solver (pair_rates).
-template <typename T, int kRiem>
+// FP64).  kRiem: the MFM face's Riemann solver; kMFV: the MFV fluxes, whose
+// mass share is summed too (pair_rates).
+template <typename T, int kRiem, bool kMFV>
 __global__ void __launch_bounds__(kXBlock)
     k_h_exchange(const int* __restrict__ tlist, const int* __restrict__ nT, const T* __restrict__ rec,
                  const long long* __restrict__ sid, const int* __restrict__ sbox,
                  const int* __restrict__ sbin, const unsigned* __restrict__ nbr,
                  const int* __restrict__ ncount, const unsigned* __restrict__ rnbr,
                  const int* __restrict__ rcount, KParams p, const double* __restrict__ D,
-                 double* __restrict__ dpdt, double* __restrict__ dEdt, int N, DevStatus* st) {
+                 double* __restrict__ dpdt, double* __restrict__ dEdt, double* __restrict__ dmdt, int N,
+                 DevStatus* st) {
+    constexpr int nq = kMFV ? 5 : 4;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= *nT) return;
     const int i = tlist[t];
@@ -362,8 +366,13 @@ __global__ void __launch_bounds__(kXBlock)
     const double Db = D[sbox[i]];
     const T gam = (T)p.gamma;
     const bool hancock = p.hancock != 0;
-    T part[4] = {T(0), T(0), T(0), T(0)};
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    T part[nq];
+    double acc[nq];
+#pragma unroll
+    for (int q = 0; q < nq; ++q) {
+        part[q] = T(0);
+        acc[q] = 0.0;
+    }
     int np = 0, nfall = 0, nneg = 0;
 #pragma unroll 1
     for (int list = 0; list < 2; ++list) {
@@ -379,19 +388,20 @@ __global__ void __launch_bounds__(kXBlock)
             hancock_inc(a, hdt, gam, hancock, inca);
             T dp[3], dE, dm;
             int fl = 0;
-            if (pair_rates<T, false, kRiem>(a, b, idi < sid[j], hdt, gam, hancock, inca, dp, dE,
+            if (pair_rates<T, kMFV, kRiem>(a, b, idi < sid[j], hdt, gam, hancock, inca, dp, dE,
                                                       dm, fl)) {
                 const T sc = (T)ldexp(1.0, ka - kab);
                 part[0] += dp[0] * sc;
                 part[1] += dp[1] * sc;
                 part[2] += dp[2] * sc;
                 part[3] += dE * sc;
+                if constexpr (kMFV) part[4] += dm * sc;
             }
             nfall += fl & 1;
             nneg += (fl >> 1) & 1;
             if (++np == 8) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < nq; ++q) {
                     acc[q] += (double)part[q];
                     part[q] = T(0);
                 }
@@ -400,11 +410,12 @@ __global__ void __launch_bounds__(kXBlock)
         }
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] += (double)part[q];
+    for (int q = 0; q < nq; ++q) acc[q] += (double)part[q];
     dpdt[i] = acc[0];
     dpdt[(size_t)N + i] = acc[1];
     dpdt[2 * (size_t)N + i] = acc[2];
     dEdt[i] = acc[3];
+    if constexpr (kMFV) dmdt[i] = acc[4];
     if (nfall) {
         atomicOr(&st->bits, GZ_S_FALLBACK);
         atomicAdd(&st->counters[GZ_C_FALLBACK], (unsigned long long)nfall);
@@ -421,8 +432,9 @@ __global__ void __launch_bounds__(kXBlock)
 template <typename T>
 __global__ void k_h_kick(const int* __restrict__ tlist, const int* __restrict__ nT, int N, Sorted<T> s,
                          const int* __restrict__ sbin, const double* __restrict__ dpdt,
-                         const double* __restrict__ dEdt, const double* __restrict__ D, gz_particles out,
-                         T* __restrict__ hdvs, int* __restrict__ box_hits, DevStatus* st) {
+                         const double* __restrict__ dEdt, const double* __restrict__ dmdt,
+                         const double* __restrict__ D, gz_particles out, T* __restrict__ hdvs,
+                         int* __restrict__ box_hits, DevStatus* st) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= *nT) return;
     const int i = tlist[t];
@@ -431,16 +443,23 @@ __global__ void k_h_kick(const int* __restrict__ tlist, const int* __restrict__ 
     const double dt = ldexp(D[b], -sbin[i]);
     const double dpx = dpdt[i], dpy = dpdt[(size_t)N + i], dpz = dpdt[2 * (size_t)N + i], dE = dEdt[i];
     T vx = s.vx[i], vy = s.vy[i], vz = s.vz[i], u = s.u[i];
-    const T m = s.m[i];
+    T m = s.m[i];
     if constexpr (std::is_same<T, float>::value) {
         float dvx, dvy, dvz;
-        kick_one(m, vx, vy, vz, u, dpx, dpy, dpz, dE, dt, dvx, dvy, dvz);
+        if (dmdt)
+            kick_one_mfv(m, vx, vy, vz, u, dpx, dpy, dpz, dE, dmdt[i], dt, dvx, dvy, dvz);
+        else
+            kick_one(m, vx, vy, vz, u, dpx, dpy, dpz, dE, dt, dvx, dvy, dvz);
         hdvs[o] = __fadd_rn(hdvs[o], dvx);
         hdvs[(size_t)N + o] = __fadd_rn(hdvs[(size_t)N + o], dvy);
         hdvs[2 * (size_t)N + o] = __fadd_rn(hdvs[2 * (size_t)N + o], dvz);
     } else {
-        kick_one(m, vx, vy, vz, u, dpx, dpy, dpz, dE, dt);
+        if (dmdt)
+            kick_one_mfv(m, vx, vy, vz, u, dpx, dpy, dpz, dE, dmdt[i], dt);
+        else
+            kick_one(m, vx, vy, vz, u, dpx, dpy, dpz, dE, dt);
     }
+    if (dmdt) ((T*)out.m)[o] = m;
     ((T*)out.vx)[o] = vx;
     ((T*)out.vy)[o] = vy;
     ((T*)out.vz)[o] = vz;
@@ -449,7 +468,7 @@ __global__ void k_h_kick(const int* __restrict__ tlist, const int* __restrict__ 
         atomicAdd(&box_hits[b], 1);
         set_status(st, GZ_S_UFLOOR, GZ_C_UFLOOR, -1);
     }
-    if (!(finite_(vx) && finite_(vy) && finite_(vz) && finite_(u)))
+    if (!(m > T(0) && finite_(vx) && finite_(vy) && finite_(vz) && finite_(u)))
         set_status(st, GZ_S_NONFINITE, GZ_C_NONFINITE, s.id[i]);
 }
 
@@ -490,14 +509,16 @@ void launch_exchange(Ctx& c, const KParams& kp, int N) {
     auto go = [&](auto kernel) {
         kernel<<<nblk(N, kXBlock), kXBlock, 0, c.stream>>>(c.tlist, c.hcount + 2, (const T*)c.rec, c.sid, c.sbox,
                                                            c.sbin, c.nbr, c.ncount, c.rnbr, c.rcount, kp, c.dt_use,
-                                                           c.dpdt, c.dEdt, N, c.status);
+                                                           c.dpdt, c.dEdt, c.dmdt, N, c.status);
     };
-    if (r == GZ_RIEMANN_EXACT)
-        go(k_h_exchange<T, GZ_RIEMANN_EXACT>);
+    if (c.params.scheme == GZ_MFV)
+        go(k_h_exchange<T, GZ_RIEMANN_HLLC, true>);
+    else if (r == GZ_RIEMANN_EXACT)
+        go(k_h_exchange<T, GZ_RIEMANN_EXACT, false>);
     else if (r == GZ_RIEMANN_FALLBACK)
-        go(k_h_exchange<T, GZ_RIEMANN_FALLBACK>);
+        go(k_h_exchange<T, GZ_RIEMANN_FALLBACK, false>);
     else
-        go(k_h_exchange<T, GZ_RIEMANN_HLLC>);
+        go(k_h_exchange<T, GZ_RIEMANN_HLLC, false>);
 }
 
 }  // namespace
@@ -633,7 +654,8 @@ cudaError_t run_step_hier(Ctx& c, gz_particles& p, int K, double dt_fixed, doubl
             cudaMemsetAsync(c.box_hits, 0, sizeof(int) * (size_t)c.nboxes, st);
             c.launches += 1;
             k_h_kick<T><<<nblk(N, 256), 256, 0, st>>>(c.tlist, c.hcount + 2, N, sv, c.sbin, c.dpdt, c.dEdt,
-                                                       c.dt_use, p, (T*)c.hdvs, c.box_hits, c.status);
+                                                       c.params.scheme == GZ_MFV ? c.dmdt : nullptr, c.dt_use,
+                                                       p, (T*)c.hdvs, c.box_hits, c.status);
             if (e == cudaSuccess) e = run_ufloor<T>(c, p);
             timer.end(GZ_PASS_UPDATE);
         }

@@ -190,9 +190,6 @@ def test_interval_is_deterministic_and_refuses_bad_arguments():
         assert np.array_equal(outs[0][k], outs[1][k]), k
     with pytest.raises(m.GZError):
         ctx.step_hier(d, 21)
-    cm = ctx_for(q.N, m.GZ_MIXED32, scheme=m.GZ_MFV)
-    with pytest.raises(m.GZError):
-        cm.step_hier(device(q, m.GZ_MIXED32), 2)
 
 
 def test_batched_boxes_equal_single_boxes():
@@ -255,3 +252,40 @@ def test_lone_particle_box_beside_a_normal_box_without_fault(scheme):
     assert "hconv" in st["bits"]
     for k in ("x", "vx", "u", "h"):
         assert torch.equal(both[k][:q.N], alone[k]), k
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mfv_k0_equals_gz_step_bitwise(prec):
+    import torch
+    m = gz()
+    q = cast_state(make("turb", 14), prec)
+    a = device(q, prec)
+    ctx = ctx_for(q.N, prec, scheme=m.GZ_MFV)
+    ctx.step(a)
+    b = device(q, prec)
+    ctx2 = ctx_for(q.N, prec, scheme=m.GZ_MFV)
+    ctx2.step_hier(b, 0)
+    assert ctx.status(reset=True)["ok"] and ctx2.status(reset=True)["ok"]
+    for k in FIELDS + ("m",):
+        assert torch.equal(a[k], b[k]), k
+
+
+def test_mfv_fp64_interval_follows_the_oracle_and_conserves_mass():
+    import torch
+    m = gz()
+    q = cast_state(make("sedov", 13), m.GZ_FP64)
+    s = ostate(q)
+    o, D_o, bins_o, na_o = O.step_hier(s, O.params(scheme=O.MFV), 3)
+    assert len(np.unique(bins_o)) > 1
+    ctx = ctx_for(q.N, m.GZ_FP64, scheme=m.GZ_MFV)
+    d = device(q, m.GZ_FP64)
+    D = torch.zeros(1, dtype=torch.float64, device="cuda")
+    bins = torch.zeros(q.N, dtype=torch.int32, device="cuda")
+    na = ctx.step_hier(d, 3, 0.0, D, bins)
+    assert ctx.status(reset=True)["ok"]
+    assert abs(float(D.item()) - D_o) <= 1e-12 * D_o and na == na_o
+    assert np.array_equal(bins.cpu().numpy(), bins_o)
+    for k in ("vx", "vy", "vz", "u", "m"):
+        mx, _ = field_err(d[k].cpu().numpy() - getattr(s, k), getattr(o, k) - getattr(s, k))
+        assert mx <= 1e-9, (k, mx)
+    assert float(d["m"].sum()) == pytest.approx(float(q.m.sum()), rel=1e-13)
