@@ -182,6 +182,43 @@ __global__ void k_h_cellact(int ncells, const int2* __restrict__ cells, const un
     cellact[c] = any;
 }
 
+// Cells within two cells (per axis, periodic) of a cell holding an active
+// particle, marked by the active cells themselves (near must start zeroed).
+__global__ void k_h_dilate(int ncells, const BoxInfo* __restrict__ boxes, int nboxes,
+                           const unsigned char* __restrict__ cellact, unsigned char* __restrict__ near) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells || !cellact[c]) return;
+    int lo = 0, hi = nboxes - 1;  // box of the cell: last box with cell_off <= c
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (boxes[mid].cell_off <= c)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const BoxInfo bx = boxes[lo];
+    const int nc = bx.nc, l = c - bx.cell_off;
+    const int cx = l % nc, cy = (l / nc) % nc, cz = l / (nc * nc);
+    for (int dz = -2; dz <= 2; ++dz) {
+        const int wz = ((cz + dz) % nc + nc) % nc;
+        for (int dy = -2; dy <= 2; ++dy) {
+            const int wy = ((cy + dy) % nc + nc) % nc;
+            for (int dx = -2; dx <= 2; ++dx) {
+                const int wx = ((cx + dx) % nc + nc) % nc;
+                near[bx.cell_off + (wz * nc + wy) * nc + wx] = 1;
+            }
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ int cell_of(T v, int nc) {
+    T f = floor(v * (T)nc);
+    if (!(f >= T(0))) return 0;
+    if (f > (T)(nc - 1)) return nc - 1;
+    return (int)f;
+}
+
 // The flux pairs of active i with r >= H_i (so r < H_j, O10), found from the
 // partner's side: every particle j scans its own support (cells without an
 // active particle skipped) and appends itself to the list of each active i
@@ -191,13 +228,20 @@ __global__ void k_h_cellact(int ncells, const int2* __restrict__ cells, const un
 template <typename T>
 __global__ void __launch_bounds__(128)
     k_h_rscatter(int N, Sorted<T> s, Grid g, KParams p, const unsigned char* __restrict__ aflag,
-                 const unsigned char* __restrict__ cellact, unsigned* __restrict__ rnbr,
-                 int* __restrict__ rcount, DevStatus* st) {
+                 const unsigned char* __restrict__ cellact, const unsigned char* __restrict__ near,
+                 unsigned* __restrict__ rnbr, int* __restrict__ rcount, DevStatus* st) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     const BoxInfo bx = g.boxes[s.box[j]];
     const P4<T> me = s.pos[j];
     const T Hj = me.w;
+    // a support spanning under two cells lies within two cells of its own
+    // (the scan's range floor((x -+ H) nc -+ 1e-3)): without an active cell
+    // there, nothing to append
+    if (Hj * (T)bx.nc < T(1.99)) {
+        const int nc = bx.nc;
+        if (!near[bx.cell_off + (cell_of(me.z, nc) * nc + cell_of(me.y, nc)) * nc + cell_of(me.x, nc)]) return;
+    }
     const T H2 = Hj * Hj;
     const unsigned char* ca = cellact + bx.cell_off;
     for_candidates<T>(
@@ -294,15 +338,30 @@ __global__ void k_h_persist(int N, const int* __restrict__ alist, const int* __r
     ((T*)p.h)[o] = s.h[i];
 }
 
-// Largest finite criterion of every box (substep 0).
+// Largest finite criterion of every box (substep 0): a warp's maximum in one
+// atomic when the warp lies in one box (positive doubles order like their
+// bit patterns).
 __global__ void k_h_dtmax(const int* __restrict__ alist, const int* __restrict__ nA,
                           const int* __restrict__ box, const double* __restrict__ dti,
                           unsigned long long* __restrict__ dtmax) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= *nA) return;
-    const int i = alist[t];
-    const double v = dti[i];
-    if (isfinite(v) && v > 0.0) atomicMax(&dtmax[box[i]], (unsigned long long)__double_as_longlong(v));
+    const bool in = t < *nA;
+    const int i = in ? alist[t] : 0;
+    const double v = in ? dti[i] : 0.0;
+    unsigned long long bits = (in && isfinite(v) && v > 0.0) ? (unsigned long long)__double_as_longlong(v) : 0ull;
+    const int b = in ? box[i] : -1;
+    const unsigned full = 0xffffffffu;
+    const int b0 = __shfl_sync(full, b, 0);
+    if (__all_sync(full, !in || b == b0)) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long w = __shfl_xor_sync(full, bits, o);
+            bits = w > bits ? w : bits;
+        }
+        if ((threadIdx.x & 31) == 0 && b0 >= 0 && bits) atomicMax(&dtmax[b0], bits);
+    } else if (in && bits) {
+        atomicMax(&dtmax[b], bits);
+    }
 }
 
 // Interval per box: min(cfl max dtc, 2^K cfl min dtc).
@@ -536,7 +595,8 @@ cudaError_t ensure_hier_scratch(Ctx& c) {
         {(void**)&c.hsa, 4 * Nz},      {(void**)&c.hbin, 4 * Nz},    {(void**)&c.sbin, 4 * Nz},
         {(void**)&c.alist, 4 * Nz},    {(void**)&c.tlist, 4 * Nz},   {(void**)&c.hcount, 4 * 4},
         {(void**)&c.bcount, 4 * nb},   {(void**)&c.aflag, Nz},       {(void**)&c.tflag, Nz},
-        {(void**)&c.cellact, (size_t)c.total_cells}, {(void**)&c.dtmax, 8 * (size_t)c.nboxes},
+        {(void**)&c.cellact, (size_t)c.total_cells}, {(void**)&c.cellnear, (size_t)c.total_cells},
+        {(void**)&c.dtmax, 8 * (size_t)c.nboxes},
     };
     size_t total = 0;
     for (auto& it : items) total += (it.bytes + 255) & ~(size_t)255;
@@ -614,9 +674,13 @@ cudaError_t run_step_hier(Ctx& c, gz_particles& p, int K, double dt_fixed, doubl
             timer.end(GZ_PASS_PRIM);
             timer.begin(GZ_PASS_REVERSE);
             c.launches += 6;
+            c.launches += 1;
             k_h_cellact<<<nblk(c.total_cells, 256), 256, 0, st>>>(c.total_cells, c.cells, c.aflag, c.cellact);
-            k_h_rscatter<T><<<nblk(N, 128), 128, 0, st>>>(N, sv, g, kp, c.aflag, c.cellact, c.rnbr, c.rcount,
-                                                           c.status);
+            cudaMemsetAsync(c.cellnear, 0, (size_t)c.total_cells, st);
+            k_h_dilate<<<nblk(c.total_cells, 256), 256, 0, st>>>(c.total_cells, c.boxes, c.nboxes, c.cellact,
+                                                                  c.cellnear);
+            k_h_rscatter<T><<<nblk(N, 128), 128, 0, st>>>(N, sv, g, kp, c.aflag, c.cellact, c.cellnear, c.rnbr,
+                                                           c.rcount, c.status);
             k_h_inlist<<<nblk(nA, 128), 128, 0, st>>>(c.alist, c.hcount + 1, c.aflag, c.nbr, c.ncount, c.rnbr,
                                                        c.rcount, c.cap, c.rcap, c.sid, c.status);
             k_h_sort<<<nblk(N, 128), 128, 0, st>>>(N, c.aflag, c.ncount, c.nbr, c.cap, c.rcount, c.rnbr,

@@ -202,10 +202,9 @@ __global__ void __launch_bounds__(kDensBlock)
 
 // The particles k_density deferred (more candidates within 1.05 H than its
 // cache holds): one warp per particle, the same bracketed Newton iteration,
-// each evaluation a warp-cooperative scan of the cells (lanes over the
-// candidates of a cell, sums reduced across the warp in FP64, so every lane
-// holds the same totals and takes the same steps); the neighbour list of the
-// returned H in scan order (ballot-compacted).  Grid-stride over the deferred
+// each evaluation a warp-cooperative scan (for_candidates_lanes; sums reduced
+// across the warp in FP64, so every lane holds the same totals and takes the
+// same steps); the neighbour list of the returned H lane by lane.  Grid-stride over the deferred
 // list, whose length only the device knows.
 constexpr int kWarpDensBlock = 128;
 
@@ -246,15 +245,14 @@ __global__ void __launch_bounds__(kWarpDensBlock)
             Acc<T> sw;
             T sd = T(0);
             int c = 0;
-            for_candidates_warp<T>(g, bx, s.pos, i, xi, yi, zi, Ht, lane,
-                                   [&](int, bool valid, T, T, T, T r2) {
-                                       if (valid && r2 < H2) {
-                                           const T q = sqrt(r2) * iH;
-                                           sw.add(kern_w(q));
-                                           sd += -kern_dw(q) * q;
-                                           ++c;
-                                       }
-                                   });
+            for_candidates_lanes<T>(g, bx, s.pos, i, xi, yi, zi, Ht, lane, [&](int, T, T, T, T r2) {
+                if (r2 < H2) {
+                    const T q = sqrt(r2) * iH;
+                    sw.add(kern_w(q));
+                    sd += -kern_dw(q) * q;
+                    ++c;
+                }
+            });
             const double Sw = warp_sum<T>(sw.value());
             const T sdw = (T)warp_sum<T>((double)sd);
 #pragma unroll
@@ -308,18 +306,27 @@ __global__ void __launch_bounds__(kWarpDensBlock)
             H = Hn;
         }
         if (it > p.max_iter) it = p.max_iter;
-        {  // list of the returned H, in scan order
+        {  // list of the returned H, lane by lane (each lane's share in its scan
+           // order, lanes in order): count, exclusive prefix across the warp, write
             const T Ht = (T)Hev;
             const T H2 = Ht * Ht;
-            int c = 0;
-            for_candidates_warp<T>(g, bx, s.pos, i, xi, yi, zi, Ht, lane,
-                                   [&](int j, bool valid, T, T, T, T r2) {
-                                       const bool in = valid && r2 < H2;
-                                       const unsigned b = __ballot_sync(0xffffffffu, in);
-                                       const int slot = c + __popc(b & ((1u << lane) - 1u));
-                                       if (in && slot < p.cap) nbr[(size_t)i * p.cap + slot] = (unsigned)j;
-                                       c += __popc(b);
-                                   });
+            int mine = 0;
+            for_candidates_lanes<T>(g, bx, s.pos, i, xi, yi, zi, Ht, lane,
+                                    [&](int, T, T, T, T r2) { mine += r2 < H2; });
+            int base = mine;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, base, o);
+                if (lane >= o) base += y;
+            }
+            base -= mine;
+            int k = base;
+            for_candidates_lanes<T>(g, bx, s.pos, i, xi, yi, zi, Ht, lane, [&](int j, T, T, T, T r2) {
+                if (r2 < H2) {
+                    if (k < p.cap) nbr[(size_t)i * p.cap + k] = (unsigned)j;
+                    ++k;
+                }
+            });
         }
         if (lane == 0) {
             s.h[i] = (T)Hev;

@@ -159,6 +159,7 @@ struct Ctx {
     unsigned char* aflag = nullptr;  // [N] active (sorted order)
     unsigned char* tflag = nullptr;  // [N] touched (sorted order)
     unsigned char* cellact = nullptr;     // [cells] cell holds an active particle
+    unsigned char* cellnear = nullptr;    // [cells] an active cell lies within two cells
     unsigned long long* dtmax = nullptr;  // [nboxes] largest finite criterion (bits)
     int* hcount_host = nullptr;           // pinned copy of hcount
 };
@@ -327,16 +328,20 @@ __device__ __forceinline__ void for_candidates(const Grid& g, const BoxInfo& bx,
     }
 }
 
-// Warp-cooperative for_candidates for one particle per warp (every lane
-// passes the same particle): the same cells in the same order; within a cell
-// the lanes take the candidates start + lane, start + 32 + lane, ... in rounds
-// that every lane runs, calling fn(j, valid, dx, dy, dz, r2) each round
-// (valid = false past the cell's end and for the particle itself).  Offsets
-// as in for_candidates (mi_diff; every offset is correctly rounded).
+// Warp-cooperative candidate scan for one particle per warp (every lane
+// passes the same particle): each lane calls fn(j, dx, dy, dz, r2) for its
+// share of the candidates j != self in the cells overlapping [x - R, x + R]
+// (cells whose nearest point lies beyond R skipped, as in for_candidates).
+// Small ranges (under 64 cells) are shared candidate by candidate (the lanes
+// take start + lane, start + 32 + lane, ... of every cell); large ones cell by
+// cell (lane l takes cells l, l + 32, ... of the range, in row order), which
+// keeps lanes busy where a wide support holds many sparse cells.  Which lane
+// sees which candidate depends only on the particle, so per-lane sums
+// combined in a fixed order are deterministic.  Offsets from mi_diff.
 template <typename T, typename F>
-__device__ __forceinline__ void for_candidates_warp(const Grid& g, const BoxInfo& bx,
-                                                    const P4<T>* __restrict__ pos, int self, T xi, T yi,
-                                                    T zi, T R, int lane, F&& fn) {
+__device__ __forceinline__ void for_candidates_lanes(const Grid& g, const BoxInfo& bx,
+                                                     const P4<T>* __restrict__ pos, int self, T xi, T yi,
+                                                     T zi, T R, int lane, F&& fn) {
     const int nc = bx.nc;
     const int2* __restrict__ cells = g.cells + bx.cell_off;
     if (!(xi >= T(0) && xi <= T(1) && yi >= T(0) && yi <= T(1) && zi >= T(0) && zi <= T(1) &&
@@ -345,6 +350,7 @@ __device__ __forceinline__ void for_candidates_warp(const Grid& g, const BoxInfo
     const bool full = !(R < T(0.5));
     const T c3[3] = {xi, yi, zi};
     int lo[3], hi[3];
+    bool wraps_all = full;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         lo[a] = full ? 0 : (int)floor((c3[a] - R) * (T)nc - T(1e-3));
@@ -352,32 +358,45 @@ __device__ __forceinline__ void for_candidates_warp(const Grid& g, const BoxInfo
         if (hi[a] - lo[a] + 1 >= nc) {
             lo[a] = 0;
             hi[a] = nc - 1;
+            wraps_all = true;
         }
     }
     const T xim1 = xi - T(1), yim1 = yi - T(1), zim1 = zi - T(1);
-    for (int cz = lo[2]; cz <= hi[2]; ++cz) {
+    const T cl = T(1) / (T)nc, R2m = R * R * T(1.0001);
+    auto gap = [&](int c, T v) { return wraps_all ? T(0) : max(max((T)c * cl - v, v - (T)(c + 1) * cl), T(0)); };
+    auto cell_range = [&](int cx, int cy, int cz, int2& se) {
+        const T gx = gap(cx, xi), gy = gap(cy, yi), gz = gap(cz, zi);
+        if (gx * gx + gy * gy + gz * gz > R2m) return false;
+        const int wx = cx < 0 ? cx + nc : (cx >= nc ? cx - nc : cx);
+        const int wy = cy < 0 ? cy + nc : (cy >= nc ? cy - nc : cy);
         const int wz = cz < 0 ? cz + nc : (cz >= nc ? cz - nc : cz);
-        for (int cy = lo[1]; cy <= hi[1]; ++cy) {
-            const int wy = cy < 0 ? cy + nc : (cy >= nc ? cy - nc : cy);
-            const int row = (wz * nc + wy) * nc;
-            for (int cx = lo[0]; cx <= hi[0]; ++cx) {
-                const int wx = cx < 0 ? cx + nc : (cx >= nc ? cx - nc : cx);
-                const int2 se = cells[row + wx];
-                for (int j0 = se.x; j0 < se.y; j0 += 32) {
-                    const int j = j0 + lane;
-                    const bool valid = j < se.y && j != self;
-                    T dx = T(0), dy = T(0), dz = T(0), r2 = T(0);
-                    if (valid) {
-                        const P4<T> q = pos[j];
-                        dx = mi_diff(q.x, xi, xim1);
-                        dy = mi_diff(q.y, yi, yim1);
-                        dz = mi_diff(q.z, zi, zim1);
-                        r2 = sep2(dx, dy, dz);
-                    }
-                    fn(j, valid, dx, dy, dz, r2);
-                }
-            }
+        se = cells[(wz * nc + wy) * nc + wx];
+        return true;
+    };
+    auto visit = [&](int j) {
+        const P4<T> q = pos[j];
+        const T dx = mi_diff(q.x, xi, xim1), dy = mi_diff(q.y, yi, yim1), dz = mi_diff(q.z, zi, zim1);
+        fn(j, dx, dy, dz, sep2(dx, dy, dz));
+    };
+    const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
+    const int ncube = ex * ey * ez;
+    if (ncube >= 64) {
+        for (int f = lane; f < ncube; f += 32) {
+            const int cx = lo[0] + f % ex, cy = lo[1] + (f / ex) % ey, cz = lo[2] + f / (ex * ey);
+            int2 se;
+            if (!cell_range(cx, cy, cz, se)) continue;
+            for (int j = se.x; j < se.y; ++j)
+                if (j != self) visit(j);
         }
+    } else {
+        for (int cz = lo[2]; cz <= hi[2]; ++cz)
+            for (int cy = lo[1]; cy <= hi[1]; ++cy)
+                for (int cx = lo[0]; cx <= hi[0]; ++cx) {
+                    int2 se;
+                    if (!cell_range(cx, cy, cz, se)) continue;
+                    for (int j = se.x + lane; j < se.y; j += 32)
+                        if (j != self) visit(j);
+                }
     }
 }
 
