@@ -1,0 +1,73 @@
+"""The FP32 (mixed) path's error against the FP64 oracle, field by field:
+each pass on the oracle's frozen inputs (rounded to FP32), and one whole
+step, on three workload kinds.  Prints the table (pytest -s) and checks the
+2e-5-of-RMS tolerance for every pass field."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1712_01294_gb300 import inputs as I
+
+from gpu_common import cast_state, device, field_err, min_image, ostate
+
+pytestmark = pytest.mark.gpu
+
+GRAD_NAMES = [f"grad {f}/{a}" for f in ("rho", "vx", "vy", "vz", "P") for a in "xyz"]
+B_NAMES = ["B xx", "B xy", "B xz", "B yy", "B yz", "B zz"]
+
+
+def report(kind, q):
+    import torch
+
+    import paper_1712_01294_gb300 as m
+    rows = []
+    s = ostate(q)
+    p = O.params()
+    Ho, no, _, _ = O.density(s, p)
+    ctx = m.Context([s.N], m.default_params(precision=m.GZ_MIXED32))
+    d = device(q, m.GZ_MIXED32)
+    n_g, _ = ctx.density(d)
+    rows.append(("density", "H", field_err(d["h"].cpu().numpy(), Ho)))
+    rows.append(("density", "n", field_err(n_g.cpu().numpy(), no)))
+    H32, n32 = (a.astype(np.float32).astype(np.float64) for a in (Ho, no))
+    g = O.gradients(s, H32, n32, p)
+    dg = device(q, m.GZ_MIXED32, H=H32)
+    grad, B = ctx.gradients(dg, torch.as_tensor(n32, dtype=torch.float32).cuda())
+    grad, B = grad.cpu().numpy(), B.cpu().numpy()
+    for r in range(15):
+        rows.append(("gradients", GRAD_NAMES[r], field_err(grad[r], g["grad"][r])))
+    for r in range(6):
+        rows.append(("gradients", B_NAMES[r], field_err(B[r], g["B"][r])))
+    g32, B32 = (a.astype(np.float32).astype(np.float64) for a in (g["grad"], g["B"]))
+    _, dt = O.timestep(s, H32, n32, p)
+    dp_o, dE_o = O.fluxes(s, H32, n32, g32, B32, dt, p)
+    dp, dE = ctx.hydro_fluxes(dg, torch.as_tensor(n32, dtype=torch.float32).cuda(),
+                              torch.as_tensor(g32, dtype=torch.float32).cuda().contiguous(),
+                              torch.as_tensor(B32, dtype=torch.float32).cuda().contiguous(), dt)
+    dp, dE = dp.cpu().numpy(), dE.cpu().numpy()
+    for r, nm in enumerate(("dp/dt x", "dp/dt y", "dp/dt z")):
+        rows.append(("fluxes", nm, field_err(dp[r], dp_o[r])))
+    rows.append(("fluxes", "dE/dt", field_err(dE, dE_o)))
+    o, _, _, _, _ = O.step(s, p)
+    ds = device(q, m.GZ_MIXED32)
+    ctx.step(ds)
+    for k in ("x", "y", "z"):
+        rows.append(("step (change)", k, field_err(min_image(ds[k].cpu().numpy().astype(np.float64) - getattr(s, k)),
+                                                    min_image(getattr(o, k) - getattr(s, k)))))
+    for k in ("vx", "vy", "vz", "u"):
+        rows.append(("step (change)", k, field_err(ds[k].cpu().numpy().astype(np.float64) - getattr(s, k),
+                                                    getattr(o, k) - getattr(s, k))))
+    assert ctx.status(reset=True)["ok"]
+    return rows
+
+
+@pytest.mark.parametrize("kind,n", [("turb", 24), ("sod", 24), ("sedov", 24)])
+def test_fp32_error_per_field(kind, n):
+    make = {"turb": I.turbulence, "sod": I.sod, "sedov": I.sedov}[kind]
+    rows = report(kind, cast_state(make(n), 1))
+    print(f"\n{kind} {n}^3: pass | field | max |err|/RMS | RMS err/RMS")
+    for pss, nm, (mx, rm) in rows:
+        print(f"{pss} | {nm} | {mx:.2e} | {rm:.2e}")
+    for pss, nm, (mx, rm) in rows:
+        if pss != "step (change)":
+            assert rm <= 2e-5, (pss, nm, rm)
