@@ -355,3 +355,40 @@ def test_invalid_positions_are_flagged():
     st = ctx.status(reset=True)
     assert "nonfinite" in st["bits"]
     assert st["first_bad_id"] == 3
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_density_with_wide_supports_matches_the_oracle(prec):
+    """Half the box thinned to one particle in 27 (supports of up to 2.6 cells
+    there, 156 candidates within 1.05 H against the density pass's 48-entry
+    cache near the dense half): those particles go to the warp-per-particle
+    kernel (both of its ways of sharing a scan: candidate by candidate, and
+    cell by cell for ranges of 64 cells or more).  FP64: neighbour sets and
+    iteration counts bit-exact; FP32: H within 2e-6."""
+    import torch
+    m = gz()
+    p = I.turbulence(24, seed=21)
+    rng = np.random.default_rng(5)
+    keep = (p.x >= 0.5) | (rng.uniform(size=p.x.size) < 1 / 27)
+    for k in ("x", "y", "z", "vx", "vy", "vz", "m", "u", "H", "id"):
+        setattr(p, k, getattr(p, k)[keep])
+    p.id = np.arange(p.x.size, dtype=np.int64)
+    q = cast_state(p, prec)
+    s = ostate(q)
+    Ho, no, ito, _ = O.density(s, O.params())
+    off, _ = O.neighbours(s, 1.05 * Ho)
+    assert np.diff(off).max() > 48  # candidates beyond the cache: the warp kernel's particles
+    ctx = ctx_for(s.N, prec, max_ngb=256)  # (up to ~150 neighbours near the interface)
+    d = device(q, prec)
+    n_g, it_g = ctx.density(d)
+    assert_status_ok(ctx)
+    cnt, gs = gpu_sets(ctx, 256)
+    Hg = d["h"].cpu().numpy().astype(np.float64)
+    if prec == 0:
+        assert np.array_equal(it_g.cpu().numpy(), ito)
+        assert np.max(np.abs(Hg - Ho) / Ho) <= 1e-12
+        os_ = oracle_sets(s, Ho)
+        bad = [i for i in range(s.N) if gs[i] != os_[i]]
+        assert not bad, bad[:10]
+    else:
+        assert np.max(np.abs(Hg - Ho) / Ho) <= 2e-6
