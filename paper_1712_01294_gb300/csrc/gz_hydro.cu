@@ -31,6 +31,55 @@ constexpr int kDensBlock = 64;
 // (blasts in a few thousand particles) overflow 40 more often.
 constexpr int kDensCacheLarge = 40, kDensCacheSmall = 48;
 
+// Radius of the candidate cache for a support Ht: 5% headroom so that small
+// growth of H during the iteration needs no rescan, never past h_lim.
+template <typename T>
+__device__ __forceinline__ T dens_cache_radius(T Ht, const KParams& p) {
+    T R = Ht * T(1.05);
+    if (!(R < (T)p.h_lim)) R = max(Ht, (T)p.h_lim);
+    return R;
+}
+
+// Rescan into the thread's shared-memory cache (the support grew past the
+// cache radius): kept out of line so that the iteration loop holds no scan
+// state; returns the number of candidates within R.
+template <typename T, int kDensCache>
+__device__ __noinline__ int dens_fill(const Grid& g, const BoxInfo& bx, const P4<T>* __restrict__ pos, int i,
+                                      T xi, T yi, T zi, T R, T (*c_r2)[kDensBlock],
+                                      unsigned (*c_j)[kDensBlock], int t) {
+    const T R2 = R * R;
+    int n = 0;
+    for_candidates<T>(g, bx, pos, i, xi, yi, zi, R, [&](int j, T, T, T, T r2) {
+        if (r2 < R2) {
+            if (n < kDensCache) {
+                c_r2[n][t] = r2;
+                c_j[n][t] = (unsigned)j;
+            }
+            ++n;
+        }
+    });
+    return n;
+}
+
+// One evaluation straight from the cells (more candidates than the cache
+// holds and no deferral): the sums and the neighbour list of Ht.
+template <typename T>
+__device__ __noinline__ void dens_eval_cells(const Grid& g, const BoxInfo& bx, const P4<T>* __restrict__ pos,
+                                             int i, T xi, T yi, T zi, T Ht, unsigned* __restrict__ row, int cap,
+                                             Acc<T>& sw, T& sd, int& c) {
+    const T H2 = Ht * Ht;
+    const T iH = T(1) / Ht;
+    for_candidates<T>(g, bx, pos, i, xi, yi, zi, Ht, [&](int j, T, T, T, T r2) {
+        if (r2 < H2) {
+            const T q = sqrt(r2) * iH;
+            sw.add(kern_w(q));
+            sd += -kern_dw(q) * q;
+            if (c < cap) row[c] = (unsigned)j;
+            ++c;
+        }
+    });
+}
+
 template <typename T, int kDensCache>
 __global__ void __launch_bounds__(kDensBlock)
     k_density(int N, Sorted<T> s, Grid g, KParams p, unsigned* __restrict__ nbr,
@@ -56,37 +105,48 @@ __global__ void __launch_bounds__(kDensBlock)
         H = cbrt(3.0 * p.ngb / (4.0 * kPi * (double)bx.count));
         if (!(H < p.h_lim)) H = 0.5 * p.h_lim;
     }
+    // the cache of the starting H, scanned before the iteration (few live
+    // values here, the iteration's FP64 state not yet among them)
+    T Rc;
+    int ncache;
+    bool cached;
+    {
+        Rc = dens_cache_radius<T>((T)H, p);
+        const T R2 = Rc * Rc;
+        int n = 0;
+        for_candidates<T>(g, bx, s.pos, i, xi, yi, zi, Rc, [&](int j, T, T, T, T r2) {
+            if (r2 < R2) {
+                if (n < kDensCache) {
+                    c_r2[n][t] = r2;
+                    c_j[n][t] = (unsigned)j;
+                }
+                ++n;
+            }
+        });
+        ncache = n;
+        cached = n <= kDensCache;
+        if (!cached && defer) {
+            // more candidates than the cache holds (a support spanning many
+            // cells): left to k_density_warp, where a whole warp scans for
+            // it and runs the iteration from the starting H
+            defer[atomicAdd(ndefer, 1)] = i;
+            return;
+        }
+    }
     const double C = 32.0 / 3.0;
     double lo = 0.0, hi = 0.0, S = 0.0, Hev = H;
-    bool has_lo = false, has_hi = false, conv = false, clamped = false, cached = false;
-    T Rc = T(0), sd_last = T(0);
-    int it, cnt = 0, ncache = 0;
+    bool has_lo = false, has_hi = false, conv = false, clamped = false;
+    T sd_last = T(0);
+    int it, cnt = 0;
     for (it = 1; it <= p.max_iter; ++it) {
         const T Ht = (T)H;
         const T H2 = Ht * Ht;
         const T iH = T(1) / Ht;
-        if (!cached || Ht > Rc) {
-            T R = Ht * T(1.05);
-            if (!(R < (T)p.h_lim)) R = max(Ht, (T)p.h_lim);
-            const T R2 = R * R;
-            int n = 0;
-            for_candidates<T>(g, bx, s.pos, i, xi, yi, zi, R,
-                              [&](int j, T, T, T, T r2) {
-                                  if (r2 < R2) {
-                                      if (n < kDensCache) {
-                                          c_r2[n][t] = r2;
-                                          c_j[n][t] = (unsigned)j;
-                                      }
-                                      ++n;
-                                  }
-                              });
-            Rc = R;
-            ncache = n;
-            cached = n <= kDensCache;
+        if (!cached || Ht > Rc) {  // grew past the cache radius: rescan
+            Rc = dens_cache_radius<T>(Ht, p);
+            ncache = dens_fill<T, kDensCache>(g, bx, s.pos, i, xi, yi, zi, Rc, c_r2, c_j, t);
+            cached = ncache <= kDensCache;
             if (!cached && defer) {
-                // more candidates than the cache holds (a support spanning many
-                // cells): left to k_density_warp, where a whole warp scans for
-                // it and runs the iteration again from the starting H
                 defer[atomicAdd(ndefer, 1)] = i;
                 return;
             }
@@ -105,16 +165,7 @@ __global__ void __launch_bounds__(kDensBlock)
                 }
             }
         } else {
-            for_candidates<T>(g, bx, s.pos, i, xi, yi, zi, Ht,
-                              [&](int j, T, T, T, T r2) {
-                                  if (r2 < H2) {
-                                      const T q = sqrt(r2) * iH;
-                                      sw.add(kern_w(q));
-                                      sd += -kern_dw(q) * q;
-                                      if (c < p.cap) nbr[(size_t)i * p.cap + c] = (unsigned)j;
-                                      ++c;
-                                  }
-                              });
+            dens_eval_cells<T>(g, bx, s.pos, i, xi, yi, zi, Ht, nbr + (size_t)i * p.cap, p.cap, sw, sd, c);
         }
         cnt = c;
         sd_last = sd;
