@@ -10,6 +10,7 @@ template <typename T>
 struct Acc {
     T s = T(0);
     __device__ __forceinline__ void add(T v) { s += v; }
+    __device__ __forceinline__ void merge(const Acc& o) { s += o.s; }
     __device__ __forceinline__ double value() const { return (double)s; }
 };
 template <>
@@ -21,6 +22,7 @@ struct Acc<float> {
         c = __fsub_rn(__fsub_rn(t, s), y);
         s = t;
     }
+    __device__ __forceinline__ void merge(const Acc& o) { add(o.fvalue()); }
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
     __device__ __forceinline__ float fvalue() const { return __fsub_rn(s, c); }
 };

@@ -71,9 +71,11 @@ __device__ __noinline__ void dens_eval_cells(const Grid& g, const BoxInfo& bx, c
     const T iH = T(1) / Ht;
     for_candidates<T>(g, bx, pos, i, xi, yi, zi, Ht, [&](int j, T, T, T, T r2) {
         if (r2 < H2) {
-            const T q = sqrt(r2) * iH;
-            sw.add(kern_w(q));
-            sd += -kern_dw(q) * q;
+            const T q = psqrt(r2) * iH;
+            T w, qdw;
+            dens_terms(q, w, qdw);
+            sw.add(w);
+            sd += qdw;
             if (c < cap) row[c] = (unsigned)j;
             ++c;
         }
@@ -158,9 +160,11 @@ __global__ void __launch_bounds__(kDensBlock)
             for (int k = 0; k < ncache; ++k) {
                 const T r2 = c_r2[k][t];
                 if (r2 < H2) {
-                    const T q = sqrt(r2) * iH;
-                    sw.add(kern_w(q));
-                    sd += -kern_dw(q) * q;
+                    const T q = psqrt(r2) * iH;
+                    T w, qdw;
+                    dens_terms(q, w, qdw);
+                    sw.add(w);
+                    sd += qdw;
                     ++c;
                 }
             }
@@ -298,9 +302,11 @@ __global__ void __launch_bounds__(kWarpDensBlock)
             int c = 0;
             for_candidates_lanes<T>(g, bx, s.pos, i, xi, yi, zi, Ht, lane, [&](int, T, T, T, T r2) {
                 if (r2 < H2) {
-                    const T q = sqrt(r2) * iH;
-                    sw.add(kern_w(q));
-                    sd += -kern_dw(q) * q;
+                    const T q = psqrt(r2) * iH;
+                    T w, qdw;
+                    dens_terms(q, w, qdw);
+                    sw.add(w);
+                    sd += qdw;
                     ++c;
                 }
             });
@@ -445,9 +451,11 @@ __global__ void __launch_bounds__(128)
     for_candidates<T>(g, bx, s.pos, i, me.x, me.y, me.z, Ht,
                       [&](int j, T, T, T, T r2) {
                           if (r2 < H2) {
-                              const T q = sqrt(r2) * iH;
-                              sw.add(kern_w(q));
-                              sd += -kern_dw(q) * q;
+                              const T q = psqrt(r2) * iH;
+                              T w, qdw;
+                              dens_terms(q, w, qdw);
+                              sw.add(w);
+                              sd += qdw;
                               if (c < p.cap) nbr[(size_t)i * p.cap + c] = (unsigned)j;
                               ++c;
                           }

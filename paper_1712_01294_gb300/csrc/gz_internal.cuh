@@ -208,6 +208,26 @@ __device__ __forceinline__ T kern_dw(T q) {
     return q <= T(0.5) ? a : (q < T(1) ? b : T(0));
 }
 
+// The two terms of the density sum at q = r / H (Eq. O2's kernel): W(q) and
+// -q W'(q).  FP64: the pieces as above.  FP32: one cubic in x = q (q <= 1/2)
+// or x = 1 - q (beyond), whose coefficients are selected, not both pieces
+// evaluated:  W = 1 - 6x^2 + 6x^3 | 2x^3,  -q W' = 12x^2 - 18x^3 | 6x^2 - 6x^3
+// (the outer piece in 1 - q, as in kern_w, so no cancellation near q = 1).
+// Callers pass q < 1 up to rounding (entries with r^2 < H^2).
+template <typename T>
+__device__ __forceinline__ void dens_terms(T q, T& w, T& qdw) {
+    w = kern_w(q);
+    qdw = -kern_dw(q) * q;
+}
+template <>
+__device__ __forceinline__ void dens_terms<float>(float q, float& w, float& qdw) {
+    const bool in = q <= 0.5f;
+    const float x = in ? q : 1.f - q;
+    const float x2 = x * x;
+    w = fmaf(fmaf(in ? 6.f : 2.f, x, in ? -6.f : 0.f), x2, in ? 1.f : 0.f);
+    qdw = fmaf(in ? -18.f : -6.f, x, in ? 12.f : 6.f) * x2;
+}
+
 __device__ __forceinline__ bool finite_(float v) { return isfinite(v); }
 __device__ __forceinline__ bool finite_(double v) { return isfinite(v); }
 
@@ -288,38 +308,50 @@ __device__ __forceinline__ void for_candidates(const Grid& g, const BoxInfo& bx,
                 if (!cell_ok(row + wx)) continue;  // (cell index within the box)
                 const int2 se = cells[row + wx];
                 if (percell) {
-                    // four candidates' positions in flight at a time
+                    // four candidates' positions in flight at a time, their
+                    // offsets formed before any is used (independent chains;
+                    // offsets of slots past the cell's end are discarded)
                     for (int j0 = se.x; j0 < se.y; j0 += 4) {
                         P4<T> q[4];
+                        T dxs[4], dys[4], dzs[4], r2s[4];
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
                             if (j0 + u < se.y) q[u] = pos[j0 + u];
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
+                            dxs[u] = (q[u].x + ax) - bxx;
+                            dys[u] = (q[u].y + ay) - by;
+                            dzs[u] = (q[u].z + az) - bz;
+                            r2s[u] = sep2(dxs[u], dys[u], dzs[u]);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
                             const int j = j0 + u;
                             if (j >= se.y) break;
                             if (j == self) continue;
-                            const T dx = (q[u].x + ax) - bxx;
-                            const T dy = (q[u].y + ay) - by;
-                            const T dz = (q[u].z + az) - bz;
-                            fn(j, dx, dy, dz, sep2(dx, dy, dz));
+                            fn(j, dxs[u], dys[u], dzs[u], r2s[u]);
                         }
                     }
                 } else {
                     for (int j0 = se.x; j0 < se.y; j0 += 4) {
                         P4<T> q[4];
+                        T dxs[4], dys[4], dzs[4], r2s[4];
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
                             if (j0 + u < se.y) q[u] = pos[j0 + u];
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
+                            dxs[u] = mi_diff(q[u].x, xi, xim1);
+                            dys[u] = mi_diff(q[u].y, yi, yim1);
+                            dzs[u] = mi_diff(q[u].z, zi, zim1);
+                            r2s[u] = sep2(dxs[u], dys[u], dzs[u]);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
                             const int j = j0 + u;
                             if (j >= se.y) break;
                             if (j == self) continue;
-                            const T dx = mi_diff(q[u].x, xi, xim1);
-                            const T dy = mi_diff(q[u].y, yi, yim1);
-                            const T dz = mi_diff(q[u].z, zi, zim1);
-                            fn(j, dx, dy, dz, sep2(dx, dy, dz));
+                            fn(j, dxs[u], dys[u], dzs[u], r2s[u]);
                         }
                     }
                 }
