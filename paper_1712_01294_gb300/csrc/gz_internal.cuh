@@ -254,6 +254,13 @@ __device__ __forceinline__ unsigned long long dbits(double v) {
 // (a, b) = (0, x_i), (-1, x_i) for cells wrapped below 0 (x_j - 1 is exact
 // there) or (0, x_i - 1) for cells wrapped above 1 (x_i - 1 is exact): the
 // same correctly rounded offsets mi_diff gives, at a third of the cost.
+// On that path fn is also called for the slots of the last group of four
+// that lie past a cell's range, with r2 = +inf (j then names no candidate):
+// every fn tests r2 against a finite radius before it uses j, so those calls
+// do nothing, and the loop needs no per-candidate bounds test.  The own cell
+// is scanned as the two ranges either side of self (no per-candidate test
+// for self either); candidates arrive in ascending j within each cell, as on
+// the other path.
 struct AllCells {
     __device__ __forceinline__ bool operator()(int) const { return true; }
 };
@@ -309,14 +316,14 @@ __device__ __forceinline__ void for_candidates(const Grid& g, const BoxInfo& bx,
                 const int2 se = cells[row + wx];
                 if (percell) {
                     // four candidates' positions in flight at a time, their
-                    // offsets formed before any is used (independent chains;
-                    // offsets of slots past the cell's end are discarded)
+                    // offsets formed before any is used (independent chains);
+                    // slots past the range read a far-away point (r2 = +inf)
                     for (int j0 = se.x; j0 < se.y; j0 += 4) {
                         P4<T> q[4];
                         T dxs[4], dys[4], dzs[4], r2s[4];
 #pragma unroll
                         for (int u = 0; u < 4; ++u)
-                            if (j0 + u < se.y) q[u] = pos[j0 + u];
+                            q[u] = j0 + u < se.y ? pos[j0 + u] : P4<T>{T(1e30), T(1e30), T(1e30), T(0)};
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             dxs[u] = (q[u].x + ax) - bxx;
@@ -325,12 +332,8 @@ __device__ __forceinline__ void for_candidates(const Grid& g, const BoxInfo& bx,
                             r2s[u] = sep2(dxs[u], dys[u], dzs[u]);
                         }
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int j = j0 + u;
-                            if (j >= se.y) break;
-                            if (j == self) continue;
-                            fn(j, dxs[u], dys[u], dzs[u], r2s[u]);
-                        }
+                        for (int u = 0; u < 4; ++u)
+                            if (j0 + u != self) fn(j0 + u, dxs[u], dys[u], dzs[u], r2s[u]);
                     }
                 } else {
                     for (int j0 = se.x; j0 < se.y; j0 += 4) {
