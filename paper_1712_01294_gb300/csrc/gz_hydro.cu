@@ -764,8 +764,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
                 dt_i = (any && vmax > T(0)) ? 2.0 * cbrt(1.0 / (double)ni) / (double)vmax : INFINITY;
             dti[i] = dt_i;
         }
-        if (ginfo) {  // what the adjoint of this pass needs
-            T* G = ginfo + (size_t)i * kGInfo;
+        if (ginfo) {  // what the adjoint of this pass needs (rows 32-byte aligned)
+            T G[kGInfo];
 #pragma unroll
             for (int q = 0; q < 15; ++q) {
                 G[q] = gt[q];
@@ -775,11 +775,18 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
             for (int f = 0; f < 5; ++f) {
                 G[30 + f] = al[f];
                 G[35 + f] = Dact[f];
-                lim[(size_t)i * 10 + f] = jact[f];
-                lim[(size_t)i * 10 + 5 + f] = kact[f];
             }
+            store_row32<kGInfo>(ginfo + (size_t)i * kGInfo, G);
+            // the limiting particles: jact[0..4] then kact[0..4], a 40-byte row
+            // (8-byte aligned) written as five 8-byte stores
+            const int Lv[10] = {jact[0], jact[1], jact[2], jact[3], jact[4],
+                                kact[0], kact[1], kact[2], kact[3], kact[4]};
+            int2* Lm = reinterpret_cast<int2*>(lim + (size_t)i * 10);
+#pragma unroll
+            for (int m = 0; m < 5; ++m) Lm[m] = make_int2(Lv[2 * m], Lv[2 * m + 1]);
         }
-        T* R = rec + (size_t)i * kRecord;
+        // the flux record: one 128-byte (FP32) row, written with 32-byte stores
+        T R[kRecord];
         R[0] = xi;
         R[1] = yi;
         R[2] = zi;
@@ -795,6 +802,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
         for (int q = 0; q < 15; ++q) R[11 + q] = al[q / 3] * gt[q];
 #pragma unroll
         for (int q = 0; q < 6; ++q) R[26 + q] = B[q];
+        store_row32<kRecord>(rec + (size_t)i * kRecord, R);
     }
     if (want_dt) {
         // warp-level minimum per box, one atomic per warp when the warp is in one box
