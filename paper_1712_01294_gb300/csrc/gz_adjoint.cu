@@ -486,7 +486,10 @@ __global__ void __launch_bounds__(128)
     T gb[15];
     T Bb[6];
     for (int q = 0; q < 6; ++q) Bb[q] = (T)a[AB + q];
-    for (int q = 28; q < kSeed; ++q) sd[q] = T(0.0);
+    // the limiter part of the record (28-55) starts at zero: 16-byte stores
+    // (rows are 32-byte aligned, 56 values a row)
+#pragma unroll
+    for (int q = 28; q < kSeed; q += 4) store4(sd + q, T(0), T(0), T(0), T(0));
     const T beta = p.beta;
     for (int f = 0; f < 5; ++f) {
         const T al = G[30 + f];
@@ -562,11 +565,13 @@ __global__ void __launch_bounds__(128)
     const T iH = T(1) / Hi;
     const T norm = T(8.0 / kPi) * iH * iH * iH / ni;
     // record read by every j with j in N_i (k_grad_gather)
-    for (int q = 0; q < 15; ++q) sd[q] = Sb[q];
-    for (int q = 0; q < 6; ++q) sd[15 + q] = Eb[q];
-    sd[21] = norm;
-    for (int f = 0; f < 5; ++f) sd[22 + f] = Wi[f];
-    sd[27] = T(0);
+    {  // (16-byte stores)
+        const T r0[28] = {Sb[0], Sb[1], Sb[2], Sb[3], Sb[4], Sb[5], Sb[6], Sb[7], Sb[8], Sb[9],
+                          Sb[10], Sb[11], Sb[12], Sb[13], Sb[14], Eb[0], Eb[1], Eb[2], Eb[3], Eb[4],
+                          Eb[5], norm, Wi[0], Wi[1], Wi[2], Wi[3], Wi[4], T(0)};
+#pragma unroll
+        for (int q = 0; q < 28; q += 4) store4(sd + q, r0[q], r0[q + 1], r0[q + 2], r0[q + 3]);
+    }
     lbloom[i] = bloom;
     T normb = T(0.0);
     const int cnt = min(ncount[i], p.cap);
