@@ -257,10 +257,8 @@ __device__ __forceinline__ unsigned long long dbits(double v) {
 // On that path fn is also called for the slots of the last group of four
 // that lie past a cell's range, with r2 = +inf (j then names no candidate):
 // every fn tests r2 against a finite radius before it uses j, so those calls
-// do nothing, and the loop needs no per-candidate bounds test.  The own cell
-// is scanned as the two ranges either side of self (no per-candidate test
-// for self either); candidates arrive in ascending j within each cell, as on
-// the other path.
+// do nothing, and the loop needs no per-candidate bounds test.  Candidates
+// arrive in ascending j within each cell, as on the other path.
 struct AllCells {
     __device__ __forceinline__ bool operator()(int) const { return true; }
 };
