@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(128)
         const P4<T> qj = qv[u];
         const T dxT = mi_diff(qj.x, xi, xim1), dyT = mi_diff(qj.y, yi, yim1), dzT = mi_diff(qj.z, zi, zim1);
         const T r2 = sep2(dxT, dyT, dzT);
-        const T r = sqrt(r2);
+        const T r = psqrt(r2);
         const T q = r * iH;
         const T w = kern_w(q), dw = kern_dw(q);
         const T psi = (T)(norm * kern_w(q));
@@ -685,7 +685,7 @@ __global__ void __launch_bounds__(128)
             const T* R = seeds + (size_t)i * kSeed;
             T sd[32];  // record 0-27 (and 4 limiter values, unused here)
             load_row32<32>(R, sd);
-            const T r = sqrt(r2);
+            const T r = psqrt(r2);
             const T iH = T(1) / Hi;
             const T q = r * iH;
             const T norm = sd[21];
@@ -792,7 +792,7 @@ __global__ void __launch_bounds__(128)
             if (k0 + u >= cnt) break;
             const P4<T> qj = qv[u];
             const T dx = mi_diff(qj.x, xi, xim1), dy = mi_diff(qj.y, yi, yim1), dz = mi_diff(qj.z, zi, zim1);
-            const T r = sqrt(sep2(dx, dy, dz));
+            const T r = psqrt(sep2(dx, dy, dz));
             if (!(r > T(0))) continue;
             const T c = kappa * (T)kern_dw(r * iH) * pdiv(T(1), r);
             xb[0] -= c * dx;
@@ -833,7 +833,7 @@ __global__ void __launch_bounds__(128)
                         dz = mi_diff(mj.z, mi.z, mi.z - T(1));
                 const T r2 = sep2(dx, dy, dz);
                 if (!(r2 < mi.w * mi.w)) continue;
-                const T r = sqrt(r2);
+                const T r = psqrt(r2);
                 if (!(r > T(0))) continue;
                 const T c = kap[i] * kern_dw(r * pdiv(T(1), mi.w)) * pdiv(T(1), r);
                 xb[0] += c * dx;

@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
                 const T dx = mi_diff(q[u].x, xi, xim1), dy = mi_diff(q[u].y, yi, yim1),
                         dz = mi_diff(q[u].z, zi, zim1);
                 const T r2 = sep2(dx, dy, dz);
-                const T r = sqrt(r2);
+                const T r = psqrt(r2);
                 const T psi = norm * kern_w(r * iH);
                 const T pdx = psi * dx, pdy = psi * dy, pdz = psi * dz;
                 E[0] += pdx * dx;
@@ -752,7 +752,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
                 const P4<T> w = s.prim[j];
                 const T dx = mi_diff(q.x, xi, xim1), dy = mi_diff(q.y, yi, yim1),
                         dz = mi_diff(q.z, zi, zim1);
-                const T r = sqrt(sep2(dx, dy, dz));
+                const T r = psqrt(sep2(dx, dy, dz));
                 const T vd = ((w.y - Wi[1]) * dx + (w.z - Wi[2]) * dy) + (w.w - Wi[3]) * dz;
                 const T vs = ci + s.prim2[j].y - min(pdiv(vd, r), T(0));
                 vmax = any ? max(vmax, vs) : vs;
