@@ -126,7 +126,7 @@ def _load():
             lib.gzo_pair.restype = C.c_int
             lib.gzo_pair.argtypes = [vp, d, d, vp, vp, vp, vp, d, d, vp, vp, vp, d,
                                      C.POINTER(Params), vp, _D, _D, vp, vp, _D, _D,
-                                     C.POINTER(C.c_int)]
+                                     C.POINTER(C.c_int), vp]
             lib.gzo_hllc_flux.restype = None
             lib.gzo_hllc_flux.argtypes = [vp, vp, vp, vp, d, _D, vp, _D]
             lib.gzo_hllc.restype = None
@@ -361,8 +361,13 @@ def exchange(x, y, z, ids, m, H, n, vx, vy, vz, u, grad, B, bins, active, D, p: 
 
 
 def pair(L: dict, R: dict, dt: float, p: Params):
-    """One canonical face (L = lower id); dicts hold x[3], H, n, W[5], g[15], B[6]."""
+    """One canonical face (L = lower id); dicts hold x[3], H, n, W[5], g[15], B[6].
+
+    Also returns the face states of O11 (rho, vx, vy, vz, P per side):
+    ``pred_L``/``pred_R`` after reconstruction and the Hancock half step,
+    ``face_L``/``face_R`` after the clamp (what the Riemann solver sees)."""
     A = np.zeros(3)
+    face = np.full(20, np.nan)
     vf = np.zeros(3)
     dp = np.zeros(3)
     ps, ss, dE, dm = C.c_double(), C.c_double(), C.c_double(), C.c_double()
@@ -371,9 +376,11 @@ def pair(L: dict, R: dict, dt: float, p: Params):
     ok = _load().gzo_pair(_p(arrs[0]), float(L["H"]), float(L["n"]), _p(arrs[1]), _p(arrs[2]),
                           _p(arrs[3]), _p(arrs[4]), float(R["H"]), float(R["n"]), _p(arrs[5]),
                           _p(arrs[6]), _p(arrs[7]), float(dt), C.byref(p), _p(A), C.byref(ps),
-                          C.byref(ss), _p(vf), _p(dp), C.byref(dE), C.byref(dm), C.byref(fl))
+                          C.byref(ss), _p(vf), _p(dp), C.byref(dE), C.byref(dm), C.byref(fl),
+                          _p(face))
     return {"ok": ok, "A": A, "pstar": ps.value, "sstar": ss.value, "vf": vf, "dp": dp,
-            "dE": dE.value, "dm": dm.value, "flags": fl.value}
+            "dE": dE.value, "dm": dm.value, "flags": fl.value, "pred_L": face[0:5],
+            "pred_R": face[5:10], "face_L": face[10:15], "face_R": face[15:20]}
 
 
 def hllc_flux(FL, FR, vf, nh, gamma):

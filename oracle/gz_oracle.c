@@ -706,7 +706,7 @@ int gzo_pair(const double* xL, double HL, double nL, const double* WL, const dou
              const double* BL, const double* xR, double HR, double nR, const double* WR,
              const double* gR, const double* BR, double dt, const gzo_params* p,
              double* A, double* pstar, double* sstar, double* vf, double* dp, double* dE,
-             double* dm, int* flags) {
+             double* dm, int* flags, double* face) {
     double d[3];
     for (int a = 0; a < 3; ++a) d[a] = gzo_min_image(xR[a] - xL[a]);
     double r2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
@@ -754,6 +754,11 @@ int gzo_pair(const double* xL, double HL, double nL, const double* WL, const dou
         FL[4] += h * (-p->gamma * WL[4] * divL);
         FR[4] += h * (-p->gamma * WR[4] * divR);
     }
+    if (face)
+        for (int q = 0; q < 5; ++q) {
+            face[q] = FL[q];
+            face[5 + q] = FR[q];
+        }
     for (int q = 0; q < 5; ++q) {
         double lo = WL[q] < WR[q] ? WL[q] : WR[q];
         double hi = WL[q] < WR[q] ? WR[q] : WL[q];
@@ -767,6 +772,11 @@ int gzo_pair(const double* xL, double HL, double nL, const double* WL, const dou
         }
         *flags |= 1;
     }
+    if (face)
+        for (int q = 0; q < 5; ++q) {
+            face[10 + q] = FL[q];
+            face[15 + q] = FR[q];
+        }
     double vfn = (vf[0] * nh[0] + vf[1] * nh[1]) + vf[2] * nh[2];
     double uL = ((FL[1] - vf[0]) * nh[0] + (FL[2] - vf[1]) * nh[1]) + (FL[3] - vf[2]) * nh[2];
     double uR = ((FR[1] - vf[0]) * nh[0] + (FR[2] - vf[1]) * nh[1]) + (FR[3] - vf[2]) * nh[2];
@@ -850,7 +860,7 @@ int gzo_fluxes(int64_t N, const double* x, const double* y, const double* z,
                 double A[3], ps, ss, vf[3], dp[3], dE, dm;
                 int fl;
                 gzo_pair(pL, H[L], n[L], WL, gL, BL, pR, H[R], n[R], WR, gR, BR, dt, p, A, &ps,
-                         &ss, vf, dp, &dE, &dm, &fl);
+                         &ss, vf, dp, &dE, &dm, &fl, NULL);
                 if (fl & 1) nfall++;
                 if (fl & 2) nneg++;
                 double sg = (i == L) ? 1.0 : -1.0;
@@ -1057,7 +1067,7 @@ int gzo_exchange(int64_t N, const double* x, const double* y, const double* z,
                 double A[3], ps, ss, vf[3], dp[3], dE, dm;
                 int fl = 0;
                 gzo_pair(pL, H[L], n[L], WL, gL, BL, pR, H[R], n[R], WR, gR, BR, dtij, p, A, &ps,
-                         &ss, vf, dp, &dE, &dm, &fl);
+                         &ss, vf, dp, &dE, &dm, &fl, NULL);
                 if (fl & 1) nfall++;
                 if (fl & 2) nneg++;
                 double sg = ((i == L) ? 1.0 : -1.0) * ldexp(1.0, bin[i] - kij);

@@ -154,13 +154,16 @@ int gzo_exchange(int64_t N, const double* x, const double* y, const double* z,
  * two particles' positions, H, n, primitives (rho, vx, vy, vz, P), limited
  * gradients [15] and B [6].  Outputs the face area vector A[3], P*, S*,
  * the face-frame velocity vf[3], and the L-side rate contributions
- * dp[3], dE and dm (zero under MFM; R receives the negatives).  Returns 0 if
- * |A| = 0. */
+ * dp[3], dE and dm (zero under MFM; R receives the negatives).  face (may be
+ * NULL) receives the face states (rho, vx, vy, vz, P) of both sides at two
+ * points of O11: [0,5) L and [5,10) R after the reconstruction and the
+ * Hancock half step, before the clamp; [10,15) L and [15,20) R as handed to
+ * the Riemann solver.  Returns 0 if |A| = 0 (face then untouched). */
 int gzo_pair(const double* xL, double HL, double nL, const double* WL, const double* gL,
              const double* BL, const double* xR, double HR, double nR, const double* WR,
              const double* gR, const double* BR, double dt, const gzo_params* p,
              double* A, double* pstar, double* sstar, double* vf, double* dp, double* dE,
-             double* dm, int* flags);
+             double* dm, int* flags, double* face);
 
 /* MFV face flux (HLLC, Davis speeds) for face states FL, FR (rho, v[3], P,
  * lab frame) through a face moving with vf, unit normal nh from L to R:
