@@ -339,21 +339,25 @@ gz_status gz_profile_read(gz_ctx* ctx, double* ms, int64_t* calls, int32_t reset
  * a library-interface addition).  For callers that cannot call cudaMalloc:
  * host codes whose device memory is all handed out by their own pool or
  * budget, and loops that cannot afford the device-wide synchronisation an
- * allocation may cause.  Same result as gz_density on a one-box context of
- * n particles with these params: reads x, y, z, h (initial guess), id
- * (device arrays of the working precision; vx, vy, vz, m, u are ignored),
- * writes the converged H back into h, n into n_out and the f-evaluation
- * counts into iters_out (either may be NULL); enqueued on cuda_stream.
- * Scratch: a fixed array inside the library (about 8.1 MB, held on every GPU
+ * allocation may cause.  Runs the same kernels as gz_density on a one-box
+ * context of n particles with these params, so h, n and the iteration counts
+ * are bitwise the same: reads x, y, z, h (initial guess), id (device arrays
+ * of the working precision; vx, vy, vz, m, u are ignored), writes the
+ * converged H back into h, n into n_out and the f-evaluation counts into
+ * iters_out (either may be NULL); enqueued on cuda_stream.  Neighbour lists
+ * are not kept (max_ngb has no effect).  status_out (device pointer, may be
+ * NULL) receives this call's device status bits (GZ_S_*: positions outside
+ * the box, non-convergence, ...; never GZ_S_NBR_OVERFLOW, as no list is
+ * kept) when the stream reaches the end of the call.
+ * Scratch: a fixed array inside the library (about 8.3 MB, held on every GPU
  * that loads the library until exit).  Limits: 1 <= n <= 32768 and a cell
  * grid of at most 32^3 cells (cell_factor * H0 >= 1/32), else GZ_E_INVAL.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture.  Every call reuses the same array, so calls that overlap on the
- * GPU (other streams, other host threads) race; serialise them.  Device-side
- * conditions are not reported: non-convergence shows as iters == max_iter. */
+ * GPU (other streams, other host threads) race; serialise them. */
 gz_status gz_density_noalloc(const gz_params* params, int64_t n, gz_particles* p, void* n_out,
-                             int32_t* iters_out, void* cuda_stream);
+                             int32_t* iters_out, uint32_t* status_out, void* cuda_stream);
 
 /* Measured throughput of one SM pipe on the current device (a measurement
  * aid for the ALU roofline, not part of the method): which = 0 FP32 fused

@@ -37,10 +37,11 @@ constexpr size_t kScratchBytes =
     + al(8 * (size_t)kMaxN)                            // sorted ids
     + 3 * al(4 * (size_t)kMaxN)                        // sorted box, iterations, counts
     + al(4 * (size_t)kMaxN * kCap)                     // neighbour lists
+    + al(4 * (size_t)kMaxN) + al(4)                    // deferred particles and their count
     + al(sizeof(DevStatus));
 
 // The scratch itself: every GPU that loads the library holds these bytes
-// (8,136,192 B, about 8.1 MB) until the process exits.  All calls share it.
+// (8,267,520 B, about 8.3 MB) until the process exits.  All calls share it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mu;
@@ -64,6 +65,19 @@ cudaError_t scratch_on_current_device(void** out) {
     return cudaSuccess;
 }
 
+// The one-box table, written on the device from values passed by value (no
+// host buffer is referenced by the enqueued work).
+__global__ void k_noalloc_box(BoxInfo* boxes, int nc, int count) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) boxes[0] = BoxInfo{nc, 0, 0, count};
+}
+
+// Copies the status bits of this call to the caller's word.  The lists are
+// not returned (and hold only kCap slots), so their overflow bit means nothing
+// to the caller and is left out.
+__global__ void k_noalloc_status(const DevStatus* st, uint32_t* out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = st->bits & ~(unsigned)GZ_S_NBR_OVERFLOW;
+}
+
 int ceil_log2i(long long v) {
     int b = 0;
     while ((1ll << b) < v) ++b;
@@ -72,7 +86,7 @@ int ceil_log2i(long long v) {
 
 template <typename T>
 gz_status run(const gz_params* prm, int N, gz_particles* p, void* n_out, int32_t* iters_out,
-              cudaStream_t stream) {
+              uint32_t* status_out, cudaStream_t stream) {
     void* base = nullptr;
     if (scratch_on_current_device(&base) != cudaSuccess) return GZ_E_CUDA;
     // same cell grid as a one-box context of this size
@@ -121,6 +135,10 @@ gz_status run(const gz_params* prm, int N, gz_particles* p, void* n_out, int32_t
     c.iters = (int*)take(4 * Nz);
     c.ncount = (int*)take(4 * Nz);
     c.nbr = (unsigned*)take(4 * Nz * kCap);
+    // particles with more candidates than the per-thread cache go to the
+    // warp-per-particle kernel, exactly as in gz_density
+    c.defer = (int*)take(4 * Nz);
+    c.ndefer = (int*)take(4);
     c.status = (DevStatus*)take(sizeof(DevStatus));
     // the density pass never touches these
     c.svx = c.svy = c.svz = c.sm = c.su = c.srho = c.sP = c.sc = c.ssd = nullptr;
@@ -133,14 +151,14 @@ gz_status run(const gz_params* prm, int N, gz_particles* p, void* n_out, int32_t
     c.box_hits = nullptr;
     c.pairs_dev = nullptr;
 
-    // the scratch keeps the previous call's contents: reset what must start clean
-    BoxInfo bx;
-    bx.nc = nc;
-    bx.cell_off = 0;
-    bx.first = 0;
-    bx.count = N;
+    // the scratch keeps the previous call's contents: reset what must start
+    // clean (the box of every particle, the box table, the status word; the
+    // deferred count is reset by the density launcher)
     cudaError_t e = cudaMemsetAsync(c.box_of, 0, 4 * (size_t)N, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(c.boxes, &bx, sizeof(bx), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) {
+        k_noalloc_box<<<1, 32, 0, stream>>>(c.boxes, nc, N);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(c.status, 0, sizeof(DevStatus), stream);
     gz_particles only = *p;
     only.vx = only.vy = only.vz = only.m = only.u = nullptr;
@@ -149,6 +167,7 @@ gz_status run(const gz_params* prm, int N, gz_particles* p, void* n_out, int32_t
     if (e == cudaSuccess) e = unpermute_T<T>(c, (const T*)c.sh, (T*)p->h, 1);
     if (e == cudaSuccess && n_out) e = unpermute_T<T>(c, (const T*)c.sn, (T*)n_out, 1);
     if (e == cudaSuccess && iters_out) e = unpermute_i(c, c.iters, iters_out);
+    if (e == cudaSuccess && status_out) k_noalloc_status<<<1, 32, 0, stream>>>(c.status, status_out);
     if (e == cudaSuccess) e = cudaGetLastError();
     return e == cudaSuccess ? GZ_OK : GZ_E_CUDA;
 }
@@ -156,7 +175,8 @@ gz_status run(const gz_params* prm, int N, gz_particles* p, void* n_out, int32_t
 }  // namespace
 
 extern "C" gz_status gz_density_noalloc(const gz_params* params, int64_t n, gz_particles* p,
-                                        void* n_out, int32_t* iters_out, void* cuda_stream) {
+                                        void* n_out, int32_t* iters_out, uint32_t* status_out,
+                                        void* cuda_stream) {
     if (!params || !p || !p->x || !p->y || !p->z || !p->h || !p->id) return GZ_E_INVAL;
     if (n < 1 || n > kMaxN) return GZ_E_INVAL;
     if (params->precision != GZ_FP64 && params->precision != GZ_MIXED32) return GZ_E_INVAL;
@@ -165,6 +185,6 @@ extern "C" gz_status gz_density_noalloc(const gz_params* params, int64_t n, gz_p
         return GZ_E_INVAL;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     return params->precision == GZ_FP64
-               ? run<double>(params, (int)n, p, n_out, iters_out, s)
-               : run<float>(params, (int)n, p, n_out, iters_out, s);
+               ? run<double>(params, (int)n, p, n_out, iters_out, status_out, s)
+               : run<float>(params, (int)n, p, n_out, iters_out, status_out, s);
 }
