@@ -135,6 +135,10 @@ typedef struct {
     int32_t scheme;      /* GZ_MFM or GZ_MFV (GZ_MFM)                                 */
     int32_t riemann;     /* MFM face solver: GZ_RIEMANN_HLLC, _EXACT or _FALLBACK     */
                          /* (GZ_RIEMANN_HLLC); GZ_MFV takes GZ_RIEMANN_HLLC only      */
+    int32_t density_cache; /* h-iteration candidate cache per particle: 40 or 48      */
+                           /* entries, or 0 (40 when every box holds >= 32^3          */
+                           /* particles, else 48); a particle with more candidates    */
+                           /* within 1.05 H is iterated by a whole warp (0)            */
 } gz_params;
 
 /* Structure-of-arrays particle set; every pointer is device memory with N
@@ -220,6 +224,45 @@ gz_status gz_hydro_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const voi
  * doubles, may be NULL) receives the steps used.  No host synchronisation. */
 gz_status gz_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev);
 
+/* The step split in two around its timestep: gz_step_begin runs S1-S3 (bin
+ * and sort, h-iteration, primitives, pair lists, gradients and limiter) and
+ * writes to dt_box_dev (device, nboxes doubles) the CFL step of each box,
+ * cfl * min_i dtc_i (O13) over the box's owned particles (all of them outside
+ * a subdomain); gz_step_finish then runs S4 and S6 (fluxes, update) with the
+ * steps in dt_dev (device, nboxes doubles, e.g. the minimum of dt_box_dev
+ * over the subdomains of one box).  gz_step_finish takes the particle set
+ * given to gz_step_begin, unchanged, with no other call on the context in
+ * between; begin then finish with dt_dev = dt_box_dev is gz_step bit for bit.
+ * No host synchronisation.  Errors: GZ_E_INVAL (null arrays, finish without
+ * begin), GZ_E_CUDA. */
+gz_status gz_step_begin(gz_ctx* ctx, gz_particles* p, double* dt_box_dev);
+gz_status gz_step_finish(gz_ctx* ctx, gz_particles* p, const double* dt_dev);
+
+/* Domain decomposition: one periodic box split into subdomains, each held by
+ * its own context (one per GPU, or several on one GPU), the GPU form of the
+ * domain decomposition of the paper's hybrid MPI + OpenMP runtime (Sec. 1
+ * and Sec. 3).  A subdomain context holds its owned particles and ghost
+ * copies of the particles whose data its owned particles' step reads (a
+ * halo, several support radii deep, refreshed by the caller each step).
+ * gz_create_subdomain: one box whose arrays hold up to capacity particles and
+ * whose cell grid (cell length cell_factor * H0) and density cache are those
+ * of a box of grid_count particles, the whole undivided box, so that its
+ * cells hold the same particles in the same order as that box's.
+ * gz_set_subdomain: the particles of the next calls are n <= capacity arrays
+ * (caller order; the whole box's relative order of particles is kept when
+ * the caller keeps them in ascending id), owned (device, n bytes, copied; 1 =
+ * owned, 0 = ghost; NULL = all owned) marks the n_owned owned ones.  Ghosts
+ * are stepped like the others but take no part in the box's CFL minimum, and
+ * the u floor (O14) takes the lower median of the owned particles' u.  With a
+ * halo deep enough that every particle the owned particles' density,
+ * gradient and flux passes read sees its full neighbourhood, the owned
+ * particles' step equals the undivided box's bit for bit (the u floor
+ * excepted: a subdomain's median is its own).  Errors: GZ_E_INVAL (not a
+ * subdomain context, sizes out of range), GZ_E_NOMEM, GZ_E_CUDA. */
+gz_status gz_create_subdomain(const gz_params* params, int64_t capacity, int64_t grid_count,
+                              void* cuda_stream, gz_ctx** out);
+gz_status gz_set_subdomain(gz_ctx* ctx, int64_t n, int64_t n_owned, const uint8_t* owned);
+
 /* Hierarchical (individual, power-of-two) timesteps: advances every box of p
  * by one sync interval D split into 2^K substeps of D/2^K (K in [0, 20]).
  * Reading of the paper's hierarchical adaptive timesteps (it gives no
@@ -275,6 +318,17 @@ gz_status gz_graph_launch(gz_ctx* ctx);
 #define GZ_CKPT_RATES 0
 #define GZ_CKPT_GRADIENTS 1
 gz_status gz_checkpoint_bytes(gz_ctx* ctx, int32_t level, int64_t* bytes);
+
+/* The choices of the O9 limiter in the step whose checkpoint is ckpt (level
+ * GZ_CKPT_GRADIENTS, the last gz_step_checkpoint on this context, with no
+ * call that sorts in between), as particle ids in caller order: ids_out
+ * (device, [10][N] int64) rows 0-4 (fields rho, vx, vy, vz, P) the neighbour
+ * whose face bound set alpha_f (-1 where alpha_f = 1), rows 5-9 the particle
+ * holding the extreme that bound reached (the particle itself where alpha_f =
+ * 1).  Two runs with the same choices crossed no limiter switch: the step is
+ * smooth between them in the limiter (a derivative check needs that).
+ * Errors: GZ_E_INVAL (null arguments, ckpt not that checkpoint), GZ_E_CUDA. */
+gz_status gz_checkpoint_limiters(gz_ctx* ctx, const void* ckpt, int64_t* ids_out);
 
 /* gz_step (same arguments and effect) that also fills the checkpoint ckpt
  * at the given level.  Host synchronisation: none. */

@@ -51,7 +51,7 @@ class Params(C.Structure):
                 ("u_floor_frac", C.c_double), ("h_lim", C.c_double),
                 ("cell_factor", C.c_double), ("precision", C.c_int32), ("hancock", C.c_int32),
                 ("max_iter", C.c_int32), ("max_ngb", C.c_int32), ("scheme", C.c_int32),
-                ("riemann", C.c_int32)]
+                ("riemann", C.c_int32), ("density_cache", C.c_int32)]
 
 
 class _Particles(C.Structure):
@@ -102,6 +102,11 @@ def load_library(build_if_missing: bool = True):
             "gz_profile_enable": (st, [vp, i32]),
             "gz_profile_read": (st, [vp, vp, vp, i32]),
             "gz_measure_alu": (st, [i32, vp, vp]),
+            "gz_step_begin": (st, [vp, P, vp]),
+            "gz_step_finish": (st, [vp, P, vp]),
+            "gz_create_subdomain": (st, [C.POINTER(Params), C.c_int64, C.c_int64, vp, C.POINTER(vp)]),
+            "gz_set_subdomain": (st, [vp, C.c_int64, C.c_int64, vp]),
+            "gz_checkpoint_limiters": (st, [vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -156,19 +161,29 @@ class Context:
 
     FIELDS = ("x", "y", "z", "vx", "vy", "vz", "m", "u", "h", "id")
 
-    def __init__(self, counts, params: Params | None = None, stream=None, **kw):
+    def __init__(self, counts, params: Params | None = None, stream=None, grid_count: int = 0, **kw):
+        """grid_count > 0: a subdomain context (gz_create_subdomain) of one box
+        holding up to counts[0] particles, its cell grid that of a box of
+        grid_count particles."""
         import torch
         self.torch = torch
         self.lib = load_library()
         self.params = params if params is not None else default_params(**kw)
         self.counts = [int(c) for c in counts]
         self.N = sum(self.counts)
+        self.capacity = self.N
         self.dtype = torch.float64 if self.params.precision == GZ_FP64 else torch.float32
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        arr = (C.c_int64 * len(self.counts))(*self.counts)
         h = C.c_void_p()
-        rc = self.lib.gz_create(C.byref(self.params), len(self.counts), C.cast(arr, C.c_void_p),
-                                C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if grid_count > 0:
+            if len(self.counts) != 1:
+                raise ValueError("a subdomain context holds one box")
+            rc = self.lib.gz_create_subdomain(C.byref(self.params), self.N, int(grid_count),
+                                              C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        else:
+            arr = (C.c_int64 * len(self.counts))(*self.counts)
+            rc = self.lib.gz_create(C.byref(self.params), len(self.counts), C.cast(arr, C.c_void_p),
+                                    C.c_void_p(self.stream.cuda_stream), C.byref(h))
         if rc != GZ_OK:
             raise GZError(rc, "gz_create failed")
         self.h = h
@@ -274,6 +289,31 @@ class Context:
                                                     _ptr(ckpt), int(level)), "gz_step_checkpoint")
         return dt_used
 
+    def step_begin(self, p, dt_box=None):
+        """gz_step_begin: S1-S3 on p; returns dt_box (device float64 [nboxes]),
+        each box's CFL step over its owned particles."""
+        dt_box = self.empty(len(self.counts), dtype=self.torch.float64) if dt_box is None else dt_box
+        s = self._parts(p)
+        self._check(self.lib.gz_step_begin(self.h, C.byref(s), _ptr(dt_box)), "gz_step_begin")
+        return dt_box
+
+    def step_finish(self, p, dt):
+        """gz_step_finish: S4 and S6 on the particle set of step_begin with the
+        steps dt (device float64 [nboxes])."""
+        s = self._parts(p)
+        self._check(self.lib.gz_step_finish(self.h, C.byref(s), _ptr(dt)), "gz_step_finish")
+
+    def set_subdomain(self, n: int, n_owned: int, owned=None):
+        """gz_set_subdomain: the next calls take n particles, of which the
+        n_owned marked in owned (CUDA uint8 [n], 1 = owned; None = all) are owned."""
+        if owned is not None and (owned.dtype != self.torch.uint8 or not owned.is_cuda
+                                  or not owned.is_contiguous() or owned.numel() != n):
+            raise ValueError("owned must be a contiguous CUDA uint8 tensor of n elements")
+        self._check(self.lib.gz_set_subdomain(self.h, int(n), int(n_owned), _ptr(owned)),
+                    "gz_set_subdomain")
+        self.N = int(n)
+        self.counts = [int(n)]
+
     def step_hier(self, p, K: int, dt_fixed: float = 0.0, dt_used=None, bins=None):
         """gz_step_hier: one sync interval of 2^K hierarchical substeps in place on
         p; dt_used (device float64 [nboxes]) receives the interval, bins (device
@@ -295,6 +335,14 @@ class Context:
         """A device buffer for one step checkpoint (GZ_CKPT_RATES = 0 or
         GZ_CKPT_GRADIENTS = 1)."""
         return self.empty(self.checkpoint_bytes(level), dtype=self.torch.uint8)
+
+    def checkpoint_limiters(self, ckpt):
+        """gz_checkpoint_limiters: the limiter's choices of the step that wrote
+        ckpt (level GZ_CKPT_GRADIENTS, the last one): int64 [10, N] of ids."""
+        out = self.empty(10, self.N, dtype=self.torch.int64)
+        self._check(self.lib.gz_checkpoint_limiters(self.h, _ptr(ckpt), _ptr(out)),
+                    "gz_checkpoint_limiters")
+        return out
 
     def _ckpt_ok(self, ckpt, level):
         if (ckpt.dtype != self.torch.uint8 or not ckpt.is_cuda or not ckpt.is_contiguous()

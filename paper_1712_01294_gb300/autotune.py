@@ -1,14 +1,21 @@
-"""Autotuner for the cell grid of a context.
+"""Autotuner for the launch-shape knobs of a context.
 
-The cell length (``cell_factor`` x H0 of each box) decides how many
-candidate cells the h-iteration scans and how evenly the per-cell loops of a
-warp are filled; the best value depends on the particle distribution (a
-lattice-aligned grid can be twice as fast as a misaligned one).  The tuner
-times a few full steps for each candidate factor on a copy of the caller's
-particles (through the C ABI, CUDA-event timed) and keeps the fastest; results
-are cached by (particle counts, precision, distribution signature) in a JSON
-file.  Kernel block shapes are fixed by design (one thread per particle,
-sized for occupancy at their register counts), so the cell grid is the knob.
+Two knobs decide how the density pass maps particles to lanes:
+* the cell length (``cell_factor`` x H0 of each box) decides how many
+  candidate cells the h-iteration scans and how evenly the per-cell loops of
+  a warp are filled; the best value depends on the particle distribution (a
+  lattice-aligned grid can be twice as fast as a misaligned one);
+* the candidate cache per particle (``density_cache``, 40 or 48 entries)
+  decides which particles get one lane and which a whole warp: a particle
+  with more candidates within 1.05 H than its cache holds is iterated by a
+  warp (a blast cavity, the smallest boxes of an ensemble), and the larger
+  cache costs occupancy.
+The tuner times a few full steps for each combination on a copy of the
+caller's particles (through the C ABI, CUDA-event timed) and keeps the
+fastest; results are cached by (particle counts, precision, distribution
+signature) in a JSON file.  The other kernels' block shapes are fixed by
+design (one thread per particle, sized for occupancy at their register
+counts).
 """
 from __future__ import annotations
 
@@ -19,6 +26,7 @@ import os
 import numpy as np
 
 DEFAULT_CANDIDATES = (0.7, 0.85, 1.0, 1.2, 1.45)
+DEFAULT_CACHES = (40, 48)
 
 
 def _cache_path(path=None):
@@ -39,14 +47,19 @@ def signature(p, precision) -> str:
     return f"{len(counts)}x{sum(counts)}:{digest}:p{int(precision)}:h{q[0]:.2f}-{q[1]:.2f}-{q[2]:.2f}"
 
 
-def tune(p, precision, candidates=DEFAULT_CANDIDATES, steps: int = 2, warmup: int = 1,
-         cache: str | None = None, use_cache: bool = True, **params):
-    """Returns (best cell_factor, {factor: ms per step}) for host particles p."""
+def _key(cf, cache):
+    return f"{float(cf)},{int(cache)}"
+
+
+def tune(p, precision, candidates=DEFAULT_CANDIDATES, caches=DEFAULT_CACHES, steps: int = 2,
+         warmup: int = 1, cache: str | None = None, use_cache: bool = True, **params):
+    """Returns (best (cell_factor, density_cache), {(cell_factor, density_cache): ms
+    per step}) for host particles p."""
     import torch
 
     import paper_1712_01294_gb300 as gz
     path = _cache_path(cache)
-    key = signature(p, precision)
+    key = signature(p, precision) + ":c" + "-".join(str(int(c)) for c in caches)
     db = {}
     if use_cache and os.path.exists(path):
         try:
@@ -54,30 +67,34 @@ def tune(p, precision, candidates=DEFAULT_CANDIDATES, steps: int = 2, warmup: in
         except Exception:
             db = {}
         if key in db:
-            return float(db[key]["best"]), {float(k): v for k, v in db[key]["ms"].items()}
+            def parse(k):
+                a, b = k.split(",")
+                return float(a), int(b)
+            return parse(db[key]["best"]), {parse(k): v for k, v in db[key]["ms"].items()}
     counts = [int(c) for c in (p.counts if len(p.counts) else [p.N])]
     stream = torch.cuda.Stream()
     ms = {}
     with torch.cuda.stream(stream):
         base = gz.to_device(p, precision)
         for cf in candidates:
-            ctx = gz.Context(counts, gz.default_params(precision=precision, cell_factor=cf, **params),
-                             stream=stream)
-            d = {k: v.clone() for k, v in base.items()}
-            for _ in range(warmup):
-                ctx.step(d)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(steps):
-                ctx.step(d)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if ctx.status(reset=True)["ok"]:
-                ms[float(cf)] = e0.elapsed_time(e1) / steps
-            ctx.close()
+            for dc in caches:
+                ctx = gz.Context(counts, gz.default_params(precision=precision, cell_factor=cf,
+                                                           density_cache=int(dc), **params), stream=stream)
+                d = {k: v.clone() for k, v in base.items()}
+                for _ in range(warmup):
+                    ctx.step(d)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(steps):
+                    ctx.step(d)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if ctx.status(reset=True)["ok"]:
+                    ms[(float(cf), int(dc))] = e0.elapsed_time(e1) / steps
+                ctx.close()
     best = min(ms, key=ms.get)
     if use_cache:
-        db[key] = {"best": best, "ms": {str(k): v for k, v in ms.items()}}
+        db[key] = {"best": _key(*best), "ms": {_key(*k): v for k, v in ms.items()}}
         os.makedirs(os.path.dirname(path), exist_ok=True)
         tmp = path + f".tmp{os.getpid()}"
         json.dump(db, open(tmp, "w"), indent=1)

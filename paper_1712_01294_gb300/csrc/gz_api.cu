@@ -49,6 +49,8 @@ bool params_ok(const gz_params* p, std::string& why) {
         return why = "riemann must be GZ_RIEMANN_HLLC, _EXACT or _FALLBACK", false;
     if (p->scheme == GZ_MFV && p->riemann != GZ_RIEMANN_HLLC)
         return why = "GZ_MFV takes GZ_RIEMANN_HLLC only", false;
+    if (p->density_cache != 0 && p->density_cache != 40 && p->density_cache != 48)
+        return why = "density_cache must be 0, 40 or 48", false;
     return true;
 }
 
@@ -329,6 +331,55 @@ gz_status do_step_backward(gz_ctx* ctx, const gz_particles* p, double dt, const 
     return cuda_check(ctx, e, "gz_step_backward");
 }
 
+// The first half of a step (S1-S3 with the CFL criterion) and, apart, its
+// second half (S4, S6) with a step given on the device: gz_step split where
+// a decomposed box takes the minimum over its subdomains.
+template <typename T>
+gz_status do_step_begin(gz_ctx* ctx, gz_particles* p, double* dt_box_dev) {
+    Ctx& c = ctx->c;
+    cudaError_t e;
+    {
+        Pass t(c, GZ_PASS_SORT);
+        e = sort_and_bin<T>(c, *p, nullptr);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_DENSITY);
+        e = run_density<T>(c);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_PRIM);
+        e = run_prim<T>(c);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_REVERSE);
+        e = run_reverse<T>(c);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_GRAD);
+        e = run_gradients<T>(c, true, false);
+        if (e == cudaSuccess) e = run_dt_out(c, dt_box_dev);
+    }
+    c.nbr_valid = 1;
+    c.step_open = e == cudaSuccess;
+    return cuda_check(ctx, e, "gz_step_begin");
+}
+
+template <typename T>
+gz_status do_step_finish(gz_ctx* ctx, gz_particles* p, const double* dt_dev) {
+    Ctx& c = ctx->c;
+    cudaError_t e = run_dt_copy(c, dt_dev);
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_FLUX);
+        e = run_fluxes<T>(c);
+    }
+    if (e == cudaSuccess) {
+        Pass t(c, GZ_PASS_UPDATE);
+        e = run_update<T>(c, *p, nullptr);
+    }
+    c.step_open = 0;
+    return cuda_check(ctx, e, "gz_step_finish");
+}
+
 template <typename T>
 gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev, const Ckpt& ck) {
     Ctx& c = ctx->c;
@@ -366,6 +417,7 @@ gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
         e = run_update<T>(c, *p, ck.rates);
     }
     c.nbr_valid = 1;
+    c.last_lim = ck.lim;
     return cuda_check(ctx, e, "gz_step");
 }
 
@@ -394,8 +446,10 @@ gz_status gz_default_params(gz_params* out) {
     return GZ_OK;
 }
 
-gz_status gz_create(const gz_params* params, int32_t nboxes, const int64_t* counts,
-                    void* cuda_stream, gz_ctx** out) {
+// gz_create, with the cell grid of each box built for grid_counts[b]
+// particles when grid_counts is given (a subdomain: the whole box's grid).
+gz_status create_ctx(const gz_params* params, int32_t nboxes, const int64_t* counts,
+                     const int64_t* grid_counts, void* cuda_stream, gz_ctx** out) {
     if (!out || !params || !counts || nboxes < 1) return GZ_E_INVAL;
     *out = nullptr;
     std::string why;
@@ -431,7 +485,8 @@ gz_status gz_create(const gz_params* params, int32_t nboxes, const int64_t* coun
     int first = 0;
     c.hboxes.resize(nboxes);
     for (int b = 0; b < nboxes; ++b) {
-        const double H0 = cbrt(3.0 * params->ngb / (4.0 * M_PI * (double)counts[b]));
+        const double gc = grid_counts ? (double)grid_counts[b] : (double)counts[b];
+        const double H0 = cbrt(3.0 * params->ngb / (4.0 * M_PI * gc));
         double f = floor(1.0 / (params->cell_factor * H0));
         int nc = f < 1.0 ? 1 : (f > 512.0 ? 512 : (int)f);
         c.hboxes[b].nc = nc;
@@ -522,8 +577,55 @@ gz_status gz_create(const gz_params* params, int32_t nboxes, const int64_t* coun
         delete ctx;
         return GZ_E_CUDA;
     }
+    c.capacity = (int)N;
     *out = ctx;
     return GZ_OK;
+}
+
+gz_status gz_create(const gz_params* params, int32_t nboxes, const int64_t* counts,
+                    void* cuda_stream, gz_ctx** out) {
+    return create_ctx(params, nboxes, counts, nullptr, cuda_stream, out);
+}
+
+gz_status gz_create_subdomain(const gz_params* params, int64_t capacity, int64_t grid_count,
+                              void* cuda_stream, gz_ctx** out) {
+    if (!out || capacity < 1 || grid_count < 1) return GZ_E_INVAL;
+    gz_status s = create_ctx(params, 1, &capacity, &grid_count, cuda_stream, out);
+    if (s) return s;
+    Ctx& c = (*out)->c;
+    c.grid_count = grid_count;
+    c.n_owned = c.N;
+    if (cudaMalloc(&c.owned, (size_t)capacity) != cudaSuccess) {
+        cudaGetLastError();
+        gz_destroy(*out);
+        *out = nullptr;
+        return GZ_E_NOMEM;
+    }
+    if (cudaMemsetAsync(c.owned, 1, (size_t)capacity, c.stream) != cudaSuccess ||
+        cudaStreamSynchronize(c.stream) != cudaSuccess) {
+        gz_destroy(*out);
+        *out = nullptr;
+        return GZ_E_CUDA;
+    }
+    return GZ_OK;
+}
+
+gz_status gz_set_subdomain(gz_ctx* ctx, int64_t n, int64_t n_owned, const uint8_t* owned) {
+    if (!ctx) return GZ_E_INVAL;
+    Ctx& c = ctx->c;
+    if (!c.owned) return fail(ctx, GZ_E_INVAL, "gz_set_subdomain: not a subdomain context");
+    if (n < 1 || n > c.capacity || n_owned < 0 || n_owned > n)
+        return fail(ctx, GZ_E_INVAL, "gz_set_subdomain: need 1 <= n <= capacity, 0 <= n_owned <= n");
+    c.N = (int)n;
+    c.counts[0] = n;
+    c.hboxes[0].count = (int)n;
+    c.n_owned = (int)n_owned;
+    c.nbr_valid = 0;
+    c.step_open = 0;
+    cudaError_t e = owned ? cudaMemcpyAsync(c.owned, owned, (size_t)n, cudaMemcpyDeviceToDevice, c.stream)
+                          : cudaMemsetAsync(c.owned, 1, (size_t)n, c.stream);
+    if (e == cudaSuccess) e = run_set_box(c);
+    return cuda_check(ctx, e, "gz_set_subdomain");
 }
 
 gz_status gz_destroy(gz_ctx* ctx) {
@@ -535,6 +637,7 @@ gz_status gz_destroy(gz_ctx* ctx) {
     }
     for (auto ev : ctx->c.ev_pool) cudaEventDestroy(ev);
     cudaFree(ctx->c.arena);
+    if (ctx->c.owned) cudaFree(ctx->c.owned);
     if (ctx->c.adj_arena) cudaFree(ctx->c.adj_arena);
     free_hier_scratch(ctx->c);
     if (ctx->c.graph_exec) cudaGraphExecDestroy(ctx->c.graph_exec);
@@ -603,6 +706,21 @@ gz_status gz_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
     if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
     return GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev, Ckpt()),
                        do_step<double>(ctx, p, dt_fixed, dt_used_dev, Ckpt()));
+}
+
+gz_status gz_step_begin(gz_ctx* ctx, gz_particles* p, double* dt_box_dev) {
+    if (!ctx) return GZ_E_INVAL;
+    if (gz_status s = check_particles(ctx, p, true)) return s;
+    if (!dt_box_dev) return fail(ctx, GZ_E_INVAL, "null dt_box_dev");
+    return GZ_DISPATCH(do_step_begin<float>(ctx, p, dt_box_dev), do_step_begin<double>(ctx, p, dt_box_dev));
+}
+
+gz_status gz_step_finish(gz_ctx* ctx, gz_particles* p, const double* dt_dev) {
+    if (!ctx) return GZ_E_INVAL;
+    if (gz_status s = check_particles(ctx, p, true)) return s;
+    if (!dt_dev) return fail(ctx, GZ_E_INVAL, "null dt_dev");
+    if (!ctx->c.step_open) return fail(ctx, GZ_E_INVAL, "gz_step_finish without gz_step_begin");
+    return GZ_DISPATCH(do_step_finish<float>(ctx, p, dt_dev), do_step_finish<double>(ctx, p, dt_dev));
 }
 
 gz_status gz_step_hier(gz_ctx* ctx, gz_particles* p, int32_t K, double dt_fixed, double* dt_used_dev,
@@ -711,6 +829,16 @@ gz_status gz_get_neighbours(gz_ctx* ctx, int32_t* count_out, int64_t* ids_out, i
     if (!ctx || !count_out || cap < 0) return GZ_E_INVAL;
     if (!ctx->c.nbr_valid) return fail(ctx, GZ_E_INVAL, "no neighbour lists yet");
     return cuda_check(ctx, run_get_neighbours(ctx->c, count_out, ids_out, cap), "gz_get_neighbours");
+}
+
+gz_status gz_checkpoint_limiters(gz_ctx* ctx, const void* ckpt, int64_t* ids_out) {
+    if (!ctx || !ckpt || !ids_out) return GZ_E_INVAL;
+    Ctx& c = ctx->c;
+    const Ckpt ck = ckpt_view(c, const_cast<void*>(ckpt), GZ_CKPT_GRADIENTS);
+    if (!c.last_lim || c.last_lim != ck.lim)
+        return fail(ctx, GZ_E_INVAL, "gz_checkpoint_limiters: ckpt is not the last step checkpoint "
+                                     "(GZ_CKPT_GRADIENTS) of this context");
+    return cuda_check(ctx, run_get_limiters(c, ck.lim, ids_out), "gz_checkpoint_limiters");
 }
 
 gz_status gz_get_status(gz_ctx* ctx, uint32_t* bits, int64_t* first_bad_id, int64_t* counters,

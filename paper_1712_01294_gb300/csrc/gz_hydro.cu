@@ -564,7 +564,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
                 const unsigned* __restrict__ rnbr, const int* __restrict__ rcount, KParams p,
                 T* __restrict__ rec, double* __restrict__ dti, unsigned long long* __restrict__ dtmin,
                 DevStatus* st, int want_dt, T* __restrict__ ginfo, int* __restrict__ lim,
-                const int* __restrict__ list, const int* __restrict__ nlist) {
+                const int* __restrict__ list, const int* __restrict__ nlist,
+                const unsigned char* __restrict__ owned) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     bool active;
     if (list) {  // the particles of an index list only (hierarchical steps)
@@ -805,9 +806,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
         store_row32<kRecord>(rec + (size_t)i * kRecord, R);
     }
     if (want_dt) {
-        // warp-level minimum per box, one atomic per warp when the warp is in one box
+        // warp-level minimum per box, one atomic per warp when the warp is in one box;
+        // in a subdomain only its owned particles take part
         const unsigned full = 0xffffffffu;
-        unsigned long long v = active ? dbits(dt_i) : dbits(INFINITY);
+        const bool counts = active && (!owned || owned[s.orig[i]]);
+        unsigned long long v = counts ? dbits(dt_i) : dbits(INFINITY);
         const int b0 = __shfl_sync(full, mybox, 0);
         const bool same = __all_sync(full, !active || mybox == b0);
         if (same) {
@@ -817,7 +820,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
                 v = w < v ? w : v;
             }
             if ((threadIdx.x & 31) == 0) atomicMin(&dtmin[b0], v);
-        } else if (active) {
+        } else if (counts) {
             atomicMin(&dtmin[mybox], v);
         }
     }
@@ -1024,20 +1027,24 @@ struct Bits<double> {
 // non-positive updated u of the box is set to u_floor_frac * median.
 template <typename T>
 __global__ void k_ufloor(Sorted<T> s, const BoxInfo* __restrict__ boxes,
-                         const int* __restrict__ box_hits, gz_particles out, double frac) {
+                         const int* __restrict__ box_hits, gz_particles out, double frac,
+                         const unsigned char* __restrict__ owned, int nown) {
     typedef typename Bits<T>::U U;
     const int b = blockIdx.x;
     if (box_hits[b] == 0) return;
     const int first = boxes[b].first, count = boxes[b].count;
+    // in a subdomain (owned non-null, one box) the median of its owned particles
     __shared__ unsigned hist[256];
     __shared__ U prefix_s;
     __shared__ int k_s;
     U prefix = 0, mask = 0;
-    int k = (count - 1) / 2;
+    int k = ((owned ? nown : count) - 1) / 2;
+    if (k < 0) return;
     for (int shift = Bits<T>::nbits - 8; shift >= 0; shift -= 8) {
         for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t] = 0;
         __syncthreads();
         for (int e = threadIdx.x; e < count; e += blockDim.x) {
+            if (owned && !owned[s.orig[first + e]]) continue;
             const U v = Bits<T>::get(s.u[first + e]);
             if ((v & mask) == prefix) atomicAdd(&hist[(unsigned)((v >> shift) & 255u)], 1u);
         }
@@ -1102,6 +1109,20 @@ __global__ void k_get_nbrs(int N, const unsigned* __restrict__ orig, const long 
         ids_out[(size_t)k * N + o] = k < m ? (int64_t)sid[nbr[(size_t)i * cap_in + k]] : (int64_t)-1;
 }
 
+// The limiter's choices per particle (sorted-order indices, 10 per particle)
+// as particle ids in caller order: rows 0-4 the neighbour whose face bound
+// set alpha_f (-1: alpha_f = 1), rows 5-9 the particle holding the extreme.
+__global__ void k_get_limiters(int N, const unsigned* __restrict__ orig, const long long* __restrict__ sid,
+                               const int* __restrict__ lim, int64_t* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const unsigned o = orig[i];
+    for (int f = 0; f < 10; ++f) {
+        const int j = lim[(size_t)i * 10 + f];
+        out[(size_t)f * N + o] = j >= 0 ? (int64_t)sid[j] : (int64_t)-1;
+    }
+}
+
 __global__ void k_pairs(int N, const int* __restrict__ ncount, const int* __restrict__ rcount,
                         int cap, int rcap, long long* __restrict__ out) {
     long long v = 0;
@@ -1149,8 +1170,11 @@ template <typename T>
 cudaError_t run_density(Ctx& c, const int* list, const int* nlist, int n) {
     if (!list) n = c.N;
     if (n < 1) return cudaSuccess;
-    int min_count = c.N;
-    for (const BoxInfo& b : c.hboxes) min_count = std::min(min_count, b.count);
+    long long min_count = c.N;
+    for (const BoxInfo& b : c.hboxes) min_count = std::min(min_count, (long long)b.count);
+    if (c.grid_count > 0) min_count = c.grid_count;  // a subdomain: as the whole box
+    if (c.params.density_cache == kDensCacheLarge) min_count = 32 * 32 * 32;
+    if (c.params.density_cache == kDensCacheSmall) min_count = 0;
     const Sorted<T> sv = sorted_view<T>(c);
     c.launches += c.defer ? 2 : 1;
     if (c.defer) cudaMemsetAsync(c.ndefer, 0, sizeof(int), c.stream);
@@ -1212,7 +1236,7 @@ cudaError_t run_gradients(Ctx& c, bool want_dt, bool with_info, const int* list,
     k_gradients<T><<<blocks(n, 128), 128, 0, c.stream>>>(
         c.N, sorted_view<T>(c), c.nbr, c.ncount, c.rnbr, c.rcount, kparams(c), (T*)c.rec, c.dti,
         (unsigned long long*)c.dt_box, c.status, want_dt ? 1 : 0, with_info ? (T*)c.ginfo : nullptr,
-        with_info ? c.lim : nullptr, list, nlist);
+        with_info ? c.lim : nullptr, list, nlist, c.owned);
     return cudaGetLastError();
 }
 
@@ -1263,7 +1287,7 @@ cudaError_t run_update(Ctx& c, gz_particles& p, double* rates_out) {
         c.N, sorted_view<T>(c), c.dpdt, c.dEdt, c.params.scheme == GZ_MFV ? c.dmdt : nullptr, c.dt_use, p,
         hits, c.status, rates_out);
     k_ufloor<T><<<c.nboxes, 1024, 0, c.stream>>>(sorted_view<T>(c), c.boxes, hits, p,
-                                                  c.params.u_floor_frac);
+                                                  c.params.u_floor_frac, c.owned, c.n_owned);
     return cudaGetLastError();
 }
 
@@ -1272,7 +1296,7 @@ template <typename T>
 cudaError_t run_ufloor(Ctx& c, gz_particles& p) {
     c.launches += 1;
     k_ufloor<T><<<c.nboxes, 1024, 0, c.stream>>>(sorted_view<T>(c), c.boxes, c.box_hits, p,
-                                                  c.params.u_floor_frac);
+                                                  c.params.u_floor_frac, c.owned, c.n_owned);
     return cudaGetLastError();
 }
 
@@ -1313,10 +1337,38 @@ cudaError_t run_dt_set(Ctx& c, double dt) {
     return cudaGetLastError();
 }
 
+__global__ void k_dt_copy(int nb, const double* __restrict__ dt, double* __restrict__ dt_use) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) dt_use[b] = dt[b];
+}
+
+cudaError_t run_dt_copy(Ctx& c, const double* dt) {
+    c.launches += 1;
+    k_dt_copy<<<blocks(c.nboxes, 256), 256, 0, c.stream>>>(c.nboxes, dt, c.dt_use);
+    return cudaGetLastError();
+}
+
+// One-box table of a subdomain, written from values passed by value.
+__global__ void k_set_box(BoxInfo* boxes, BoxInfo b) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) boxes[0] = b;
+}
+
+cudaError_t run_set_box(Ctx& c) {
+    c.launches += 1;
+    k_set_box<<<1, 32, 0, c.stream>>>(c.boxes, c.hboxes[0]);
+    return cudaGetLastError();
+}
+
 cudaError_t run_dt_out(Ctx& c, double* out) {
     c.launches += 1;
     k_dt_out<<<blocks(c.nboxes, 256), 256, 0, c.stream>>>(c.nboxes, (const unsigned long long*)c.dt_box,
                                                           c.params.cfl, out);
+    return cudaGetLastError();
+}
+
+cudaError_t run_get_limiters(Ctx& c, const int* lim, int64_t* out) {
+    c.launches += 1;
+    k_get_limiters<<<blocks(c.N, 256), 256, 0, c.stream>>>(c.N, c.vals, c.sid, lim, out);
     return cudaGetLastError();
 }
 

@@ -162,6 +162,14 @@ struct Ctx {
     unsigned char* cellnear = nullptr;    // [cells] an active cell lies within two cells
     unsigned long long* dtmax = nullptr;  // [nboxes] largest finite criterion (bits)
     int* hcount_host = nullptr;           // pinned copy of hcount
+    // subdomain of a decomposed box (gz_create_subdomain): the particles held
+    // are the owned ones and ghost copies completing their neighbourhoods
+    unsigned char* owned = nullptr;  // [capacity] 1 = owned (caller order); null: all owned
+    int n_owned = 0;                 // owned particles held
+    long long grid_count = 0;        // particle count the cell grid is built for (0: the box's own)
+    int capacity = 0;                // particles the arrays hold (the context's creation count)
+    int step_open = 0;               // gz_step_begin done, gz_step_finish pending
+    const int* last_lim = nullptr;   // limiter indices of the last step checkpoint, in this sort
 };
 
 // ------------------------------------------------------------------ status

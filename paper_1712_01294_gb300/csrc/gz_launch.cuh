@@ -55,7 +55,10 @@ cudaError_t run_dt_init(Ctx& c);
 cudaError_t run_dt_finalize(Ctx& c, double dt_fixed, double* dt_used_dev);
 cudaError_t run_dt_set(Ctx& c, double dt);
 cudaError_t run_dt_out(Ctx& c, double* out);
+cudaError_t run_dt_copy(Ctx& c, const double* dt);
+cudaError_t run_set_box(Ctx& c);
 cudaError_t run_get_neighbours(Ctx& c, int32_t* count_out, int64_t* ids_out, int cap);
+cudaError_t run_get_limiters(Ctx& c, const int* lim, int64_t* out);
 
 cudaError_t run_pair_count(Ctx& c, long long* out_dev);
 

@@ -181,7 +181,8 @@ extern "C" gz_status gz_density_noalloc(const gz_params* params, int64_t n, gz_p
     if (n < 1 || n > kMaxN) return GZ_E_INVAL;
     if (params->precision != GZ_FP64 && params->precision != GZ_MIXED32) return GZ_E_INVAL;
     if (!(params->ngb >= 1.0) || !(params->tol > 0.0) || !(params->cell_factor > 0.0) ||
-        !(params->h_lim > 0.0 && params->h_lim <= 0.5) || params->max_iter < 1)
+        !(params->h_lim > 0.0 && params->h_lim <= 0.5) || params->max_iter < 1 ||
+        (params->density_cache != 0 && params->density_cache != 40 && params->density_cache != 48))
         return GZ_E_INVAL;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     return params->precision == GZ_FP64

@@ -237,6 +237,7 @@ template Sorted<double> sorted_view<double>(Ctx&);
 
 template <typename T>
 cudaError_t sort_and_bin(Ctx& c, const gz_particles& p, const void* n_in) {
+    c.last_lim = nullptr;  // a new sort: earlier sorted-order indices no longer apply
     const int N = c.N;
     cudaStream_t st = c.stream;
     k_keys<T><<<blocks(N, 256), 256, 0, st>>>(N, (const T*)p.x, (const T*)p.y, (const T*)p.z, p.id,

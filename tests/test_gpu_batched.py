@@ -5,7 +5,7 @@ import torch
 
 from paper_1712_01294_gb300 import inputs as I
 
-from gpu_common import cast_state
+from gpu_common import cast_state, device
 
 pytestmark = pytest.mark.gpu
 
@@ -66,17 +66,38 @@ def test_ensemble_boxes_take_their_own_steps():
             assert torch.equal(d1[k], d[k][off[b]:off[b + 1]]), (b, k)
 
 
-def test_autotuner_picks_a_measured_factor(tmp_path):
+def test_autotuner_picks_a_measured_setting(tmp_path):
     m = gz()
     from paper_1712_01294_gb300 import autotune
     p = I.turbulence(24, seed=2)
     q = cast_state(p, m.GZ_MIXED32)
-    best, ms = autotune.tune(q, m.GZ_MIXED32, candidates=(0.8, 1.0, 1.3), steps=1,
+    best, ms = autotune.tune(q, m.GZ_MIXED32, candidates=(0.8, 1.0, 1.3), caches=(40, 48), steps=1,
                              cache=str(tmp_path / "tune.json"))
-    assert best in ms and ms[best] == min(ms.values()) and len(ms) == 3
-    best2, ms2 = autotune.tune(q, m.GZ_MIXED32, candidates=(0.8, 1.0, 1.3), steps=1,
+    assert best in ms and ms[best] == min(ms.values()) and len(ms) == 6
+    best2, ms2 = autotune.tune(q, m.GZ_MIXED32, candidates=(0.8, 1.0, 1.3), caches=(40, 48), steps=1,
                                cache=str(tmp_path / "tune.json"))
     assert best2 == best and ms2 == ms  # served from the cache
+
+
+def test_density_cache_knob_changes_no_result():
+    # which particles get a warp changes the sum order of those particles
+    # only; every field agrees to rounding and the counts of f evaluations
+    # agree except where an evaluation lands on the stop threshold
+    import torch
+    m = gz()
+    q = cast_state(I.sedov(20, seed=4), m.GZ_MIXED32)
+    out = {}
+    for dc in (40, 48):
+        c = m.Context([q.N], m.default_params(density_cache=dc))
+        d = device(q, m.GZ_MIXED32)
+        n, it = c.density(d)
+        assert c.status(reset=True)["ok"]
+        out[dc] = (d["h"].double().cpu().numpy(), n.double().cpu().numpy(), it.cpu().numpy())
+        c.close()
+    assert np.max(np.abs(out[40][0] / out[48][0] - 1.0)) < 1e-5
+    assert np.mean(out[40][2] == out[48][2]) > 0.99
+    with pytest.raises(m.GZError):
+        m.Context([q.N], m.default_params(density_cache=32))
 
 
 def test_measured_alu_pipes_are_ordered():
