@@ -202,3 +202,65 @@ def test_kh_64cubed_sharp_layer_rollout_is_deterministic():
     for k in g1:
         assert np.all(np.isfinite(g1[k]))
         assert np.array_equal(g1[k], g2[k]), k
+
+
+def test_kh_64cubed_sharp_layer_fp32_gradient():
+    """The workload as specified (sharp layer, 10 FP32 steps, loss = kinetic
+    energy of the particles starting at y > 0.75).
+    (1) The FP32 adjoint against the FP64 adjoint of the same sharp-layer
+        rollout (same steps).
+    (2) FP64 central differences.  The sharp layer's vx, rho and P are
+        exactly uniform in each region, so at the start every bulk particle
+        sits on a limiter kink (0/0 in alpha, tied extremes, degenerate clamp
+        bounds), where the step has one-sided derivatives only: along the
+        full gradient the limiter's choices change at every eps (about 3.6e5
+        of them at eps = 1e-8 as at 1e-5) and central differences differ from
+        the adjoint by 1.2e-4.  Along the gradient's vy part (vy is the one
+        smooth field; the uniform fields stay uniform at the start) the
+        step is smooth at the base point: the limiter's choices that change
+        (gz_checkpoint_limiters: limiting neighbour and extreme particle per
+        field, every step, at +eps and -eps against the base run) are kinks
+        the perturbed runs cross, their number falls with eps, and the
+        differences converge to the adjoint."""
+    m = gz()
+    q = I.kh(64)
+    q64 = cast_state(q, m.GZ_FP64)
+    ctx64, mask, dts, L64, g64 = kh_grad(m, m.GZ_FP64, q64, 10)
+    q32 = cast_state(q, m.GZ_MIXED32)
+    _, _, _, L32, g32 = kh_grad(m, m.GZ_MIXED32, q32, 10, dts)
+    errs = {k: float(np.linalg.norm(g32[k] - g64[k]) / np.linalg.norm(g64[k])) for k in g64}
+    print("kh sharp 64^3: FP32 vs FP64 adjoint", errs, "loss", L32, L64)
+    assert abs(L32 / L64 - 1.0) < 1e-4
+    assert max(errs.values()) < 2e-2
+    ck = ctx64.new_checkpoint(m.GZ_CKPT_GRADIENTS)
+
+    def run(delta, eps):
+        d = device(q64, m.GZ_FP64)
+        for k in delta:
+            d[k] = d[k] + eps * delta[k]
+        lims = []
+        for dt in dts:
+            ctx64.step(d, dt, None, ck, m.GZ_CKPT_GRADIENTS)
+            lims.append(ctx64.checkpoint_limiters(ck))
+        return float(region_ke(d, mask)), lims
+
+    def fd_rows(delta, epss):
+        L0, base = run(delta, 0.0)
+        assert abs(L0 / L64 - 1.0) < 1e-12
+        rows = []
+        for eps in epss:
+            Lp, lp = run(delta, eps)
+            Lm, lm = run(delta, -eps)
+            sw = sum(int((a != b).sum()) + int((c != b).sum()) for a, c, b in zip(lp, lm, base))
+            rows.append((eps, sw, (Lp - Lm) / (2 * eps)))
+        return rows
+
+    nvy = float(np.linalg.norm(g64["vy"]))
+    rows = fd_rows({"vy": torch.as_tensor(g64["vy"] / nvy).cuda()}, (1e-5, 1e-6, 1e-7))
+    rel = [(e, sw, abs(fd - nvy) / abs(fd)) for e, sw, fd in rows]
+    choices = 2 * 10 * q.N * len(dts)  # both perturbed runs, 10 per particle, every step
+    print("kh sharp 64^3 FD along the gradient's vy part (eps, limiter switches, rel to adjoint):",
+          rel, "adjoint", nvy, "choices", choices)
+    assert rel[0][1] > rel[1][1] > rel[2][1]   # crossings made by the perturbed runs
+    assert rel[2][1] < 1e-5 * choices
+    assert rel[2][2] < 1e-4, rel
