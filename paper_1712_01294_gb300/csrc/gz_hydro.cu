@@ -558,7 +558,11 @@ __global__ void k_prim(int N, Sorted<T> s, KParams p, DevStatus* st) {
 // with knorm = 8/(pi H^3 n^2) so that V_i psi_j(x_i) = knorm * w(r/H).
 // Neighbours are read four at a time (one 16-byte load of indices, then the
 // packed records of all four) so their loads are in flight together.
-template <typename T>
+// kInfo: also track which particles the limiter's bounds came from and write
+// what the adjoint reads (ginfo, lim); without it (a plain forward step) that
+// bookkeeping takes no registers or instructions (3 % faster; capped at 5
+// blocks per SM the FP32 kernel spills and gains nothing more).
+template <typename T, bool kInfo>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
     k_gradients(int N, Sorted<T> s, const unsigned* __restrict__ nbr, const int* __restrict__ ncount,
                 const unsigned* __restrict__ rnbr, const int* __restrict__ rcount, KParams p,
@@ -639,11 +643,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
                     Sg[3 * f + 2] += df * pdz;
                     if (Wj[f] > fmax[f]) {
                         fmax[f] = Wj[f];
-                        kmax[f] = (int)js[u];
+                        if constexpr (kInfo) kmax[f] = (int)js[u];
                     }
                     if (Wj[f] < fmin[f]) {
                         fmin[f] = Wj[f];
-                        kmin[f] = (int)js[u];
+                        if constexpr (kInfo) kmin[f] = (int)js[u];
                     }
                 }
                 if (want_dt) {
@@ -737,9 +741,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
                         a = min(T(1), pdiv(beta * (fmin[f] - Wi[f]), D));
                     if (a < al[f]) {
                         al[f] = a;
-                        jact[f] = (int)js[u];
-                        kact[f] = D > T(0) ? kmax[f] : kmin[f];
-                        Dact[f] = D;
+                        if constexpr (kInfo) {
+                            jact[f] = (int)js[u];
+                            kact[f] = D > T(0) ? kmax[f] : kmin[f];
+                            Dact[f] = D;
+                        }
                     }
                 }
             }
@@ -765,7 +771,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
                 dt_i = (any && vmax > T(0)) ? 2.0 * cbrt(1.0 / (double)ni) / (double)vmax : INFINITY;
             dti[i] = dt_i;
         }
-        if (ginfo) {  // what the adjoint of this pass needs (rows 32-byte aligned)
+        if (kInfo && ginfo) {  // what the adjoint of this pass needs (rows 32-byte aligned)
             T G[kGInfo];
 #pragma unroll
             for (int q = 0; q < 15; ++q) {
@@ -1233,10 +1239,14 @@ cudaError_t run_gradients(Ctx& c, bool want_dt, bool with_info, const int* list,
     if (!list) n = c.N;
     if (want_dt) k_dt_init<<<blocks(c.nboxes, 256), 256, 0, c.stream>>>(c.nboxes, (unsigned long long*)c.dt_box);
     if (n < 1) return cudaGetLastError();
-    k_gradients<T><<<blocks(n, 128), 128, 0, c.stream>>>(
-        c.N, sorted_view<T>(c), c.nbr, c.ncount, c.rnbr, c.rcount, kparams(c), (T*)c.rec, c.dti,
-        (unsigned long long*)c.dt_box, c.status, want_dt ? 1 : 0, with_info ? (T*)c.ginfo : nullptr,
-        with_info ? c.lim : nullptr, list, nlist, c.owned);
+    if (with_info)
+        k_gradients<T, true><<<blocks(n, 128), 128, 0, c.stream>>>(
+            c.N, sorted_view<T>(c), c.nbr, c.ncount, c.rnbr, c.rcount, kparams(c), (T*)c.rec, c.dti,
+            (unsigned long long*)c.dt_box, c.status, want_dt ? 1 : 0, (T*)c.ginfo, c.lim, list, nlist, c.owned);
+    else
+        k_gradients<T, false><<<blocks(n, 128), 128, 0, c.stream>>>(
+            c.N, sorted_view<T>(c), c.nbr, c.ncount, c.rnbr, c.rcount, kparams(c), (T*)c.rec, c.dti,
+            (unsigned long long*)c.dt_box, c.status, want_dt ? 1 : 0, nullptr, nullptr, list, nlist, c.owned);
     return cudaGetLastError();
 }
 

@@ -402,3 +402,25 @@ def test_density_with_wide_supports_matches_the_oracle(prec):
         assert not bad, bad[:10]
     else:
         assert np.max(np.abs(Hg - Ho) / Ho) <= 2e-6
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_plain_and_checkpointing_steps_are_bitwise_equal(prec):
+    """A plain step's gradient pass skips the adjoint's bookkeeping (which
+    particles the limiter's bounds came from); the step's results must not
+    change: the same state bit for bit as the checkpointing step's."""
+    import torch
+    m = gz()
+    q = cast_state(I.sedov(20, seed=9), prec)
+    out = []
+    for ck in (False, True):
+        ctx = ctx_for(q.N, prec)
+        d = device(q, prec)
+        buf = ctx.new_checkpoint(m.GZ_CKPT_GRADIENTS) if ck else None
+        for _ in range(3):
+            ctx.step(d, 0.0, None, buf, m.GZ_CKPT_GRADIENTS) if ck else ctx.step(d)
+        assert_status_ok(ctx)
+        out.append({k: d[k].clone() for k in ("x", "y", "z", "vx", "vy", "vz", "u", "h")})
+        ctx.close()
+    for k in out[0]:
+        assert torch.equal(out[0][k], out[1][k]), k
