@@ -197,6 +197,8 @@ def run_decomposed(a, world, rank, local):
             torch.cuda.synchronize()
         dist.barrier()
         ms = ev0.elapsed_time(ev1)
+        if box.ctx[rank] is not ctx:  # the subdomain outgrew its context during the timed steps
+            ctx, launches0 = box.ctx[rank], 0
         launches = ctx.info()["launches"] - launches0
         prof = ctx.profile_read(reset=True)
         st = ctx.status(reset=True)
@@ -621,8 +623,30 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p, fp64_peak=None):
             torch.cuda.synchronize()
             if r > 0:
                 msg += e0.elapsed_time(e1) / R
+        # the same 20 steps launched one kernel at a time, per-pass profile
+        # (what a graph saves; where the time goes)
+        for k in de:
+            de[k].copy_(d_init[k])
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(20):
+            ce.step(de, 0.0, dte)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_direct = e0.elapsed_time(e1)
+        for k in de:
+            de[k].copy_(d_init[k])
+        ce.profile_read(reset=True)
+        ce.profile(True)
+        for _ in range(20):
+            ce.step(de, 0.0, dte)
+        prof_e = ce.profile_read(reset=True)
+        ce.profile(False)
         ntot = sum(counts)
         out["ensemble"] = {"value": round(ntot * 20 / (msg / 1e3), 1), "unit": UNIT,
+                           "direct_launch_ms": round(ms_direct, 3),
+                           "pass_ms_per_step": {k: round(v[0] / max(v[1], 1), 4) for k, v in prof_e.items()
+                                                if v[1]},
                            "boxes": len(counts), "particles": ntot, "steps_per_graph": 20,
                            "ms_per_graph": round(msg, 3), "graph_replays": R,
                            "kernels_per_graph": (ce.info()["launches"] - l1) // R,

@@ -130,7 +130,7 @@ class DistComm:
         table = [torch.zeros(self.size, dtype=torch.int64, device=wdev) for _ in range(self.size)]
         dist.all_gather(table, counts.to(wdev))
         table = [t.cpu() for t in table]
-        reqs, recv = [], {}
+        ops, recv = [], {}
         for src in range(self.size):
             n = int(table[src][self.rank])
             if src == self.rank or n == 0:
@@ -138,19 +138,16 @@ class DistComm:
             fb = torch.empty((len(FLOATS), n), dtype=fdtype, device=wdev)
             ib = torch.empty(n, dtype=torch.int64, device=wdev)
             recv[src] = (fb, ib)
-            reqs.append(dist.irecv(fb, src))
-            reqs.append(dist.irecv(ib, src))
-        keep = []
+            ops += [dist.P2POp(dist.irecv, fb, src), dist.P2POp(dist.irecv, ib, src)]
         for dst, parts in mine.items():
             if dst == self.rank or parts["id"].numel() == 0:
                 continue
             fb = self._wire(torch.stack([parts[k] for k in FLOATS]).contiguous())
             ib = self._wire(parts["id"].contiguous())
-            keep += [fb, ib]
-            reqs.append(dist.isend(fb, dst))
-            reqs.append(dist.isend(ib, dst))
-        for r in reqs:
-            r.wait()
+            ops += [dist.P2POp(dist.isend, fb, dst), dist.P2POp(dist.isend, ib, dst)]
+        if ops:  # one group of point-to-point operations (NCCL runs them together)
+            for r in dist.batch_isend_irecv(ops):
+                r.wait()
         inbox = {}
         for src, (fb, ib) in recv.items():
             fb, ib = fb.to(dev), ib.to(dev)
