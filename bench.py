@@ -50,7 +50,7 @@ FLOPS_PER_GRAD_PARTICLE = 60    # gradient pass, per particle
 # summarised in TRAFFIC_SOURCE (64^3 turbulence, one launch each), scaled to a
 # launch by the work units of the run; to be emptied whenever one of these
 # kernels changes after that capture
-TRAFFIC_PER_UNIT = {"density": 1.06, "gradients": 8.78, "fluxes": 23.0}
+TRAFFIC_PER_UNIT = {"density": 1.08, "gradients": 8.73, "fluxes": 22.9}
 TRAFFIC_SOURCE = "profiles/kernels_turb64_fp32.md (64^3 capture, scaled by work units)"
 FP32_LANES = 128  # FP32 lanes per SM (Blackwell)
 
@@ -623,6 +623,7 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p, fp64_peak=None):
             torch.cuda.synchronize()
             if r > 0:
                 msg += e0.elapsed_time(e1) / R
+        per_graph = (ce.info()["launches"] - l1) // R
         # the same 20 steps launched one kernel at a time, per-pass profile
         # (what a graph saves; where the time goes)
         for k in de:
@@ -649,7 +650,7 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p, fp64_peak=None):
                                                 if v[1]},
                            "boxes": len(counts), "particles": ntot, "steps_per_graph": 20,
                            "ms_per_graph": round(msg, 3), "graph_replays": R,
-                           "kernels_per_graph": (ce.info()["launches"] - l1) // R,
+                           "kernels_per_graph": per_graph,
                            "cell_factor": cf, "density_cache": dc,
                            "tuning_ms_per_step": {f"{k[0]},{k[1]}": round(v, 3) for k, v in tune_ms.items()},
                            "what": "each replay: the 20 steps of the configuration from the initial state",
