@@ -113,16 +113,25 @@ __global__ void k_rs_scatter(const unsigned* __restrict__ kin, const unsigned* _
                              int N, int shift, const unsigned* __restrict__ hist, int nblk,
                              const unsigned* __restrict__ totals, unsigned* __restrict__ kout,
                              unsigned* __restrict__ vout) {
+    static_assert(kSortThreads == 256, "one thread per digit");
     __shared__ unsigned cnt[kSortWarps][256];
     __shared__ unsigned dbase[256];
+    __shared__ unsigned wsum[kSortWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int t = threadIdx.x; t < kSortWarps * 256; t += blockDim.x) (&cnt[0][0])[t] = 0;
-    if (threadIdx.x == 0) {  // exclusive scan of the 256 digit totals
-        unsigned acc = 0;
-        for (int d = 0; d < 256; ++d) {
-            dbase[d] = acc;
-            acc += totals[d];
+    {  // exclusive scan of the 256 digit totals, one digit per thread
+        const unsigned tv = totals[threadIdx.x];
+        unsigned incl = tv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
         }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        unsigned before = 0;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        dbase[threadIdx.x] = before + incl - tv;
     }
     __syncthreads();
     const int wbase = blockIdx.x * kSortTile + warp * kSortPerWarp;
