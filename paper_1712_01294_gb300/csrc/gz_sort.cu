@@ -1,6 +1,8 @@
 // Binning, device LSD radix sort and permutation (step S1: particles are
 // Morton-sorted into a uniform cell grid per box; cell ranges are derived
 // from the sorted keys).
+#include <algorithm>
+
 #include "gz_launch.cuh"
 
 namespace gz {
@@ -9,6 +11,8 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kMaxDigitBits = 9;  // digits of up to 9 bits: 512 buckets a pass
+constexpr int kMaxDigits = 1 << kMaxDigitBits;
 constexpr int kSortTile = 4096;
 constexpr int kSortPerWarp = kSortTile / kSortWarps;
 
@@ -57,18 +61,19 @@ __global__ void k_keys(int N, const T* __restrict__ x, const T* __restrict__ y,
     vals[i] = (unsigned)i;
 }
 
-__global__ void k_rs_hist(const unsigned* __restrict__ keys, int N, int shift,
+// Digit counts of one tile (nd = 2^bits digits, mask = nd - 1).
+__global__ void k_rs_hist(const unsigned* __restrict__ keys, int N, int shift, unsigned mask, int nd,
                           unsigned* __restrict__ hist, int nblk) {
-    __shared__ unsigned h[256];
-    for (int t = threadIdx.x; t < 256; t += blockDim.x) h[t] = 0;
+    __shared__ unsigned h[kMaxDigits];
+    for (int t = threadIdx.x; t < nd; t += blockDim.x) h[t] = 0;
     __syncthreads();
     const int base = blockIdx.x * kSortTile;
     for (int k = threadIdx.x; k < kSortTile; k += blockDim.x) {
         int e = base + k;
-        if (e < N) atomicAdd(&h[(keys[e] >> shift) & 255u], 1u);
+        if (e < N) atomicAdd(&h[(keys[e] >> shift) & mask], 1u);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < 256; t += blockDim.x) hist[t * nblk + blockIdx.x] = h[t];
+    for (int t = threadIdx.x; t < nd; t += blockDim.x) hist[t * nblk + blockIdx.x] = h[t];
 }
 
 // Exclusive scan of one digit's row hist[d][0..nblk) (block d), and the row
@@ -110,17 +115,19 @@ __global__ void k_rs_rows(unsigned* __restrict__ hist, int nblk, unsigned* __res
 // Stable scatter: each warp owns a contiguous sub-tile and walks it in order;
 // lanes with equal digits are ranked with __match_any_sync.
 __global__ void k_rs_scatter(const unsigned* __restrict__ kin, const unsigned* __restrict__ vin,
-                             int N, int shift, const unsigned* __restrict__ hist, int nblk,
-                             const unsigned* __restrict__ totals, unsigned* __restrict__ kout,
+                             int N, int shift, unsigned mask, int nd, const unsigned* __restrict__ hist,
+                             int nblk, const unsigned* __restrict__ totals, unsigned* __restrict__ kout,
                              unsigned* __restrict__ vout) {
-    static_assert(kSortThreads == 256, "one thread per digit");
-    __shared__ unsigned cnt[kSortWarps][256];
-    __shared__ unsigned dbase[256];
+    static_assert(kMaxDigits == 2 * kSortThreads, "two digits per thread");
+    __shared__ unsigned cnt[kSortWarps][kMaxDigits];
+    __shared__ unsigned dbase[kMaxDigits];
     __shared__ unsigned wsum[kSortWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int t = threadIdx.x; t < kSortWarps * 256; t += blockDim.x) (&cnt[0][0])[t] = 0;
-    {  // exclusive scan of the 256 digit totals, one digit per thread
-        const unsigned tv = totals[threadIdx.x];
+    for (int t = threadIdx.x; t < kSortWarps * kMaxDigits; t += blockDim.x) (&cnt[0][0])[t] = 0;
+    {  // exclusive scan of the nd digit totals, two digits per thread
+        const int d0 = 2 * threadIdx.x;
+        const unsigned v0 = d0 < nd ? totals[d0] : 0u, v1 = d0 + 1 < nd ? totals[d0 + 1] : 0u;
+        const unsigned tv = v0 + v1;
         unsigned incl = tv;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -131,16 +138,17 @@ __global__ void k_rs_scatter(const unsigned* __restrict__ kin, const unsigned* _
         __syncthreads();
         unsigned before = 0;
         for (int w = 0; w < warp; ++w) before += wsum[w];
-        dbase[threadIdx.x] = before + incl - tv;
+        dbase[d0] = before + incl - tv;
+        dbase[d0 + 1] = before + incl - tv + v0;
     }
     __syncthreads();
     const int wbase = blockIdx.x * kSortTile + warp * kSortPerWarp;
     for (int c = 0; c < kSortPerWarp; c += 32) {
         int e = wbase + c + lane;
-        if (e < N) atomicAdd(&cnt[warp][(kin[e] >> shift) & 255u], 1u);
+        if (e < N) atomicAdd(&cnt[warp][(kin[e] >> shift) & mask], 1u);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
         unsigned run = dbase[d] + hist[d * nblk + blockIdx.x];
         for (int w = 0; w < kSortWarps; ++w) {
             unsigned v = cnt[w][d];
@@ -157,7 +165,7 @@ __global__ void k_rs_scatter(const unsigned* __restrict__ kin, const unsigned* _
         unsigned peers = 0, d = 0;
         if (valid) {
             const unsigned k = kin[e];
-            d = (k >> shift) & 255u;
+            d = (k >> shift) & mask;
             peers = __match_any_sync(vmask, d);
             const unsigned pos = cnt[warp][d] + __popc(peers & lt);
             kout[pos] = k;
@@ -254,13 +262,19 @@ cudaError_t sort_and_bin(Ctx& c, const gz_particles& p, const void* n_in) {
                                                c.status);
     const int nblk = blocks(N, kSortTile);
     const int total_bits = 3 * c.cbits + c.box_bits;
-    c.launches += 2 + 3 * ((total_bits + 7) / 8);
+    // the fewest passes of at most kMaxDigitBits bits, the bits spread evenly
+    const int npass = (total_bits + kMaxDigitBits - 1) / kMaxDigitBits;
+    const int bits = npass ? (total_bits + npass - 1) / npass : 0;
+    c.launches += 2 + 3 * npass;
     unsigned *ki = c.keys, *vi = c.vals, *ko = c.keys_alt, *vo = c.vals_alt;
-    for (int shift = 0; shift < total_bits; shift += 8) {
-        unsigned* totals = c.hist + 256 * (size_t)nblk;
-        k_rs_hist<<<nblk, kSortThreads, 0, st>>>(ki, N, shift, c.hist, nblk);
-        k_rs_rows<<<256, kSortThreads, 0, st>>>(c.hist, nblk, totals);
-        k_rs_scatter<<<nblk, kSortThreads, 0, st>>>(ki, vi, N, shift, c.hist, nblk, totals, ko, vo);
+    for (int shift = 0; shift < total_bits; shift += bits) {
+        const int pb = std::min(bits, total_bits - shift);
+        const int nd = 1 << pb;
+        const unsigned mask = (unsigned)nd - 1u;
+        unsigned* totals = c.hist + (size_t)nd * nblk;
+        k_rs_hist<<<nblk, kSortThreads, 0, st>>>(ki, N, shift, mask, nd, c.hist, nblk);
+        k_rs_rows<<<nd, kSortThreads, 0, st>>>(c.hist, nblk, totals);
+        k_rs_scatter<<<nblk, kSortThreads, 0, st>>>(ki, vi, N, shift, mask, nd, c.hist, nblk, totals, ko, vo);
         unsigned* t = ki;
         ki = ko;
         ko = t;
