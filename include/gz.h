@@ -257,7 +257,11 @@ gz_status gz_step_finish(gz_ctx* ctx, gz_particles* p, const double* dt_dev);
  * halo deep enough that every particle the owned particles' density,
  * gradient and flux passes read sees its full neighbourhood, the owned
  * particles' step equals the undivided box's bit for bit (the u floor
- * excepted: a subdomain's median is its own).  Errors: GZ_E_INVAL (not a
+ * excepted: a subdomain's median is its own).  A subdomain context takes
+ * gz_step, gz_step_begin / gz_step_finish and the single passes; the calls
+ * whose buffers or captured launches are laid out for one particle count
+ * (gz_checkpoint_bytes, gz_step_checkpoint, gz_step_backward, gz_step_hier,
+ * gz_graph_capture) refuse it with GZ_E_INVAL.  Errors: GZ_E_INVAL (not a
  * subdomain context, sizes out of range), GZ_E_NOMEM, GZ_E_CUDA. */
 gz_status gz_create_subdomain(const gz_params* params, int64_t capacity, int64_t grid_count,
                               void* cuda_stream, gz_ctx** out);

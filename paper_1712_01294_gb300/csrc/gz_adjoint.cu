@@ -894,7 +894,7 @@ template cudaError_t run_step_adjoint<double>(Ctx&, const gz_particles&, gz_part
 
 cudaError_t ensure_adjoint_scratch(Ctx& c) {
     if (c.adj) return cudaSuccess;
-    const size_t Nz = (size_t)c.N;
+    const size_t Nz = (size_t)c.capacity;  // (a subdomain context's N changes)
     const size_t tsz = c.precision == GZ_FP64 ? 8 : 4;
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };  // 256-byte aligned slices
     const size_t sz[6] = {up(sizeof(double) * Nz * kAdj), up(sizeof(double) * Nz * 4), up(tsz * Nz * kSeed),

@@ -587,6 +587,13 @@ gz_status gz_create(const gz_params* params, int32_t nboxes, const int64_t* coun
     return create_ctx(params, nboxes, counts, nullptr, cuda_stream, out);
 }
 
+// Calls whose buffers or captured launches are laid out for one particle
+// count (checkpoints, CUDA graphs, the hierarchical step's bins) refuse a
+// subdomain context, whose count changes with every gz_set_subdomain.
+static gz_status refuse_subdomain(gz_ctx* ctx, const char* what) {
+    return fail(ctx, GZ_E_INVAL, std::string(what) + ": not taken on a subdomain context");
+}
+
 gz_status gz_create_subdomain(const gz_params* params, int64_t capacity, int64_t grid_count,
                               void* cuda_stream, gz_ctx** out) {
     if (!out || capacity < 1 || grid_count < 1) return GZ_E_INVAL;
@@ -729,6 +736,7 @@ gz_status gz_step_hier(gz_ctx* ctx, gz_particles* p, int32_t K, double dt_fixed,
     if (gz_status s = check_particles(ctx, p, true)) return s;
     if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
     if (K < 0 || K > 20) return fail(ctx, GZ_E_INVAL, "K must be in [0, 20]");
+    if (ctx->c.owned) return refuse_subdomain(ctx, "gz_step_hier");
     Ctx& c = ctx->c;
     const PassTimer timer{&c};
     long long act = 0;
@@ -742,6 +750,7 @@ gz_status gz_step_hier(gz_ctx* ctx, gz_particles* p, int32_t K, double dt_fixed,
 
 gz_status gz_checkpoint_bytes(gz_ctx* ctx, int32_t level, int64_t* bytes) {
     if (!ctx || !bytes || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS) return GZ_E_INVAL;
+    if (ctx->c.owned) return refuse_subdomain(ctx, "gz_checkpoint_bytes");
     *bytes = (int64_t)ckpt_bytes(ctx->c, level);
     return GZ_OK;
 }
@@ -755,6 +764,7 @@ gz_status gz_step_checkpoint(gz_ctx* ctx, gz_particles* p, double dt_fixed, doub
         return fail(ctx, GZ_E_INVAL, "checkpoint: need a 256-byte aligned buffer and a valid level");
     if (!adjoint_covers(ctx->c.params))
         return fail(ctx, GZ_E_INVAL, "the adjoint covers GZ_MFM with GZ_RIEMANN_HLLC only");
+    if (ctx->c.owned) return refuse_subdomain(ctx, "gz_step_checkpoint");
     const Ckpt ck = ckpt_view(ctx->c, ckpt, level);
     return GZ_DISPATCH(do_step<float>(ctx, p, dt_fixed, dt_used_dev, ck),
                        do_step<double>(ctx, p, dt_fixed, dt_used_dev, ck));
@@ -766,6 +776,7 @@ gz_status gz_graph_capture(gz_ctx* ctx, gz_particles* p, int32_t nsteps, double 
     if (gz_status s = check_particles(ctx, p, true)) return s;
     Ctx& c = ctx->c;
     if (!c.stream) return fail(ctx, GZ_E_INVAL, "graph capture needs a created (non-default) stream");
+    if (c.owned) return refuse_subdomain(ctx, "gz_graph_capture");
     if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
     if (c.graph_exec) cudaGraphExecDestroy(c.graph_exec);
     if (c.graph) cudaGraphDestroy(c.graph);
@@ -820,6 +831,7 @@ gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt, 
         return fail(ctx, GZ_E_INVAL, "the adjoint covers GZ_MFM with GZ_RIEMANN_HLLC only");
     if (ckpt && (((uintptr_t)ckpt & 255) || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS))
         return fail(ctx, GZ_E_INVAL, "checkpoint: need a 256-byte aligned buffer and a valid level");
+    if (ctx->c.owned) return refuse_subdomain(ctx, "gz_step_backward");
     const Ckpt ck = ckpt_view(ctx->c, const_cast<void*>(ckpt), level);
     return GZ_DISPATCH(do_step_backward<float>(ctx, p_start, dt, ck, gbar_end, gbar_start),
                        do_step_backward<double>(ctx, p_start, dt, ck, gbar_end, gbar_start));

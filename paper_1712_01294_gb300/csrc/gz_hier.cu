@@ -584,8 +584,9 @@ void launch_exchange(Ctx& c, const KParams& kp, int N) {
 
 cudaError_t ensure_hier_scratch(Ctx& c) {
     if (c.hier_arena) return cudaSuccess;
-    const size_t Nz = (size_t)c.N, sz = c.precision == GZ_FP64 ? 8 : 4;
-    const size_t nb = (size_t)nblk(c.N, kCmpBlock);
+    // sized for the context's capacity (a subdomain context's N changes)
+    const size_t Nz = (size_t)c.capacity, sz = c.precision == GZ_FP64 ? 8 : 4;
+    const size_t nb = (size_t)nblk(c.capacity, kCmpBlock);
     struct Item {
         void** ptr;
         size_t bytes;

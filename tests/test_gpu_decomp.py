@@ -5,7 +5,8 @@ Owned particles must end bitwise where the undivided box's gz_step puts
 them, in FP64 and FP32, over several steps with migration between slabs
 (the Sod split at x = 1/2 lies on a slab boundary).  The split step
 (gz_step_begin + gz_step_finish) must equal gz_step bitwise, and the
-subdomain calls must refuse what they do not take."""
+subdomain calls must refuse what they do not take (and a subdomain context the
+calls laid out for one particle count)."""
 import numpy as np
 import pytest
 
@@ -95,4 +96,17 @@ def test_subdomain_calls_refuse_bad_use():
     with pytest.raises(m.GZError):
         sub.set_subdomain(q.N, q.N + 1)  # more owned than held
     sub.set_subdomain(q.N, q.N)
+    d = device(q, 1)
+    # calls laid out for one particle count refuse a subdomain context
+    with pytest.raises(m.GZError):
+        sub.checkpoint_bytes(1)
+    with pytest.raises(m.GZError):
+        sub.step_hier(d, 1)
+    stream = torch.cuda.Stream()
+    sub2 = m.Context([q.N], m.default_params(), stream=stream, grid_count=q.N)
+    with pytest.raises(m.GZError):
+        sub2.graph_capture(d, 1)
+    sub2.close()
+    sub.step(d)  # the plain step is taken
+    assert sub.status(reset=True)["ok"]
     sub.close()
