@@ -48,9 +48,11 @@
  *   - Boxes: a context holds nboxes independent periodic unit boxes; box b's
  *     particles are the contiguous slice [sum_{c<b} counts[c], ...).  Every
  *     box has its own cell grid and its own CFL timestep.
- *   - Ids must be unique non-negative int64 (within each box); every pair
- *     quantity is evaluated in the order (lower id, higher id), so both
- *     particles of a pair receive bitwise-opposite rate contributions.
+ *   - Ids must be unique non-negative int64 (within each box).  Every pair
+ *     quantity is evaluated in one fixed order of the pair, so both
+ *     particles of a pair receive bitwise-opposite rate contributions: the
+ *     lower sorted position first in the MFM flux passes, the lower id first
+ *     under GZ_MFV and in the adjoint.
  */
 #ifndef GZ_H
 #define GZ_H

@@ -333,6 +333,20 @@ __device__ __forceinline__ bool exact_star(T rL, T uL, T PL, T rR, T uR, T PR, T
     return true;
 }
 
+// Orientation of a pair (sorted indices i, j; ids idi = id of i, sid[]) in
+// the forward flux passes: whether i is L.  MFM: the lower sorted index,
+// which both particles of the pair know, so no id is gathered.  MFV: the
+// lower id.  Either is a fixed order of the pair, so its two particles
+// compute the same canonical flux and get bitwise-opposite contributions
+// (the adjoint orients by id: its tie rule at the clamp names L).
+template <bool kById>
+__device__ __forceinline__ bool pair_order(int i, int j, long long idi, const long long* __restrict__ sid) {
+    if constexpr (kById)
+        return idi < sid[j];
+    else
+        return i < j;
+}
+
 // Contribution of the pair (a, b) to particle a's rates: dp (3), dE and,
 // under MFV (O15), dm.  kRiem: the MFM face's star from HLLC (0), the exact
 // solver (1), or HLLC with the exact star where HLLC's P* < 0 (2).  Returns
@@ -385,7 +399,7 @@ __device__ __forceinline__ bool pair_rates(const T (&a)[kRecord], const T (&b)[k
         }
         fl |= 1;
     }
-    // canonical order: L = lower id
+    // canonical order: L = a when aL (pair_order)
     T FL[5], FR[5];
 #pragma unroll
     for (int f = 0; f < 5; ++f) {

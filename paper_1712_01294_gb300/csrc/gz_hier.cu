@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kXBlock)
     const int i = tlist[t];
     T a[kRecord];
     load_rec(rec + (size_t)i * kRecord, a);
-    const long long idi = sid[i];
+    const long long idi = kMFV ? sid[i] : 0;  // (MFV pairs are oriented by id)
     const int ka = sbin[i];
     const double Db = D[sbox[i]];
     const T gam = (T)p.gamma;
@@ -447,8 +447,8 @@ __global__ void __launch_bounds__(kXBlock)
             hancock_inc(a, hdt, gam, hancock, inca);
             T dp[3], dE, dm;
             int fl = 0;
-            if (pair_rates<T, kMFV, kRiem>(a, b, idi < sid[j], hdt, gam, hancock, inca, dp, dE,
-                                                      dm, fl)) {
+            const bool aL = pair_order<kMFV>(i, j, idi, sid);
+            if (pair_rates<T, kMFV, kRiem>(a, b, aL, hdt, gam, hancock, inca, dp, dE, dm, fl)) {
                 const T sc = (T)ldexp(1.0, ka - kab);
                 part[0] += dp[0] * sc;
                 part[1] += dp[1] * sc;

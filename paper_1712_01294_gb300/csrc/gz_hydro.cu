@@ -900,7 +900,7 @@ __global__ void __launch_bounds__(kFluxBlock)
     if (i >= N) return;
     T a[kRecord];
     load_rec(rec + (size_t)i * kRecord, a);
-    const long long idi = sid[i];
+    const long long idi = kMFV ? sid[i] : 0;  // (MFV pairs are oriented by id)
     const T hdt = (T)(0.5 * dt_use[sbox[i]]);
     const T gam = (T)p.gamma;
     const bool hancock = p.hancock != 0;
@@ -929,7 +929,8 @@ __global__ void __launch_bounds__(kFluxBlock)
                 load_rec(rec + (size_t)j * kRecord, b);
                 T dp[3], dE, dm;
                 int fl = 0;
-                if (pair_rates<T, kMFV, kRiem>(a, b, idi < sid[j], hdt, gam, hancock, inca, dp, dE, dm, fl)) {
+                if (pair_rates<T, kMFV, kRiem>(a, b, pair_order<kMFV>(i, j, idi, sid), hdt, gam, hancock, inca,
+                                               dp, dE, dm, fl)) {
                     part[0] += dp[0];
                     part[1] += dp[1];
                     part[2] += dp[2];
