@@ -358,10 +358,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 1)
 #pragma unroll
     for (int q = 0; q < kAdj; ++q) acc[q] = T(0);
     for (int list = 0; list < 2; ++list) {
-        const unsigned* L = list == 0 ? nbr + (size_t)i * p.cap : rnbr + (size_t)i * p.rcap;
+        const unsigned* L = list == 0 ? nbr + 4 * (size_t)i : rnbr + 4 * (size_t)i;
         const int cnt = list == 0 ? min(ncount[i], p.cap) : min(rcount[i], p.rcap);
         for (int k = 0; k < cnt; ++k) {
-            const int j = (int)L[k];
+            const int j = (int)L[lcol(k, N)];
             T b[kRecord];
             load_rec(rec + (size_t)j * kRecord, b);
             T wj[4];
@@ -575,9 +575,9 @@ __global__ void __launch_bounds__(128)
     lbloom[i] = bloom;
     T normb = T(0.0);
     const int cnt = min(ncount[i], p.cap);
-    const unsigned* L = nbr + (size_t)i * p.cap;
+    const unsigned* L = nbr + 4 * (size_t)i;
     for (int k0 = 0; k0 < cnt; k0 += 4) {  // four neighbours' loads in flight at a time
-      const uint4 jj = *reinterpret_cast<const uint4*>(L + k0);
+      const uint4 jj = col4(L, k0, N);
       const unsigned js[4] = {jj.x, jj.y, jj.z, jj.w};
       P4<T> qv[4], pv[4];
       T Pv[4];
@@ -662,10 +662,10 @@ __global__ void __launch_bounds__(128)
     const unsigned long long jbit = 1ull << (j & 63);
     T fb[5] = {0, 0, 0, 0, 0}, xb[3] = {0, 0, 0}, Hb = T(0.0);
     for (int list = 0; list < 2; ++list) {
-        const unsigned* Lj = list == 0 ? nbr + (size_t)j * p.cap : rnbr + (size_t)j * p.rcap;
+        const unsigned* Lj = list == 0 ? nbr + 4 * (size_t)j : rnbr + 4 * (size_t)j;
         const int cnt = list == 0 ? min(ncount[j], p.cap) : min(rcount[j], p.rcap);
         for (int k0 = 0; k0 < cnt; k0 += 4) {  // four candidates' loads in flight at a time
-          const uint4 ii = *reinterpret_cast<const uint4*>(Lj + k0);
+          const uint4 ii = col4(Lj, k0, N);
           const unsigned is[4] = {ii.x, ii.y, ii.z, ii.w};
           P4<T> mv[4];
 #pragma unroll
@@ -767,7 +767,7 @@ __global__ void __launch_bounds__(128)
     const T xim1 = xi - T(1), yim1 = yi - T(1), zim1 = zi - T(1);
     const T iH = T(1) / Hi;
     const int cnt = min(ncount[i], p.cap);
-    const unsigned* L = nbr + (size_t)i * p.cap;
+    const unsigned* L = nbr + 4 * (size_t)i;
     // sum over N_i of w'(q) q: the density pass kept its negative (same
     // terms, same order), so no loop over N_i is needed for it here
     const T dsum = -s.sd[i];
@@ -781,7 +781,7 @@ __global__ void __launch_bounds__(128)
     kap[i] = kappa;
     T xb[3] = {0, 0, 0};
     for (int k0 = 0; k0 < cnt; k0 += 4) {  // four neighbours' loads in flight at a time
-        const uint4 jj = *reinterpret_cast<const uint4*>(L + k0);
+        const uint4 jj = col4(L, k0, N);
         const unsigned js[4] = {jj.x, jj.y, jj.z, jj.w};
         P4<T> qv[4];
 #pragma unroll
@@ -815,10 +815,10 @@ __global__ void __launch_bounds__(128)
     const P4<T> mj = s.pos[j];
     T xb[3] = {0, 0, 0};
     for (int list = 0; list < 2; ++list) {
-        const unsigned* Lj = list == 0 ? nbr + (size_t)j * p.cap : rnbr + (size_t)j * p.rcap;
+        const unsigned* Lj = list == 0 ? nbr + 4 * (size_t)j : rnbr + 4 * (size_t)j;
         const int cnt = list == 0 ? min(ncount[j], p.cap) : min(rcount[j], p.rcap);
         for (int k0 = 0; k0 < cnt; k0 += 4) {  // four candidates' loads in flight at a time
-            const uint4 ii = *reinterpret_cast<const uint4*>(Lj + k0);
+            const uint4 ii = col4(Lj, k0, N);
             const unsigned is[4] = {ii.x, ii.y, ii.z, ii.w};
             P4<T> mv[4];
 #pragma unroll

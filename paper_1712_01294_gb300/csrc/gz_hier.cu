@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(128)
                 if (!(r2 < Hi * Hi)) {
                     const int slot = atomicAdd(&rcount[i], 1);
                     if (slot < p.rcap)
-                        rnbr[(size_t)i * p.rcap + slot] = (unsigned)j;
+                        rnbr[lslot(slot, i, N)] = (unsigned)j;
                     else
                         set_status(st, GZ_S_NBR_OVERFLOW, GZ_C_NBR_OVERFLOW, s.id[i]);
                 }
@@ -266,19 +266,19 @@ __global__ void k_h_inlist(const int* __restrict__ alist, const int* __restrict_
                            const unsigned char* __restrict__ aflag, unsigned* __restrict__ nbr,
                            int* __restrict__ ncount, const unsigned* __restrict__ rnbr,
                            const int* __restrict__ rcount, int cap, int rcap,
-                           const long long* __restrict__ sid, DevStatus* st) {
+                           const long long* __restrict__ sid, int N, DevStatus* st) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= *nA) return;
     const int i = alist[t];
     for (int list = 0; list < 2; ++list) {
-        const unsigned* L = list == 0 ? nbr + (size_t)i * cap : rnbr + (size_t)i * rcap;
+        const unsigned* L = list == 0 ? nbr + 4 * (size_t)i : rnbr + 4 * (size_t)i;
         const int n = list == 0 ? min(ncount[i], cap) : min(rcount[i], rcap);
         for (int k = 0; k < n; ++k) {
-            const int j = (int)L[k];
+            const int j = (int)L[lcol(k, N)];
             if (aflag[j]) continue;
             const int slot = atomicAdd(&ncount[j], 1);
             if (slot < cap)
-                nbr[(size_t)j * cap + slot] = (unsigned)i;
+                nbr[lslot(slot, j, N)] = (unsigned)i;
             else
                 set_status(st, GZ_S_NBR_OVERFLOW, GZ_C_NBR_OVERFLOW, sid[j]);
         }
@@ -295,21 +295,21 @@ __global__ void k_h_sort(int N, const unsigned char* __restrict__ aflag, int* __
     unsigned* L;
     int n;
     if (aflag[i]) {
-        L = rnbr + (size_t)i * rcap;
+        L = rnbr + 4 * (size_t)i;
         n = min(rcount[i], rcap);
     } else {
         n = min(ncount[i], cap);
         ncount[i] = n;
-        L = nbr + (size_t)i * cap;
+        L = nbr + 4 * (size_t)i;
     }
     for (int a = 1; a < n; ++a) {
-        const unsigned v = L[a];
+        const unsigned v = L[lcol(a, N)];
         int b = a - 1;
-        while (b >= 0 && L[b] > v) {
-            L[b + 1] = L[b];
+        while (b >= 0 && L[lcol(b, N)] > v) {
+            L[lcol(b + 1, N)] = L[lcol(b, N)];
             --b;
         }
-        L[b + 1] = v;
+        L[lcol(b + 1, N)] = v;
     }
 }
 
@@ -435,10 +435,10 @@ __global__ void __launch_bounds__(kXBlock)
     int np = 0, nfall = 0, nneg = 0;
 #pragma unroll 1
     for (int list = 0; list < 2; ++list) {
-        const unsigned* L = list == 0 ? nbr + (size_t)i * p.cap : rnbr + (size_t)i * p.rcap;
+        const unsigned* L = list == 0 ? nbr + 4 * (size_t)i : rnbr + 4 * (size_t)i;
         const int cnt = list == 0 ? min(ncount[i], p.cap) : min(rcount[i], p.rcap);
         for (int k = 0; k < cnt; ++k) {
-            const int j = (int)L[k];
+            const int j = (int)L[lcol(k, N)];
             T b[kRecord];
             load_rec(rec + (size_t)j * kRecord, b);
             const int kab = max(ka, sbin[j]);
@@ -683,7 +683,7 @@ cudaError_t run_step_hier(Ctx& c, gz_particles& p, int K, double dt_fixed, doubl
             k_h_rscatter<T><<<nblk(N, 128), 128, 0, st>>>(N, sv, g, kp, c.aflag, c.cellact, c.cellnear, c.rnbr,
                                                            c.rcount, c.status);
             k_h_inlist<<<nblk(nA, 128), 128, 0, st>>>(c.alist, c.hcount + 1, c.aflag, c.nbr, c.ncount, c.rnbr,
-                                                       c.rcount, c.cap, c.rcap, c.sid, c.status);
+                                                       c.rcount, c.cap, c.rcap, c.sid, c.N, c.status);
             k_h_sort<<<nblk(N, 128), 128, 0, st>>>(N, c.aflag, c.ncount, c.nbr, c.cap, c.rcount, c.rnbr,
                                                     c.rcap);
             k_h_tflags<<<nblk(N, 256), 256, 0, st>>>(N, c.aflag, c.ncount, c.tflag);

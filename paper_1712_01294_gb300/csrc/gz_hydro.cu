@@ -1,8 +1,9 @@
 // Hydro passes of the MFM step in sorted particle order (steps S2-S6).
-// One thread per particle; neighbour lists are slot-major ([slot][N]) so a
-// warp's accesses to slot k are coalesced.  Every pair quantity that mixes
-// both particles of a pair is either symmetric in its operands or evaluated
-// after ordering the pair by id, so both particles get bitwise-opposite
+// One thread per particle; neighbour lists are stored in groups of four
+// slots across the particles (lslot), so a warp reads one group of its lists
+// as contiguous bytes.  Every pair quantity that mixes both particles of a
+// pair is either symmetric in its operands or evaluated in one fixed order of
+// the pair (pair_order), so both particles get bitwise-opposite
 // contributions (no atomics on rates).
 #include <algorithm>
 #include <type_traits>
@@ -65,8 +66,8 @@ __device__ __noinline__ int dens_fill(const Grid& g, const BoxInfo& bx, const P4
 // holds and no deferral): the sums and the neighbour list of Ht.
 template <typename T>
 __device__ __noinline__ void dens_eval_cells(const Grid& g, const BoxInfo& bx, const P4<T>* __restrict__ pos,
-                                             int i, T xi, T yi, T zi, T Ht, unsigned* __restrict__ row, int cap,
-                                             Acc<T>& sw, T& sd, int& c) {
+                                             int i, T xi, T yi, T zi, T Ht, unsigned* __restrict__ col, int cap,
+                                             int N, Acc<T>& sw, T& sd, int& c) {
     const T H2 = Ht * Ht;
     const T iH = T(1) / Ht;
     for_candidates<T>(g, bx, pos, i, xi, yi, zi, Ht, [&](int j, T, T, T, T r2) {
@@ -76,7 +77,7 @@ __device__ __noinline__ void dens_eval_cells(const Grid& g, const BoxInfo& bx, c
             dens_terms(q, w, qdw);
             sw.add(w);
             sd += qdw;
-            if (c < cap) row[c] = (unsigned)j;
+            if (c < cap) col[lcol(c, N)] = (unsigned)j;
             ++c;
         }
     });
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(kDensBlock, sizeof(T) == 4 ? 10 : 1)
                 }
             }
         } else {
-            dens_eval_cells<T>(g, bx, s.pos, i, xi, yi, zi, Ht, nbr + (size_t)i * p.cap, p.cap, sw, sd, c);
+            dens_eval_cells<T>(g, bx, s.pos, i, xi, yi, zi, Ht, nbr + 4 * (size_t)i, p.cap, N, sw, sd, c);
         }
         cnt = c;
         sd_last = sd;
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(kDensBlock, sizeof(T) == 4 ? 10 : 1)
         int c = 0;
         for (int k = 0; k < ncache; ++k) {
             if (c_r2[k][t] < H2) {
-                if (c < p.cap) nbr[(size_t)i * p.cap + c] = c_j[k][t];
+                if (c < p.cap) nbr[lslot(c, i, N)] = c_j[k][t];
                 ++c;
             }
         }
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(kWarpDensBlock)
             int k = base;
             for_candidates_lanes<T>(g, bx, s.pos, i, xi, yi, zi, Ht, lane, [&](int j, T, T, T, T r2) {
                 if (r2 < H2) {
-                    if (k < p.cap) nbr[(size_t)i * p.cap + k] = (unsigned)j;
+                    if (k < p.cap) nbr[lslot(k, i, N)] = (unsigned)j;
                     ++k;
                 }
             });
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(128)
     for_candidates<T>(g, bx, s.pos, i, me.x, me.y, me.z, Hi,
                       [&](int j, T, T, T, T r2) {
                           if (r2 < H2) {
-                              if (c < p.cap) nbr[(size_t)i * p.cap + c] = (unsigned)j;
+                              if (c < p.cap) nbr[lslot(c, i, N)] = (unsigned)j;
                               ++c;
                           }
                       });
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(128)
                               dens_terms(q, w, qdw);
                               sw.add(w);
                               sd += qdw;
-                              if (c < p.cap) nbr[(size_t)i * p.cap + c] = (unsigned)j;
+                              if (c < p.cap) nbr[lslot(c, i, N)] = (unsigned)j;
                               ++c;
                           }
                       });
@@ -490,9 +491,9 @@ __global__ void k_reverse(int N, Sorted<T> s, KParams p, const unsigned* __restr
     const P4<T> me = s.pos[i];
     const T xim1 = me.x - T(1), yim1 = me.y - T(1), zim1 = me.z - T(1);
     const int cnt = min(ncount[i], p.cap);
-    const unsigned* L = nbr + (size_t)i * p.cap;
+    const unsigned* L = nbr + 4 * (size_t)i;
     for (int k0 = 0; k0 < cnt; k0 += 4) {
-        const uint4 jj = *reinterpret_cast<const uint4*>(L + k0);
+        const uint4 jj = col4(L, k0, N);
         const unsigned js[4] = {jj.x, jj.y, jj.z, jj.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -505,7 +506,7 @@ __global__ void k_reverse(int N, Sorted<T> s, KParams p, const unsigned* __restr
             if (!(r2 < q.w * q.w)) {
                 const int slot = atomicAdd(&rcount[j], 1);
                 if (slot < p.rcap)
-                    rnbr[(size_t)j * p.rcap + slot] = (unsigned)i;
+                    rnbr[lslot(slot, j, N)] = (unsigned)i;
                 else
                     set_status(st, GZ_S_NBR_OVERFLOW, GZ_C_NBR_OVERFLOW, s.id[j]);
             }
@@ -519,15 +520,15 @@ __global__ void k_sort_rev(int N, const int* __restrict__ rcount, unsigned* __re
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int n = min(rcount[i], rcap);
-    unsigned* L = rnbr + (size_t)i * rcap;
+    unsigned* L = rnbr + 4 * (size_t)i;
     for (int a = 1; a < n; ++a) {
-        const unsigned v = L[a];
+        const unsigned v = L[lcol(a, N)];
         int b = a - 1;
-        while (b >= 0 && L[b] > v) {
-            L[b + 1] = L[b];
+        while (b >= 0 && L[lcol(b, N)] > v) {
+            L[lcol(b + 1, N)] = L[lcol(b, N)];
             --b;
         }
-        L[b + 1] = v;
+        L[lcol(b + 1, N)] = v;
     }
 }
 
@@ -605,9 +606,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
         T vmax = T(0);
         bool any = false;
         const int cnt = min(ncount[i], p.cap);
-        const unsigned* L = nbr + (size_t)i * p.cap;
+        const unsigned* L = nbr + 4 * (size_t)i;
         for (int k0 = 0; k0 < cnt; k0 += 4) {
-            const uint4 jj = *reinterpret_cast<const uint4*>(L + k0);
+            const uint4 jj = col4(L, k0, N);
             const unsigned js[4] = {jj.x, jj.y, jj.z, jj.w};
             P4<T> q[4], w[4];
             P2<T> w2[4];
@@ -669,7 +670,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
             const double iHd = 1.0 / (double)Hi;
             const double normd = 8.0 / kPi * iHd * iHd * iHd / (double)ni;
             for (int k = 0; k < cnt; ++k) {
-                const P4<T> q = s.pos[L[k]];
+                const P4<T> q = s.pos[L[lcol(k, N)]];
                 const double dx = mi_diff((double)q.x, xd, 0.0), dy = mi_diff((double)q.y, yd, 0.0),
                              dz = mi_diff((double)q.z, zd, 0.0);
                 const double r = sqrt(sep2(dx, dy, dz));
@@ -718,7 +719,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
         T Dact[5] = {T(0), T(0), T(0), T(0), T(0)};
         const T beta = (T)p.beta;
         for (int k0 = 0; k0 < cnt; k0 += 4) {
-            const uint4 jj = *reinterpret_cast<const uint4*>(L + k0);
+            const uint4 jj = col4(L, k0, N);
             const unsigned js[4] = {jj.x, jj.y, jj.z, jj.w};
             P4<T> q[4];
 #pragma unroll
@@ -752,9 +753,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
         }
         if (want_dt) {
             const int rc = min(rcount[i], p.rcap);
-            const unsigned* RL = rnbr + (size_t)i * p.rcap;
+            const unsigned* RL = rnbr + 4 * (size_t)i;
             for (int k = 0; k < rc; ++k) {
-                const int j = (int)RL[k];
+                const int j = (int)RL[lcol(k, N)];
                 const P4<T> q = s.pos[j];
                 const P4<T> w = s.prim[j];
                 const T dx = mi_diff(q.x, xi, xim1), dy = mi_diff(q.y, yi, yim1),
@@ -916,10 +917,10 @@ __global__ void __launch_bounds__(kFluxBlock)
     int np = 0, nfall = 0, nneg = 0;
 #pragma unroll 1
     for (int list = 0; list < 2; ++list) {
-        const unsigned* L = list == 0 ? nbr + (size_t)i * p.cap : rnbr + (size_t)i * p.rcap;
+        const unsigned* L = list == 0 ? nbr + 4 * (size_t)i : rnbr + 4 * (size_t)i;
         const int cnt = list == 0 ? min(ncount[i], p.cap) : min(rcount[i], p.rcap);
         for (int k0 = 0; k0 < cnt; k0 += 4) {
-            const uint4 jj = *reinterpret_cast<const uint4*>(L + k0);
+            const uint4 jj = col4(L, k0, N);
             const unsigned js[4] = {jj.x, jj.y, jj.z, jj.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -1113,7 +1114,7 @@ __global__ void k_get_nbrs(int N, const unsigned* __restrict__ orig, const long 
     if (!ids_out) return;
     const int m = min(min(c, cap_in), cap);
     for (int k = 0; k < cap; ++k)
-        ids_out[(size_t)k * N + o] = k < m ? (int64_t)sid[nbr[(size_t)i * cap_in + k]] : (int64_t)-1;
+        ids_out[(size_t)k * N + o] = k < m ? (int64_t)sid[nbr[lslot(k, i, N)]] : (int64_t)-1;
 }
 
 // The limiter's choices per particle (sorted-order indices, 10 per particle)

@@ -250,6 +250,20 @@ __device__ __forceinline__ float sep2(float dx, float dy, float dz) {
     return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
+// Neighbour lists (N_i and the reverse lists) are stored in groups of four
+// slots: slots 4g..4g+3 of sorted particle i are the 16 bytes at (g N + i) 4,
+// N the context's particle count.  A warp, whose threads hold consecutive
+// particles, reads one group of their lists as 512 contiguous bytes, one
+// 16-byte load a thread.  A particle's list is the column nbr + 4 i; slot k
+// of a column lies at lcol(k, N).  (Capacities are multiples of four.)
+__device__ __forceinline__ size_t lcol(int k, int N) { return (size_t)(k >> 2) * 4 * (size_t)N + (size_t)(k & 3); }
+__device__ __forceinline__ size_t lslot(int k, int i, int N) { return 4 * (size_t)i + lcol(k, N); }
+// Slots k0..k0+3 (k0 a multiple of four) of the list column L; those at or
+// past the list's count hold no particle.
+__device__ __forceinline__ uint4 col4(const unsigned* __restrict__ L, int k0, int N) {
+    return *reinterpret_cast<const uint4*>(L + lcol(k0, N));
+}
+
 // ordered-integer image of a non-negative double (for atomicMin)
 __device__ __forceinline__ unsigned long long dbits(double v) {
     return (unsigned long long)__double_as_longlong(v);
