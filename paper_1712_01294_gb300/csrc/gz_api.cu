@@ -512,7 +512,7 @@ gz_status create_ctx(const gz_params* params, int32_t nboxes, const int64_t* cou
     const size_t Nz = (size_t)N;
     const size_t sz = params->precision == GZ_FP64 ? 8 : 4;
     const int nblk = (int)((N + 4095) / 4096);
-    c.hist_len = 512 * nblk + 512;  // per-block counts of up to 512 digits, then the digit totals
+    c.hist_len = 1024 * nblk + 1024;  // per-block counts of up to 1024 digits, then the digit totals
     struct Item {
         void** ptr;
         size_t bytes;

@@ -24,7 +24,7 @@ constexpr int kCap = 32;          // neighbour-list slots (lists are not returne
 constexpr int kMaxDevices = 64;
 
 constexpr size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
-constexpr size_t kHistLen = 512 * ((kMaxN + 4095) / 4096) + 512;  // counts + digit totals
+constexpr size_t kHistLen = 1024 * ((kMaxN + 4095) / 4096) + 1024;  // counts + digit totals
 // Worst case (FP64) of every slice the density pass touches.
 constexpr size_t kScratchBytes =
     4 * al(4 * (size_t)kMaxN)                          // keys, keys_alt, vals, vals_alt
@@ -41,7 +41,7 @@ constexpr size_t kScratchBytes =
     + al(sizeof(DevStatus));
 
 // The scratch itself: every GPU that loads the library holds these bytes
-// (8,276,736 B, about 8.3 MB) until the process exits.  All calls share it.
+// (8,295,168 B, about 8.3 MB) until the process exits.  All calls share it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_mu;

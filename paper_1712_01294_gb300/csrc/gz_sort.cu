@@ -11,8 +11,9 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kMaxDigitBits = 9;  // digits of up to 9 bits: 512 buckets a pass
+constexpr int kMaxDigitBits = 10;  // digits of up to 10 bits: 1024 buckets a pass
 constexpr int kMaxDigits = 1 << kMaxDigitBits;
+constexpr int kDigitsPerThread = kMaxDigits / kSortThreads;
 constexpr int kSortTile = 4096;
 constexpr int kSortPerWarp = kSortTile / kSortWarps;
 
@@ -118,16 +119,24 @@ __global__ void k_rs_scatter(const unsigned* __restrict__ kin, const unsigned* _
                              int N, int shift, unsigned mask, int nd, const unsigned* __restrict__ hist,
                              int nblk, const unsigned* __restrict__ totals, unsigned* __restrict__ kout,
                              unsigned* __restrict__ vout) {
-    static_assert(kMaxDigits == 2 * kSortThreads, "two digits per thread");
+    static_assert(kDigitsPerThread * kSortThreads == kMaxDigits, "whole digits per thread");
     __shared__ unsigned cnt[kSortWarps][kMaxDigits];
     __shared__ unsigned dbase[kMaxDigits];
     __shared__ unsigned wsum[kSortWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int t = threadIdx.x; t < kSortWarps * kMaxDigits; t += blockDim.x) (&cnt[0][0])[t] = 0;
-    {  // exclusive scan of the nd digit totals, two digits per thread
-        const int d0 = 2 * threadIdx.x;
-        const unsigned v0 = d0 < nd ? totals[d0] : 0u, v1 = d0 + 1 < nd ? totals[d0 + 1] : 0u;
-        const unsigned tv = v0 + v1;
+    {  // the nd digits of this pass (nd a power of 2)
+        const int lg = __ffs(nd) - 1;
+        for (int t = threadIdx.x; t < kSortWarps * nd; t += blockDim.x) cnt[t >> lg][t & (nd - 1)] = 0;
+    }
+    {  // exclusive scan of the nd digit totals, kDigitsPerThread consecutive digits a thread
+        const int d0 = kDigitsPerThread * threadIdx.x;
+        unsigned v[kDigitsPerThread];
+        unsigned tv = 0;
+#pragma unroll
+        for (int u = 0; u < kDigitsPerThread; ++u) {
+            v[u] = d0 + u < nd ? totals[d0 + u] : 0u;
+            tv += v[u];
+        }
         unsigned incl = tv;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -138,8 +147,12 @@ __global__ void k_rs_scatter(const unsigned* __restrict__ kin, const unsigned* _
         __syncthreads();
         unsigned before = 0;
         for (int w = 0; w < warp; ++w) before += wsum[w];
-        dbase[d0] = before + incl - tv;
-        dbase[d0 + 1] = before + incl - tv + v0;
+        unsigned run = before + incl - tv;
+#pragma unroll
+        for (int u = 0; u < kDigitsPerThread; ++u) {
+            dbase[d0 + u] = run;
+            run += v[u];
+        }
     }
     __syncthreads();
     const int wbase = blockIdx.x * kSortTile + warp * kSortPerWarp;
