@@ -246,6 +246,10 @@ class DecomposedBox:
         for r in ranks:
             parts, flags = self.assemble(r, inbox[r])
             n, nown = int(parts["id"].numel()), int(self.owned[r]["id"].numel())
+            if n == 0:  # nothing in or near this slab: no step, no bound on the box's step
+                dts[r] = torch.full((1,), math.inf, dtype=torch.float64, device=self.device)
+                local[r] = None
+                continue
             ctx = self.context(r, n)
             ctx.set_subdomain(n, nown, flags)
             dts[r] = ctx.step_begin(parts)
@@ -255,6 +259,8 @@ class DecomposedBox:
         else:
             dt = self.comm.allreduce(dts, "min")
         for r in ranks:
+            if local[r] is None:
+                continue
             parts, flags = local[r]
             self.ctx[r].step_finish(parts, dt[r])
             self.owned[r] = take(parts, torch.nonzero(flags).flatten())

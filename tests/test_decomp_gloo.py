@@ -110,6 +110,20 @@ def test_three_subdomains_in_one_process_equal_the_undivided_box():
     assert sum(got.owned[r]["id"].numel() for r in range(3)) == N
 
 
+def test_empty_slab_is_skipped():
+    # every particle in x < 1/4: with 4 slabs, slab 2 holds none and lies
+    # beyond the halo of every particle (slabs 1 and 3 hold ghosts only)
+    parts, N = box()
+    parts["x"] = parts["x"] * 0.25
+    ref, dref = run(parts, N, 1, D.LocalComm(1), 3)
+    got, dgot = run(parts, N, 4, D.LocalComm(4), 3)
+    assert dgot == dref
+    assert 2 not in got.ctx or not got.ctx[2].held  # slab 2 never stepped
+    a, b = ref.gather(), got.gather()
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+
+
 def _rank(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
                       WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
