@@ -100,9 +100,9 @@ struct Ctx {
     int* sbox;
     int* iters;
     int* ncount;
-    unsigned* nbr;  // [N][cap], particle i's list contiguous
+    unsigned* nbr;  // cap slots a particle, in groups of four across the particles (lslot)
     int* rcount;
-    unsigned* rnbr;  // [N][rcap]
+    unsigned* rnbr;  // rcap slots a particle, laid out like nbr
     void* rec;       // [N][kRecord] working precision
     int* defer = nullptr;   // [N] particles the density pass leaves to its warp-per-particle kernel
     int* ndefer = nullptr;  // [1] their number
