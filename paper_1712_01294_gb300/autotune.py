@@ -10,10 +10,14 @@ Two knobs decide how the density pass maps particles to lanes:
   with more candidates within 1.05 H than its cache holds is iterated by a
   warp (a blast cavity, the smallest boxes of an ensemble), and the larger
   cache costs occupancy.
-The tuner times a few full steps for each combination on a copy of the
-caller's particles (through the C ABI, CUDA-event timed) and keeps the
-fastest; results are cached by (particle counts, precision, distribution
-signature) in a JSON file.  The other kernels' block shapes are fixed by
+The tuner times full steps for each combination on a copy of the caller's
+particles (through the C ABI, CUDA-event timed) and keeps the fastest.  The
+steps timed should cover the run being tuned for: the best cache size moves
+as the run evolves (in the 256-box Sod/Sedov ensemble the 40-entry cache is
+fastest over steps 2-3 and the 48-entry one over the 20 steps of the run,
+by 8 %, once the blast cavities form), so `tune(..., steps=20, warmup=0)`
+tunes a 20-step run from its initial state.  Results are cached by
+(particle counts, precision, distribution signature, steps) in a JSON file.  The other kernels' block shapes are fixed by
 design (one thread per particle, sized for occupancy at their register
 counts).
 """
@@ -51,7 +55,7 @@ def _key(cf, cache):
     return f"{float(cf)},{int(cache)}"
 
 
-def tune(p, precision, candidates=DEFAULT_CANDIDATES, caches=DEFAULT_CACHES, steps: int = 2,
+def tune(p, precision, candidates=DEFAULT_CANDIDATES, caches=DEFAULT_CACHES, steps: int = 8,
          warmup: int = 1, cache: str | None = None, use_cache: bool = True, **params):
     """Returns (best (cell_factor, density_cache), {(cell_factor, density_cache): ms
     per step}) for host particles p."""
@@ -59,7 +63,8 @@ def tune(p, precision, candidates=DEFAULT_CANDIDATES, caches=DEFAULT_CACHES, ste
 
     import paper_1712_01294_gb300 as gz
     path = _cache_path(cache)
-    key = signature(p, precision) + ":c" + "-".join(str(int(c)) for c in caches)
+    key = (signature(p, precision) + ":c" + "-".join(str(int(c)) for c in caches)
+           + f":s{int(warmup)}+{int(steps)}")
     db = {}
     if use_cache and os.path.exists(path):
         try:
