@@ -1,7 +1,7 @@
 """The benchmark's own launch at full size: one gz_step of the 128^3
 turbulence box (2,097,152 particles, FP32 mixed path, one box, default cell
-size), checked against the FP64 oracle on sampled outputs it can compute one
-by one: every particle of four cubic sub-boxes (one of them around the
+size), and of a 256^3 box, checked against the FP64 oracle on sampled
+outputs it can compute one by one: every particle of four cubic sub-boxes (one of them around the
 particle that sets the CFL step), each oracle pass run on the particles it
 needs there (sub-box plus halos of 2.2 and 4.4 times the largest support).
 Tolerances as in the per-pass parity tests.  FP32: H within 2e-6, per-particle
@@ -31,13 +31,12 @@ def around(s, centres, half):
     return ok
 
 
-@pytest.mark.parametrize("prec", [1, 0])
-def test_128cubed_step_matches_oracle_on_sampled_sub_boxes(prec):
+def sampled_step_check(n, prec):
     import torch
 
     import paper_1712_01294_gb300 as m
     f64 = prec == m.GZ_FP64
-    q = cast_state(I.turbulence(128, seed=1714), prec)
+    q = cast_state(I.turbulence(n, seed=1714), prec)
     s = ostate(q)
     ctx = m.Context([q.N], m.default_params(precision=prec))
     # per-pass view of the step's first passes: converged H, n, per-particle dt
@@ -57,7 +56,7 @@ def test_128cubed_step_matches_oracle_on_sampled_sub_boxes(prec):
     dt = float(dtu.item())
     assert dt == float(dtb[0].item())
 
-    rng = np.random.default_rng(128)
+    rng = np.random.default_rng(n)
     centres = [rng.uniform(0, 1, 3) for _ in range(3)] + [np.array([s.x[kmin], s.y[kmin], s.z[kmin]])]
     half = 0.02
     Hm = 1.3 * float(np.max(s.H))
@@ -90,6 +89,20 @@ def test_128cubed_step_matches_oracle_on_sampled_sub_boxes(prec):
         assert (mx <= 1e-10) if f64 else (rm <= 50 * 2e-5), (k, mx, rm)
     assert np.max(np.abs(d["h"].cpu().numpy().astype(np.float64)[m_f] - H[m_f]) / H[m_f]) <= \
         (1e-12 if f64 else 2e-6)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_128cubed_step_matches_oracle_on_sampled_sub_boxes(prec):
+    sampled_step_check(128, prec)
+
+
+def test_256cubed_fp32_step_matches_oracle_on_sampled_sub_boxes():
+    """The same check at 256^3 = 16,777,216 particles (about 18 GB of
+    context on the device): indices, list layouts and the 24-bit sort keys
+    at eight times the benchmark's size."""
+    import paper_1712_01294_gb300 as m
+    sampled_step_check(256, m.GZ_MIXED32)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
