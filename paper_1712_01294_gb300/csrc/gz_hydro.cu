@@ -713,10 +713,13 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
 #pragma unroll
             for (int q = 0; q < 15; ++q) gt[q] = T(0);
         }
-        // O9 limiter: alpha_f = min_j min(1, beta (f_ext - f_i) / (g . s_ij d))
-        T al[5] = {T(1), T(1), T(1), T(1), T(1)};
-        int jact[5] = {-1, -1, -1, -1, -1}, kact[5] = {i, i, i, i, i};
-        T Dact[5] = {T(0), T(0), T(0), T(0), T(0)};
+        // O9 limiter: alpha_f = min_j min(1, beta (f_ext - f_i) / D_j), D_j = g . s_ij d.
+        // The numerator is fixed per field and the quotient decreases as D
+        // moves away from 0 on its side, so the minimum is taken by the
+        // largest positive and the most negative D_j: one division per field
+        // and side after the loop instead of one per neighbour
+        T Dpos[5] = {T(0), T(0), T(0), T(0), T(0)}, Dneg[5] = {T(0), T(0), T(0), T(0), T(0)};
+        int jpos[5] = {-1, -1, -1, -1, -1}, jneg[5] = {-1, -1, -1, -1, -1};
         const T beta = (T)p.beta;
         for (int k0 = 0; k0 < cnt; k0 += 4) {
             const uint4 jj = col4(L, k0, N);
@@ -735,21 +738,45 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1)
 #pragma unroll
                 for (int f = 0; f < 5; ++f) {
                     const T D = (gt[3 * f] * ox + gt[3 * f + 1] * oy) + gt[3 * f + 2] * oz;
-                    T a = T(1);
-                    if (D > T(0))
-                        a = min(T(1), pdiv(beta * (fmax[f] - Wi[f]), D));
-                    else if (D < T(0))
-                        a = min(T(1), pdiv(beta * (fmin[f] - Wi[f]), D));
-                    if (a < al[f]) {
-                        al[f] = a;
-                        if constexpr (kInfo) {
-                            jact[f] = (int)js[u];
-                            kact[f] = D > T(0) ? kmax[f] : kmin[f];
-                            Dact[f] = D;
-                        }
+                    if (D > Dpos[f]) {
+                        Dpos[f] = D;
+                        if constexpr (kInfo) jpos[f] = (int)js[u];
+                    }
+                    if (D < Dneg[f]) {
+                        Dneg[f] = D;
+                        if constexpr (kInfo) jneg[f] = (int)js[u];
                     }
                 }
             }
+        }
+        T al[5];
+        int jact[5], kact[5];
+        T Dact[5];
+#pragma unroll
+        for (int f = 0; f < 5; ++f) {
+            T a = T(1);
+            jact[f] = -1;
+            kact[f] = i;
+            Dact[f] = T(0);
+            if (Dpos[f] > T(0)) {
+                const T ap = min(T(1), pdiv(beta * (fmax[f] - Wi[f]), Dpos[f]));
+                if (ap < a) {
+                    a = ap;
+                    jact[f] = jpos[f];
+                    kact[f] = kmax[f];
+                    Dact[f] = Dpos[f];
+                }
+            }
+            if (Dneg[f] < T(0)) {
+                const T am = min(T(1), pdiv(beta * (fmin[f] - Wi[f]), Dneg[f]));
+                if (am < a) {
+                    a = am;
+                    jact[f] = jneg[f];
+                    kact[f] = kmin[f];
+                    Dact[f] = Dneg[f];
+                }
+            }
+            al[f] = a;
         }
         if (want_dt) {
             const int rc = min(rcount[i], p.rcap);
