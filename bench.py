@@ -479,13 +479,14 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p, fp64_peak=None):
         if a.extras in ("all", "adjoint"):
             # adjoint of one step (same workload, same precision), dt frozen, in the
             # configuration MFMStep runs it: the forward fills the step checkpoint
-            # (gz_step_checkpoint: rates and the gradient pass's per-particle
-            # outputs) and returns the converged H; the backward recomputes the
-            # sort, density and pair-list passes and every pair quantity
+            # (gz_step_checkpoint at GZ_CKPT_LISTS: rates, the gradient pass's
+            # per-particle outputs, the sorted order, n and the neighbour lists)
+            # and returns the converged H; the backward recomputes the reverse
+            # lists and every pair quantity
             rng = np.random.default_rng(0)
             T = d["x"].dtype
             start = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in d.items()}
-            level = gz.GZ_CKPT_GRADIENTS
+            level = gz.GZ_CKPT_LISTS
             ck = ctx.new_checkpoint(level)
             K = max(2, a.steps // 2)
             # the plain forward over the same K steps (the denominator of the
@@ -539,9 +540,10 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p, fp64_peak=None):
                               "checkpoint_bytes_per_particle": round(ctx.checkpoint_bytes(level) / p.N, 1),
                               "backward_full_recompute_ms_per_step": round(ms_bwd_full, 4),
                               "steps": K, "status_ok": st["ok"],
-                              "what": "gz_step_backward from the MFMStep checkpoint (start state, "
-                                      "converged H, rates and gradient-pass outputs): sort, density, "
-                                      "pair lists and all pair quantities recomputed, then the adjoint "
+                              "what": "gz_step_backward from the MFMStep checkpoint at GZ_CKPT_LISTS "
+                                      "(start state, converged H, n, rates, gradient-pass outputs, the "
+                                      "sorted order and the lists' first 64 slots): the reverse pair "
+                                      "lists and all pair quantities recomputed, then the adjoint "
                                       "passes"}
             del ck
         if a.extras == "adjoint":

@@ -314,15 +314,22 @@ gz_status gz_graph_launch(gz_ctx* ctx);
  * gz_checkpoint_bytes(level) bytes, written by gz_step_checkpoint and read
  * by gz_step_backward of the same step; its layout is private.  Level
  * GZ_CKPT_RATES keeps the step's conserved-variable rates (the momentum
- * and total-energy rates of the MFM update, O12) and the converged support
- * radii (O4; 36 bytes a particle in FP32) so the backward pass skips the
- * h-iteration and the flux pass; GZ_CKPT_GRADIENTS also keeps the
+ * and total-energy rates of the MFM update, O12), the converged support
+ * radii (O4) and the number density and kernel-derivative sum at them (44
+ * bytes a particle in FP32) so the backward pass skips the h-iteration and
+ * the flux pass; GZ_CKPT_GRADIENTS also keeps the
  * gradient pass's per-particle outputs (limited gradients, E^-1, limiter
  * factors and the indices of the limiting particles; about 330 bytes a
- * particle in FP32) so the backward pass skips that pass too.  No pair
- * quantity is ever stored: the backward pass recomputes every one. */
+ * particle in FP32) so the backward pass skips that pass too;
+ * GZ_CKPT_LISTS also keeps the sort's order and the neighbour lists
+ * (their first 64 slots: about 270 bytes a particle more in FP32) so the
+ * backward pass skips the radix sort and the density rescan that rebuilds
+ * them (lists longer than 64 are rebuilt by a scan).  No pair quantity is
+ * ever stored: the backward pass recomputes every one.  Every level gives
+ * the same backward result bit for bit. */
 #define GZ_CKPT_RATES 0
 #define GZ_CKPT_GRADIENTS 1
+#define GZ_CKPT_LISTS 2
 gz_status gz_checkpoint_bytes(gz_ctx* ctx, int32_t level, int64_t* bytes);
 
 /* The choices of the O9 limiter in the step whose checkpoint is ckpt (level

@@ -28,7 +28,7 @@ GZ_OK, GZ_E_INVAL, GZ_E_NOMEM, GZ_E_CUDA, GZ_E_DEVICE = 0, 1, 2, 3, 4
 GZ_FP64, GZ_MIXED32 = 0, 1
 GZ_MFM, GZ_MFV = 0, 1
 GZ_RIEMANN_HLLC, GZ_RIEMANN_EXACT, GZ_RIEMANN_FALLBACK = 0, 1, 2
-GZ_CKPT_RATES, GZ_CKPT_GRADIENTS = 0, 1
+GZ_CKPT_RATES, GZ_CKPT_GRADIENTS, GZ_CKPT_LISTS = 0, 1, 2
 STATUS_BITS = {
     "hconv": 1 << 0, "singular": 1 << 1, "nonfinite": 1 << 2, "nbr_overflow": 1 << 3,
     "hlim": 1 << 4, "fallback": 1 << 8, "pstar_neg": 1 << 9, "ufloor": 1 << 10,
@@ -332,8 +332,8 @@ class Context:
         return int(v.value)
 
     def new_checkpoint(self, level: int = 1):
-        """A device buffer for one step checkpoint (GZ_CKPT_RATES = 0 or
-        GZ_CKPT_GRADIENTS = 1)."""
+        """A device buffer for one step checkpoint (GZ_CKPT_RATES = 0,
+        GZ_CKPT_GRADIENTS = 1 or GZ_CKPT_LISTS = 2)."""
         return self.empty(self.checkpoint_bytes(level), dtype=self.torch.uint8)
 
     def checkpoint_limiters(self, ckpt):

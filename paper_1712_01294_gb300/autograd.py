@@ -4,13 +4,16 @@ gz_step_backward (the hand-written adjoint in the CUDA library).
 Per-step checkpointing: each MFMStep node keeps the state its step started
 from (x, y, z, vx, vy, vz, m, u), the converged support radius the step
 returned and the step's checkpoint buffer (gz_step_checkpoint): the
-per-particle momentum and energy rates and, at the default level
-GZ_CKPT_GRADIENTS, the gradient pass's per-particle outputs (about 360 bytes
-a particle in FP32 in all; GZ_CKPT_RATES keeps 32).  The backward pass
-re-runs the step's sort, density and pair-list passes inside
-gz_step_backward (neighbour sets, H and every pair quantity recomputed, not
-stored); starting the h-iteration at the converged H makes it accept that H
-at once.  The step dt is frozen at the value the forward used: a CFL step is
+per-particle momentum and energy rates with n and the kernel-derivative sum
+at the converged H, at GZ_CKPT_GRADIENTS also the gradient pass's
+per-particle outputs (about 370 bytes a particle in FP32; GZ_CKPT_RATES
+keeps 40), and at the default level GZ_CKPT_LISTS also the sort's order and
+the neighbour lists' first 64 slots (about 640 bytes a
+particle in all).  The backward pass re-runs inside gz_step_backward what the
+checkpoint does not hold (at level 2: the reverse pair lists; at lower
+levels the sort, the density pass at the converged H and the lists) and
+recomputes every pair quantity: none is stored.  Every level gives the same
+gradients bit for bit.  The step dt is frozen at the value the forward used: a CFL step is
 read back once per step.
 
 Differentiable inputs: x, y, z, vx, vy, vz, m, u.  The support radius h is
@@ -57,9 +60,10 @@ class MFMStep(torch.autograd.Function):
                 gstart["vy"], gstart["vz"], gstart["m"], gstart["u"], None)
 
 
-def step(gz_ctx, state: dict, dt: float = 0.0, level: int = 1) -> dict:
+def step(gz_ctx, state: dict, dt: float = 0.0, level: int = 2) -> dict:
     """One differentiable step; state holds x..u, h (tensors) and id; level is
-    the checkpoint level (1: rates and gradient pass kept, 0: rates only)."""
+    the checkpoint level (2: also the sorted order and lists, 1: rates and
+    gradient pass kept, 0: rates only)."""
     outs = MFMStep.apply(gz_ctx, float(dt), int(level), state["id"], *(state[k] for k in STATE))
     new = dict(zip(OUT, outs))
     new["m"] = state["m"]
@@ -67,7 +71,7 @@ def step(gz_ctx, state: dict, dt: float = 0.0, level: int = 1) -> dict:
     return new
 
 
-def rollout(gz_ctx, state: dict, nsteps: int, dts=None, level: int = 1):
+def rollout(gz_ctx, state: dict, nsteps: int, dts=None, level: int = 2):
     """nsteps differentiable steps (CFL steps unless dts gives them); returns
     the final state and the list of steps used."""
     used = []

@@ -233,21 +233,37 @@ gz_status do_fluxes_backward(gz_ctx* ctx, const gz_particles* p, const void* n, 
 // order] [converged H, sorted order] then, at GZ_CKPT_GRADIENTS, the
 // gradient pass's per-particle outputs in sorted order: flux record
 // [N][kRecord], adjoint info [N][kGInfo] (working precision) and limiter
-// indices [N][10]; slices start on 256-byte boundaries.  (The backward
-// pass sorts the same start state, so sorted order is the same.)
+// indices [N][10]; at GZ_CKPT_LISTS also the sorted keys and order [N] u32
+// each, the neighbour counts [N] and the first kCkptSlots slots of the
+// neighbour lists (a prefix of their grouped layout); slices start on
+// 256-byte boundaries.  Every level also keeps n and sum(-w'q) at the
+// converged H (sorted order, after H): the density pass of a particle the
+// h-iteration left to the warp kernel sums them in another order than a
+// rescan would.
+// (The backward pass sorts the same start state, so sorted order is the
+// same.)
+constexpr int kCkptSlots = 64;
 struct Ckpt {
     double* rates = nullptr;
     void* H = nullptr;
+    void *n = nullptr, *sd = nullptr;
     void* rec = nullptr;
     void* ginfo = nullptr;
     int* lim = nullptr;
+    unsigned *keys = nullptr, *vals = nullptr;  // GZ_CKPT_LISTS
+    int* ncount = nullptr;
+    unsigned* nbr = nullptr;
+    int slots = 0;
 };
 size_t ckpt_slice(size_t b) { return (b + 255) & ~(size_t)255; }
+int ckpt_slots(const Ctx& c) { return std::min(c.cap, kCkptSlots); }
 size_t ckpt_bytes(const Ctx& c, int level) {
     const size_t N = (size_t)c.N, ts = c.precision == GZ_FP64 ? 8 : 4;
-    size_t b = ckpt_slice(sizeof(double) * 4 * N) + ckpt_slice(ts * N);
+    size_t b = ckpt_slice(sizeof(double) * 4 * N) + 3 * ckpt_slice(ts * N);
     if (level >= GZ_CKPT_GRADIENTS)
         b += ckpt_slice(ts * N * kRecord) + ckpt_slice(ts * N * kGInfo) + ckpt_slice(sizeof(int) * N * 10);
+    if (level >= GZ_CKPT_LISTS)
+        b += 3 * ckpt_slice(4 * N) + ckpt_slice(4 * N * (size_t)ckpt_slots(c));
     return b;
 }
 Ckpt ckpt_view(const Ctx& c, void* base, int level) {
@@ -259,14 +275,66 @@ Ckpt ckpt_view(const Ctx& c, void* base, int level) {
     p += ckpt_slice(sizeof(double) * 4 * N);
     k.H = p;
     p += ckpt_slice(ts * N);
+    k.n = p;
+    p += ckpt_slice(ts * N);
+    k.sd = p;
+    p += ckpt_slice(ts * N);
     if (level >= GZ_CKPT_GRADIENTS) {
         k.rec = p;
         p += ckpt_slice(ts * N * kRecord);
         k.ginfo = p;
         p += ckpt_slice(ts * N * kGInfo);
         k.lim = (int*)p;
+        p += ckpt_slice(sizeof(int) * N * 10);
+    }
+    if (level >= GZ_CKPT_LISTS) {
+        k.keys = (unsigned*)p;
+        p += ckpt_slice(4 * N);
+        k.vals = (unsigned*)p;
+        p += ckpt_slice(4 * N);
+        k.ncount = (int*)p;
+        p += ckpt_slice(4 * N);
+        k.nbr = (unsigned*)p;
+        k.slots = ckpt_slots(c);
     }
     return k;
+}
+
+// What the sort and the density pass leave that the backward pass would
+// otherwise recompute: the sort's keys and order, the neighbour counts and
+// the lists' first slots (groups of four slots across the particles:
+// the first slots/4 groups are one contiguous prefix).
+template <typename T>
+cudaError_t save_lists(Ctx& c, const Ckpt& k) {
+    const size_t N = (size_t)c.N;
+    cudaStream_t st = c.stream;
+    cudaError_t e = cudaMemcpyAsync(k.keys, c.keys, 4 * N, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(k.vals, c.vals, 4 * N, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(k.ncount, c.ncount, 4 * N, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(k.nbr, c.nbr, 4 * N * (size_t)k.slots, cudaMemcpyDeviceToDevice, st);
+    return e;
+}
+
+// The backward pass's sort and density pass from a GZ_CKPT_LISTS checkpoint:
+// the sorted order and cells from the saved keys, the saved H, n, sums,
+// counts and list slots, and a scan for the lists longer than the saved
+// slots; the same values the sort and k_dens_given give.
+template <typename T>
+cudaError_t restore_lists(Ctx& c, const gz_particles& p, const Ckpt& k) {
+    const size_t N = (size_t)c.N;
+    cudaStream_t st = c.stream;
+    cudaError_t e = cudaMemcpyAsync(c.keys, k.keys, 4 * N, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.vals, k.vals, 4 * N, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = permute_and_bin<T>(c, p, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.sh, k.H, sizeof(T) * N, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.sn, k.n, sizeof(T) * N, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.ssd, k.sd, sizeof(T) * N, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.ncount, k.ncount, 4 * N, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c.nbr, k.nbr, 4 * N * (size_t)k.slots, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && k.slots < c.cap) e = run_lists_over<T>(c, k.slots);
+    return e;
 }
 
 // Points the context's gradient-pass outputs at a checkpoint for one call.
@@ -299,15 +367,22 @@ gz_status do_step_backward(gz_ctx* ctx, const gz_particles* p, double dt, const 
     Ctx& c = ctx->c;
     cudaError_t e = ensure_adjoint_scratch(c);
     GradOutputs outs(c, ck);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && ck.keys) {  // GZ_CKPT_LISTS: sorted order and lists kept
+        Pass t(c, GZ_PASS_SORT);
+        e = restore_lists<T>(c, *p, ck);
+    }
+    if (e == cudaSuccess && !ck.keys) {
         Pass t(c, GZ_PASS_SORT);
         e = sort_and_bin<T>(c, *p, nullptr);
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !ck.keys) {
         Pass t(c, GZ_PASS_DENSITY);
-        if (ck.H) {  // the forward's converged H: no h-iteration
-            e = cudaMemcpyAsync(c.sh, ck.H, sizeof(T) * (size_t)c.N, cudaMemcpyDeviceToDevice, c.stream);
+        if (ck.H) {  // the forward's converged H: no h-iteration; its n and sums
+            const size_t bytes = sizeof(T) * (size_t)c.N;
+            e = cudaMemcpyAsync(c.sh, ck.H, bytes, cudaMemcpyDeviceToDevice, c.stream);
             if (e == cudaSuccess) e = run_density_given<T>(c);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(c.sn, ck.n, bytes, cudaMemcpyDeviceToDevice, c.stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(c.ssd, ck.sd, bytes, cudaMemcpyDeviceToDevice, c.stream);
         } else {
             e = run_density<T>(c);
         }
@@ -392,8 +467,11 @@ gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_DENSITY);
         e = run_density<T>(c);
-        if (e == cudaSuccess && ck.H)
-            e = cudaMemcpyAsync(ck.H, c.sh, sizeof(T) * (size_t)c.N, cudaMemcpyDeviceToDevice, c.stream);
+        const size_t bytes = sizeof(T) * (size_t)c.N;
+        if (e == cudaSuccess && ck.H) e = cudaMemcpyAsync(ck.H, c.sh, bytes, cudaMemcpyDeviceToDevice, c.stream);
+        if (e == cudaSuccess && ck.n) e = cudaMemcpyAsync(ck.n, c.sn, bytes, cudaMemcpyDeviceToDevice, c.stream);
+        if (e == cudaSuccess && ck.sd) e = cudaMemcpyAsync(ck.sd, c.ssd, bytes, cudaMemcpyDeviceToDevice, c.stream);
+        if (e == cudaSuccess && ck.keys) e = save_lists<T>(c, ck);
     }
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_PRIM);
@@ -749,7 +827,7 @@ gz_status gz_step_hier(gz_ctx* ctx, gz_particles* p, int32_t K, double dt_fixed,
 }
 
 gz_status gz_checkpoint_bytes(gz_ctx* ctx, int32_t level, int64_t* bytes) {
-    if (!ctx || !bytes || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS) return GZ_E_INVAL;
+    if (!ctx || !bytes || level < GZ_CKPT_RATES || level > GZ_CKPT_LISTS) return GZ_E_INVAL;
     if (ctx->c.owned) return refuse_subdomain(ctx, "gz_checkpoint_bytes");
     *bytes = (int64_t)ckpt_bytes(ctx->c, level);
     return GZ_OK;
@@ -760,7 +838,7 @@ gz_status gz_step_checkpoint(gz_ctx* ctx, gz_particles* p, double dt_fixed, doub
     if (!ctx) return GZ_E_INVAL;
     if (gz_status s = check_particles(ctx, p, true)) return s;
     if (!isfinite(dt_fixed)) return fail(ctx, GZ_E_INVAL, "dt_fixed must be finite");
-    if (!ckpt || ((uintptr_t)ckpt & 255) || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS)
+    if (!ckpt || ((uintptr_t)ckpt & 255) || level < GZ_CKPT_RATES || level > GZ_CKPT_LISTS)
         return fail(ctx, GZ_E_INVAL, "checkpoint: need a 256-byte aligned buffer and a valid level");
     if (!adjoint_covers(ctx->c.params))
         return fail(ctx, GZ_E_INVAL, "the adjoint covers GZ_MFM with GZ_RIEMANN_HLLC only");
@@ -829,7 +907,7 @@ gz_status gz_step_backward(gz_ctx* ctx, const gz_particles* p_start, double dt, 
     if (!(dt > 0.0) || !isfinite(dt)) return fail(ctx, GZ_E_INVAL, "dt must be finite and > 0");
     if (!adjoint_covers(ctx->c.params))
         return fail(ctx, GZ_E_INVAL, "the adjoint covers GZ_MFM with GZ_RIEMANN_HLLC only");
-    if (ckpt && (((uintptr_t)ckpt & 255) || level < GZ_CKPT_RATES || level > GZ_CKPT_GRADIENTS))
+    if (ckpt && (((uintptr_t)ckpt & 255) || level < GZ_CKPT_RATES || level > GZ_CKPT_LISTS))
         return fail(ctx, GZ_E_INVAL, "checkpoint: need a 256-byte aligned buffer and a valid level");
     if (ctx->c.owned) return refuse_subdomain(ctx, "gz_step_backward");
     const Ckpt ck = ckpt_view(ctx->c, const_cast<void*>(ckpt), level);

@@ -366,26 +366,11 @@ __global__ void __launch_bounds__(kWarpDensBlock)
             H = Hn;
         }
         if (it > p.max_iter) it = p.max_iter;
-        {  // list of the returned H, lane by lane (each lane's share in its scan
-           // order, lanes in order): count, exclusive prefix across the warp, write
+        {  // list of the returned H, in the order a thread's scan writes it (the
+           // order of k_density, k_dens_given and k_lists)
             const T Ht = (T)Hev;
-            const T H2 = Ht * Ht;
-            int mine = 0;
-            for_candidates_lanes<T>(g, bx, s.pos, i, xi, yi, zi, Ht, lane,
-                                    [&](int, T, T, T, T r2) { mine += r2 < H2; });
-            int base = mine;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, base, o);
-                if (lane >= o) base += y;
-            }
-            base -= mine;
-            int k = base;
-            for_candidates_lanes<T>(g, bx, s.pos, i, xi, yi, zi, Ht, lane, [&](int j, T, T, T, T r2) {
-                if (r2 < H2) {
-                    if (k < p.cap) nbr[lslot(k, i, N)] = (unsigned)j;
-                    ++k;
-                }
+            for_hits_lanes_ordered<T>(g, bx, s.pos, i, xi, yi, zi, Ht, Ht * Ht, lane, [&](int k, int j) {
+                if (k < p.cap) nbr[lslot(k, i, N)] = (unsigned)j;
             });
         }
         if (lane == 0) {
@@ -409,13 +394,16 @@ __global__ void __launch_bounds__(kWarpDensBlock)
     }
 }
 
-// Neighbour lists N_i = {j : r_ij < H_i} for given H (O3).
+// Neighbour lists N_i = {j : r_ij < H_i} for given H (O3).  only_over > 0:
+// only the particles whose count exceeds it (lists a checkpoint kept up to
+// that many slots; the others are restored from it).
 template <typename T>
 __global__ void __launch_bounds__(128)
     k_lists(int N, Sorted<T> s, Grid g, KParams p, unsigned* __restrict__ nbr,
-            int* __restrict__ ncount, DevStatus* st) {
+            int* __restrict__ ncount, DevStatus* st, int only_over) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    if (only_over > 0 && ncount[i] <= only_over) return;
     const BoxInfo bx = g.boxes[s.box[i]];
     const T Hi = s.h[i];
     const T H2 = Hi * Hi;
@@ -1241,7 +1229,15 @@ template <typename T>
 cudaError_t run_build_lists(Ctx& c) {
     c.launches += 1;
     k_lists<T><<<blocks(c.N, 128), 128, 0, c.stream>>>(c.N, sorted_view<T>(c), grid_of(c), kparams(c),
-                                                        c.nbr, c.ncount, c.status);
+                                                        c.nbr, c.ncount, c.status, 0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t run_lists_over(Ctx& c, int kept) {
+    c.launches += 1;
+    k_lists<T><<<blocks(c.N, 128), 128, 0, c.stream>>>(c.N, sorted_view<T>(c), grid_of(c), kparams(c),
+                                                        c.nbr, c.ncount, c.status, kept);
     return cudaGetLastError();
 }
 
@@ -1422,6 +1418,7 @@ cudaError_t run_get_neighbours(Ctx& c, int32_t* count_out, int64_t* ids_out, int
     template cudaError_t run_density<T>(Ctx&, const int*, const int*, int);                    \
     template cudaError_t run_density_given<T>(Ctx&);                                            \
     template cudaError_t run_build_lists<T>(Ctx&);                                              \
+    template cudaError_t run_lists_over<T>(Ctx&, int);                                          \
     template cudaError_t run_reverse<T>(Ctx&);                                                  \
     template cudaError_t run_prim<T>(Ctx&);                                                     \
     template cudaError_t run_gradients<T>(Ctx&, bool, bool, const int*, const int*, int);      \

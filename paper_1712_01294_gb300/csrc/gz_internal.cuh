@@ -455,4 +455,98 @@ __device__ __forceinline__ void for_candidates_lanes(const Grid& g, const BoxInf
     }
 }
 
+// The candidates j != self with r^2 < R2 in the cells overlapping
+// [x - R, x + R] (every lane passes the same particle), handed to
+// emit(k, j) with k = 0, 1, ... in the order for_candidates visits them
+// (cells in its loop order, j ascending within a cell), so a list written
+// by a warp equals the one a thread's scan writes.  Cells are taken as
+// for_candidates_lanes takes them: small ranges candidate by candidate (a
+// ballot per 32 candidates places the hits), large ones 32 cells at a time
+// (each lane counts its cell's hits, an exclusive prefix across the warp
+// places them, the lane writes them).  Returns the number of hits.
+template <typename T, typename E>
+__device__ __forceinline__ int for_hits_lanes_ordered(const Grid& g, const BoxInfo& bx,
+                                                      const P4<T>* __restrict__ pos, int self, T xi, T yi,
+                                                      T zi, T R, T R2, int lane, E&& emit) {
+    const int nc = bx.nc;
+    const int2* __restrict__ cells = g.cells + bx.cell_off;
+    if (!(xi >= T(0) && xi <= T(1) && yi >= T(0) && yi <= T(1) && zi >= T(0) && zi <= T(1) &&
+          R >= T(0)))
+        return 0;
+    const bool full = !(R < T(0.5));
+    const T c3[3] = {xi, yi, zi};
+    int lo[3], hi[3];
+    bool wraps_all = full;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = full ? 0 : (int)floor((c3[a] - R) * (T)nc - T(1e-3));
+        hi[a] = full ? nc - 1 : (int)floor((c3[a] + R) * (T)nc + T(1e-3));
+        if (hi[a] - lo[a] + 1 >= nc) {
+            lo[a] = 0;
+            hi[a] = nc - 1;
+            wraps_all = true;
+        }
+    }
+    const T xim1 = xi - T(1), yim1 = yi - T(1), zim1 = zi - T(1);
+    const T cl = T(1) / (T)nc, R2m = R * R * T(1.0001);
+    auto gap = [&](int c, T v) { return wraps_all ? T(0) : max(max((T)c * cl - v, v - (T)(c + 1) * cl), T(0)); };
+    auto cell_range = [&](int cx, int cy, int cz, int2& se) {
+        const T gx = gap(cx, xi), gy = gap(cy, yi), gz = gap(cz, zi);
+        if (gx * gx + gy * gy + gz * gz > R2m) return false;
+        const int wx = cx < 0 ? cx + nc : (cx >= nc ? cx - nc : cx);
+        const int wy = cy < 0 ? cy + nc : (cy >= nc ? cy - nc : cy);
+        const int wz = cz < 0 ? cz + nc : (cz >= nc ? cz - nc : cz);
+        se = cells[(wz * nc + wy) * nc + wx];
+        return true;
+    };
+    auto hit = [&](int j) {
+        const P4<T> q = pos[j];
+        const T dx = mi_diff(q.x, xi, xim1), dy = mi_diff(q.y, yi, yim1), dz = mi_diff(q.z, zi, zim1);
+        return sep2(dx, dy, dz) < R2;
+    };
+    const unsigned full_mask = 0xffffffffu;
+    int base = 0;
+    const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
+    const int ncube = ex * ey * ez;
+    if (ncube >= 64) {
+        for (int f0 = 0; f0 < ncube; f0 += 32) {
+            const int f = f0 + lane;
+            int2 se = make_int2(0, 0);
+            bool ok = false;
+            if (f < ncube) ok = cell_range(lo[0] + f % ex, lo[1] + (f / ex) % ey, lo[2] + f / (ex * ey), se);
+            int cnt = 0;
+            if (ok)
+                for (int j = se.x; j < se.y; ++j)
+                    if (j != self && hit(j)) ++cnt;
+            int pre = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(full_mask, pre, o);
+                if (lane >= o) pre += y;
+            }
+            const int total = __shfl_sync(full_mask, pre, 31);
+            int k = base + pre - cnt;
+            if (ok)
+                for (int j = se.x; j < se.y; ++j)
+                    if (j != self && hit(j)) emit(k++, j);
+            base += total;
+        }
+    } else {
+        for (int cz = lo[2]; cz <= hi[2]; ++cz)
+            for (int cy = lo[1]; cy <= hi[1]; ++cy)
+                for (int cx = lo[0]; cx <= hi[0]; ++cx) {
+                    int2 se;
+                    if (!cell_range(cx, cy, cz, se)) continue;  // (the same for every lane)
+                    for (int j0 = se.x; j0 < se.y; j0 += 32) {
+                        const int j = j0 + lane;
+                        const bool h = j < se.y && j != self && hit(j);
+                        const unsigned m = __ballot_sync(full_mask, h);
+                        if (h) emit(base + __popc(m & ((1u << lane) - 1u)), j);
+                        base += __popc(m);
+                    }
+                }
+    }
+    return base;
+}
+
 }  // namespace gz

@@ -13,6 +13,10 @@ Sorted<T> sorted_view(Ctx& c);
 // n array as well.  Returns a CUDA error code.
 template <typename T>
 cudaError_t sort_and_bin(Ctx& c, const gz_particles& p, const void* n_in);
+// The part of sort_and_bin after the radix sort, from c.keys and c.vals as a
+// sort left them (a checkpoint's copy of them: the same start state).
+template <typename T>
+cudaError_t permute_and_bin(Ctx& c, const gz_particles& p, const void* n_in);
 
 // Writes sorted-order arrays back to caller order.
 template <typename T>
@@ -29,6 +33,10 @@ template <typename T>
 cudaError_t run_density_given(Ctx& c);
 template <typename T>
 cudaError_t run_build_lists(Ctx& c);
+// Rebuilds the lists of the particles with more than `kept` neighbours (the
+// others' lists and counts restored from a checkpoint).
+template <typename T>
+cudaError_t run_lists_over(Ctx& c, int kept);
 template <typename T>
 cudaError_t run_reverse(Ctx& c);
 template <typename T>

@@ -278,7 +278,7 @@ cudaError_t sort_and_bin(Ctx& c, const gz_particles& p, const void* n_in) {
     // the fewest passes of at most kMaxDigitBits bits, the bits spread evenly
     const int npass = (total_bits + kMaxDigitBits - 1) / kMaxDigitBits;
     const int bits = npass ? (total_bits + npass - 1) / npass : 0;
-    c.launches += 2 + 3 * npass;
+    c.launches += 1 + 3 * npass;  // (and k_permute, counted by permute_and_bin)
     unsigned *ki = c.keys, *vi = c.vals, *ko = c.keys_alt, *vo = c.vals_alt;
     for (int shift = 0; shift < total_bits; shift += bits) {
         const int pb = std::min(bits, total_bits - shift);
@@ -299,6 +299,15 @@ cudaError_t sort_and_bin(Ctx& c, const gz_particles& p, const void* n_in) {
         cudaMemcpyAsync(c.keys, ki, sizeof(unsigned) * N, cudaMemcpyDeviceToDevice, st);
         cudaMemcpyAsync(c.vals, vi, sizeof(unsigned) * N, cudaMemcpyDeviceToDevice, st);
     }
+    return permute_and_bin<T>(c, p, n_in);
+}
+
+template <typename T>
+cudaError_t permute_and_bin(Ctx& c, const gz_particles& p, const void* n_in) {
+    c.last_lim = nullptr;
+    const int N = c.N;
+    cudaStream_t st = c.stream;
+    c.launches += 1;
     cudaMemsetAsync(c.cells, 0, sizeof(int2) * (size_t)c.total_cells, st);
     Sorted<T> s = sorted_view<T>(c);
     k_permute<T><<<blocks(N, 256), 256, 0, st>>>(N, c.keys, c.vals, p, n_in, c.box_of, c.boxes,
@@ -307,6 +316,8 @@ cudaError_t sort_and_bin(Ctx& c, const gz_particles& p, const void* n_in) {
 }
 template cudaError_t sort_and_bin<float>(Ctx&, const gz_particles&, const void*);
 template cudaError_t sort_and_bin<double>(Ctx&, const gz_particles&, const void*);
+template cudaError_t permute_and_bin<float>(Ctx&, const gz_particles&, const void*);
+template cudaError_t permute_and_bin<double>(Ctx&, const gz_particles&, const void*);
 
 template <typename T>
 cudaError_t unpermute_T(Ctx& c, const T* src, T* dst, int rows) {

@@ -161,22 +161,27 @@ def test_step_adjoint_matches_autograd(prec):
     assert_all()
 
 
-@pytest.mark.parametrize("level", [0, 1])
+@pytest.mark.parametrize("level,ngb", [(0, 32.0), (0, 80.0), (1, 32.0), (1, 80.0), (2, 32.0),
+                                       (2, 80.0)])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_checkpointed_backward_equals_full_recompute(prec, level):
-    """gz_step_backward from a step checkpoint (saved rates, and at level 1
-    the gradient pass's outputs) with the converged H as the initial guess
-    equals the full recompute from the start state bit for bit: the
-    h-iteration accepts the converged H at once and the saved values are the
-    ones the recomputed passes would produce."""
+def test_checkpointed_backward_equals_full_recompute(prec, level, ngb):
+    """gz_step_backward from a step checkpoint (saved rates, H, n and the
+    kernel-derivative sums; at level 1 the gradient pass's outputs; at level
+    2 also the sorted order and the neighbour lists' first 64 slots) equals
+    the full recompute from the start state bit for bit: the saved values
+    are the ones the recomputed passes would produce.  With N_ngb = 80 many
+    particles outgrow the density pass's per-thread cache and are finished
+    by the warp-per-particle kernel, whose sums a rescan at H would not
+    reproduce (hence n and the sums are kept at every level), and most lists
+    are longer than the slots kept, and are rebuilt by a scan."""
     m = gz()
     q = cast_state(I.smooth_turbulence(12, seed=5), prec)
-    ctx = m.Context([q.N], m.default_params(precision=prec))
+    ctx = m.Context([q.N], m.default_params(precision=prec, ngb=ngb))
     start = device(q, prec)
     d = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in start.items()}
     ck = ctx.new_checkpoint(level)
     assert ck.numel() == ctx.checkpoint_bytes(level)
-    assert ctx.checkpoint_bytes(1) > ctx.checkpoint_bytes(0) >= 32 * q.N
+    assert ctx.checkpoint_bytes(2) > ctx.checkpoint_bytes(1) > ctx.checkpoint_bytes(0) >= 32 * q.N
     dtu = torch.zeros(1, dtype=torch.float64, device="cuda")
     ctx.step(d, 0.0, dtu, ck, level)
     dt = float(dtu.item())
