@@ -305,14 +305,25 @@ Ckpt ckpt_view(const Ctx& c, void* base, int level) {
 // the lists' first slots (groups of four slots across the particles:
 // the first slots/4 groups are one contiguous prefix).
 template <typename T>
-cudaError_t save_lists(Ctx& c, const Ckpt& k) {
+cudaError_t save_lists(Ctx& c, const Ckpt& k, cudaStream_t st) {
     const size_t N = (size_t)c.N;
-    cudaStream_t st = c.stream;
     cudaError_t e = cudaMemcpyAsync(k.keys, c.keys, 4 * N, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(k.vals, c.vals, 4 * N, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(k.ncount, c.ncount, 4 * N, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(k.nbr, c.nbr, 4 * N * (size_t)k.slots, cudaMemcpyDeviceToDevice, st);
+    return e;
+}
+
+// Makes the side stream wait for the work issued so far on the context's
+// stream (creating the stream and its events on first use).
+cudaError_t fork_side(Ctx& c) {
+    cudaError_t e = cudaSuccess;
+    if (!c.side) e = cudaStreamCreateWithFlags(&c.side, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !c.side_fork) e = cudaEventCreateWithFlags(&c.side_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !c.side_join) e = cudaEventCreateWithFlags(&c.side_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(c.side_fork, c.stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c.side, c.side_fork, 0);
     return e;
 }
 
@@ -460,6 +471,7 @@ gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
     Ctx& c = ctx->c;
     GradOutputs outs(c, ck);
     cudaError_t e;
+    bool forked = false;
     {
         Pass t(c, GZ_PASS_SORT);
         e = sort_and_bin<T>(c, *p, nullptr);
@@ -471,7 +483,17 @@ gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
         if (e == cudaSuccess && ck.H) e = cudaMemcpyAsync(ck.H, c.sh, bytes, cudaMemcpyDeviceToDevice, c.stream);
         if (e == cudaSuccess && ck.n) e = cudaMemcpyAsync(ck.n, c.sn, bytes, cudaMemcpyDeviceToDevice, c.stream);
         if (e == cudaSuccess && ck.sd) e = cudaMemcpyAsync(ck.sd, c.ssd, bytes, cudaMemcpyDeviceToDevice, c.stream);
-        if (e == cudaSuccess && ck.keys) e = save_lists<T>(c, ck);
+        // the sort's order and the lists are not written again in this
+        // step: their copies run on the side stream, beside the pair passes
+        if (e == cudaSuccess && ck.keys) {
+            e = fork_side(c);
+            if (e == cudaSuccess) {
+                forked = true;
+                e = save_lists<T>(c, ck, c.side);
+                const cudaError_t e2 = cudaEventRecord(c.side_join, c.side);
+                if (e == cudaSuccess) e = e2;
+            }
+        }
     }
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_PRIM);
@@ -493,6 +515,10 @@ gz_status do_step(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used
     if (e == cudaSuccess) {
         Pass t(c, GZ_PASS_UPDATE);
         e = run_update<T>(c, *p, ck.rates);
+    }
+    if (forked) {  // the step ends when the side stream's copies are done
+        const cudaError_t e2 = cudaStreamWaitEvent(c.stream, c.side_join, 0);
+        if (e == cudaSuccess) e = e2;
     }
     c.nbr_valid = 1;
     c.last_lim = ck.lim;
@@ -716,6 +742,12 @@ gz_status gz_set_subdomain(gz_ctx* ctx, int64_t n, int64_t n_owned, const uint8_
 gz_status gz_destroy(gz_ctx* ctx) {
     if (!ctx) return GZ_E_INVAL;
     cudaStreamSynchronize(ctx->c.stream);
+    if (ctx->c.side) {
+        cudaStreamSynchronize(ctx->c.side);
+        cudaStreamDestroy(ctx->c.side);
+    }
+    if (ctx->c.side_fork) cudaEventDestroy(ctx->c.side_fork);
+    if (ctx->c.side_join) cudaEventDestroy(ctx->c.side_join);
     for (auto& pe : ctx->c.pending) {
         cudaEventDestroy(pe.a);
         cudaEventDestroy(pe.b);

@@ -82,6 +82,10 @@ struct Ctx {
     int cbits;     // bits per axis of a cell coordinate
     int box_bits;  // bits of the box index in a key
     cudaStream_t stream;
+    // a second stream for the step checkpoint's list copies, which overlap
+    // the pair passes (created on the first checkpointing step)
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_fork = nullptr, side_join = nullptr;
     std::string err;
 
     // device buffers

@@ -210,6 +210,64 @@ def test_checkpointed_backward_equals_full_recompute(prec, level, ngb):
         assert abs(r[k].sum()) <= (1e-12 if prec == 0 else 1e-6) * np.abs(r[k]).sum(), k
 
 
+def _boxes(sizes):
+    """Smooth-turbulence boxes of the given sizes, concatenated box by box
+    (ids running on across the boxes)."""
+    parts, id0 = [], 0
+    for n, seed in sizes:
+        b = I.smooth_turbulence(n, seed=seed)
+        b.id += id0
+        id0 += b.N
+        parts.append(b)
+    cat = {k: np.concatenate([getattr(b, k) for b in parts]) for k in I.FIELDS + ("id",)}
+    return I.Particles(*(cat[k] for k in I.FIELDS + ("id",)),
+                       counts=np.array([b.N for b in parts], dtype=np.int64)), parts
+
+
+def _fixed_dt_backward(m, q, counts, prec, dt, gend, level):
+    ctx = m.Context(counts, m.default_params(precision=prec))
+    start = device(q, prec)
+    d = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in start.items()}
+    ck = ctx.new_checkpoint(level)
+    dtu = torch.zeros(len(counts), dtype=torch.float64, device="cuda")
+    ctx.step(d, dt, dtu, ck, level)
+    assert bool((dtu == dt).all())
+    T = d["x"].dtype
+    g = {k: torch.zeros(q.N, dtype=T, device="cuda") for k in KEYS}
+    st = dict(start)
+    st["h"] = d["h"].clone()
+    ctx.step_backward(st, dt, {k: v.to(T) for k, v in gend.items()}, g, ck, level)
+    st_ = ctx.status(reset=True)
+    assert st_["ok"], st_
+    ctx.close()
+    return d, g
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batched_backward_equals_each_box_alone(prec):
+    """A batched context of three uneven boxes stepped with one fixed dt: the
+    backward from its level-2 checkpoint equals, box by box, the backward of
+    a context holding that box alone, bit for bit (each pass treats the boxes
+    independently; the sort keeps each box's particles in their own order)."""
+    m = gz()
+    q, parts = _boxes([(8, 21), (11, 22), (9, 23)])
+    counts = [b.N for b in parts]
+    q = cast_state(q, prec)
+    dt = 2e-3
+    rng = np.random.default_rng(17)
+    gend = {k: torch.as_tensor(rng.normal(size=q.N), dtype=torch.float64).cuda() for k in OUTK}
+    d, g = _fixed_dt_backward(m, q, counts, prec, dt, gend, m.GZ_CKPT_LISTS)
+    off = np.concatenate([[0], np.cumsum(counts)])
+    for b, pb in enumerate(parts):
+        sl = slice(int(off[b]), int(off[b + 1]))
+        db, gb = _fixed_dt_backward(m, cast_state(pb, prec), [pb.N], prec, dt,
+                                    {k: v[sl] for k, v in gend.items()}, m.GZ_CKPT_LISTS)
+        for k in ("x", "vx", "u", "h"):
+            assert torch.equal(db[k], d[k][sl]), (b, k)
+        for k in KEYS:
+            assert torch.equal(gb[k], g[k][sl]), (b, k)
+
+
 def region_ke(state, mask):
     v2 = state["vx"] ** 2 + state["vy"] ** 2 + state["vz"] ** 2
     return (0.5 * state["m"].to(torch.float64) * v2.to(torch.float64) * mask).sum()
