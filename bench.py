@@ -297,6 +297,12 @@ def run_ours(a, world, rank, local):
         nc64 = nbr_counts.to(torch.int64)
         work = {"density_eval_neighbours": int((it64 * nc64).sum()), "neighbours": int(nc64.sum()),
                 "mean_iterations": round(float(it64.double().mean()), 3)}
+        # the cell scan's candidates per true neighbour (overhead the density
+        # pass's algorithmic FLOP count leaves out)
+        sc = ctx.scan_stats()
+        work["scan_candidates_per_particle"] = round(sc["candidates"] / p.N, 2)
+        work["scan_candidates_per_neighbour"] = round(sc["candidates"] / max(sc["neighbours"], 1), 3)
+        work["cached_per_particle"] = round(sc["within_cache_radius"] / p.N, 2)
         del dcopy
         st = ctx.status(reset=True)
         if not st["ok"]:
@@ -582,6 +588,31 @@ def measure_extras(a, ctx, d, dtu, stream, prec, p, fp64_peak=None):
             return out
         if a.extras in ("all", "hier"):
             out["hierarchical"] = measure_hier(a, stream, prec)
+        if a.extras == "all":
+            # the other configured workloads at the same precision, one box
+            # each: 10 steps from the initial state, after 2 steps on a copy
+            cfg = {}
+            for name in ("sod32", "sedov64", "kh64"):
+                q = I.WORKLOADS[name]()
+                c2 = gz.Context([q.N], gz.default_params(precision=prec), stream=stream)
+                warm = gz.to_device(q, prec)
+                for _ in range(2):
+                    c2.step(warm)
+                dd = gz.to_device(q, prec)
+                t2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+                e0, e1 = ev(), ev()
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(10):
+                    c2.step(dd, 0.0, t2)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / 10
+                cfg[name] = {"particles": q.N, "value": round(q.N / (ms / 1e3), 1), "unit": UNIT,
+                             "ms_per_step": round(ms, 4), "steps": 10,
+                             "status_ok": c2.status(reset=True)["ok"]}
+                c2.close()
+            out["configs"] = cfg
         if a.extras == "hier":
             return out
         # the same box further on: 20 more steps from the state the timed loop
@@ -865,6 +896,18 @@ def main():
             line["cpu_baseline_1thread"] = {"value": round(r1, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
                                             "sample": f"one oracle step of a cubic sub-box of {ns1} particles "
                                                       f"of the same state, {secs1:.1f} s"}
+            if "configs" in line:
+                # the oracle on the other configured workloads: one full step
+                # from each initial state on all host cores
+                from paper_1712_01294_gb300 import inputs as I
+                cb = {}
+                for name, g in line["configs"].items():
+                    rc, secsc, nsc, _ = cpu_sample_rate(I.WORKLOADS[name](), sample_frac=1.0)
+                    cb[name] = {"value": round(rc, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"one full oracle step of the {nsc}-particle initial state, "
+                                          f"{secsc:.1f} s",
+                                "gpu_over_oracle": round(g["value"] / rc, 1)}
+                line["cpu_baseline_configs"] = cb
         print(json.dumps(line), flush=True)
     return 0
 

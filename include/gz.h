@@ -395,6 +395,16 @@ gz_status gz_get_info(gz_ctx* ctx, int64_t* info, int32_t n);
  * (device reduction; synchronises the stream). */
 gz_status gz_pair_count(gz_ctx* ctx, int64_t* ordered_pairs);
 
+/* Work of the neighbour search (a diagnostic; the paper has no counterpart):
+ * over the particles of the last density pass, at their converged H and the
+ * positions that pass sorted, out3[0] = candidates a cell scan of radius
+ * 1.05 H tests (the density cache's radius; the cells whose nearest point
+ * lies beyond it are skipped, as in the density pass), out3[1] = those
+ * within 1.05 H, out3[2] = those within H (the neighbours, O3).  out3 is a
+ * host array of 3.  One extra kernel; synchronises the stream.  Errors:
+ * GZ_E_INVAL (null arguments, no density pass yet), GZ_E_CUDA. */
+gz_status gz_scan_stats(gz_ctx* ctx, int64_t* out3);
+
 /* enable != 0: record CUDA events on the context stream around every pass of
  * subsequent calls (a few microseconds per pass).  gz_profile_read
  * synchronises and returns the accumulated milliseconds and invocation

@@ -99,6 +99,7 @@ def load_library(build_if_missing: bool = True):
             "gz_version": (C.c_char_p, []),
             "gz_get_info": (st, [vp, vp, i32]),
             "gz_pair_count": (st, [vp, vp]),
+            "gz_scan_stats": (st, [vp, vp]),
             "gz_profile_enable": (st, [vp, i32]),
             "gz_profile_read": (st, [vp, vp, vp, i32]),
             "gz_measure_alu": (st, [i32, vp, vp]),
@@ -399,6 +400,13 @@ class Context:
         v = C.c_int64()
         self._check(self.lib.gz_pair_count(self.h, C.byref(v)), "gz_pair_count")
         return int(v.value)
+
+    def scan_stats(self) -> dict:
+        """gz_scan_stats: candidates a 1.05 H cell scan tests, those within
+        1.05 H and those within H, summed over the last density pass."""
+        v = (C.c_int64 * 3)()
+        self._check(self.lib.gz_scan_stats(self.h, C.cast(v, C.c_void_p)), "gz_scan_stats")
+        return dict(zip(("candidates", "within_cache_radius", "neighbours"), (int(x) for x in v)))
 
     def profile(self, enable: bool = True):
         """gz_profile_enable: CUDA-event timing of every pass."""

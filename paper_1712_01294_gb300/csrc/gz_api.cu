@@ -648,7 +648,7 @@ gz_status create_ctx(const gz_params* params, int32_t nboxes, const int64_t* cou
         {(void**)&c.dt_use, 8 * (size_t)nboxes},
         {(void**)&c.box_hits, 4 * (size_t)nboxes},
         {(void**)&c.status, sizeof(DevStatus)},
-        {(void**)&c.pairs_dev, sizeof(long long)},
+        {(void**)&c.pairs_dev, 3 * sizeof(long long)},
     };
     size_t total = 0;
     for (auto& it : items) total += (it.bytes + 255) & ~(size_t)255;
@@ -1005,6 +1005,19 @@ gz_status gz_pair_count(gz_ctx* ctx, int64_t* ordered_pairs) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
     if (e != cudaSuccess) return fail(ctx, GZ_E_CUDA, std::string("gz_pair_count: ") + cudaGetErrorString(e));
     *ordered_pairs = h;
+    return GZ_OK;
+}
+
+gz_status gz_scan_stats(gz_ctx* ctx, int64_t* out3) {
+    if (!ctx || !out3) return GZ_E_INVAL;
+    Ctx& c = ctx->c;
+    if (!c.nbr_valid) return fail(ctx, GZ_E_INVAL, "gz_scan_stats: no density pass yet");
+    long long h[3] = {0, 0, 0};
+    cudaError_t e = GZ_DISPATCH(run_scan_stats<float>(c, c.pairs_dev), run_scan_stats<double>(c, c.pairs_dev));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, c.pairs_dev, sizeof(h), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return fail(ctx, GZ_E_CUDA, std::string("gz_scan_stats: ") + cudaGetErrorString(e));
+    for (int k = 0; k < 3; ++k) out3[k] = h[k];
     return GZ_OK;
 }
 

@@ -1155,6 +1155,34 @@ __global__ void k_pairs(int N, const int* __restrict__ ncount, const int* __rest
     if ((threadIdx.x & 31) == 0) atomicAdd((unsigned long long*)out, (unsigned long long)v);
 }
 
+// Work of the cell scan at the converged H: per particle, the candidates a
+// scan of radius 1.05 H (the density cache's) tests, those inside 1.05 H and
+// those inside H; summed over the particles (out[0..2]).
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_scan_stats(int N, Sorted<T> s, Grid g, KParams p, unsigned long long* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v[3] = {0, 0, 0};
+    if (i < N) {
+        const BoxInfo bx = g.boxes[s.box[i]];
+        const P4<T> me = s.pos[i];
+        const T Ht = s.h[i];
+        const T R = dens_cache_radius<T>(Ht, p);
+        const T R2 = R * R, H2 = Ht * Ht;
+        for_candidates<T>(g, bx, s.pos, i, me.x, me.y, me.z, R, [&](int, T, T, T, T r2) {
+            if (r2 < T(1e29)) ++v[0];  // (slots past a cell's range read a far point)
+            if (r2 < R2) ++v[1];
+            if (r2 < H2) ++v[2];
+        });
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        unsigned long long x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(out + k, x);
+    }
+}
+
 }  // namespace
 
 cudaError_t run_pair_count(Ctx& c, long long* out_dev) {
@@ -1188,6 +1216,18 @@ static Grid grid_of(const Ctx& c) {
     g.cells = c.cells;
     return g;
 }
+
+template <typename T>
+cudaError_t run_scan_stats(Ctx& c, long long* out_dev) {
+    c.launches += 1;
+    cudaError_t e = cudaMemsetAsync(out_dev, 0, 3 * sizeof(long long), c.stream);
+    if (e != cudaSuccess) return e;
+    k_scan_stats<T><<<blocks(c.N, 128), 128, 0, c.stream>>>(c.N, sorted_view<T>(c), grid_of(c), kparams(c),
+                                                             (unsigned long long*)out_dev);
+    return cudaGetLastError();
+}
+template cudaError_t run_scan_stats<float>(Ctx&, long long*);
+template cudaError_t run_scan_stats<double>(Ctx&, long long*);
 
 template <typename T>
 cudaError_t run_density(Ctx& c, const int* list, const int* nlist, int n) {

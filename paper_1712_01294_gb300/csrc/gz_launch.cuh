@@ -69,6 +69,8 @@ cudaError_t run_get_neighbours(Ctx& c, int32_t* count_out, int64_t* ids_out, int
 cudaError_t run_get_limiters(Ctx& c, const int* lim, int64_t* out);
 
 cudaError_t run_pair_count(Ctx& c, long long* out_dev);
+template <typename T>
+cudaError_t run_scan_stats(Ctx& c, long long* out_dev);
 
 // Adjoint passes.
 cudaError_t ensure_adjoint_scratch(Ctx& c);
