@@ -387,14 +387,18 @@ __device__ __forceinline__ void for_candidates(const Grid& g, const BoxInfo& bx,
     }
 }
 
+constexpr int kLaneCells = 16;
+
 // Warp-cooperative candidate scan for one particle per warp (every lane
 // passes the same particle): each lane calls fn(j, dx, dy, dz, r2) for its
 // share of the candidates j != self in the cells overlapping [x - R, x + R]
 // (cells whose nearest point lies beyond R skipped, as in for_candidates).
-// Small ranges (under 64 cells) are shared candidate by candidate (the lanes
-// take start + lane, start + 32 + lane, ... of every cell); large ones cell by
-// cell (lane l takes cells l, l + 32, ... of the range, in row order), which
-// keeps lanes busy where a wide support holds many sparse cells.  Which lane
+// Ranges of under kLaneCells cells are shared candidate by candidate (the
+// lanes take start + lane, start + 32 + lane, ... of every cell); larger ones
+// cell by cell (lane l takes cells l, l + 32, ... of the range, in row
+// order), which keeps lanes busy where a support holds many cells and puts
+// the cells' range and candidate loads in flight together instead of one
+// cell after another.  Which lane
 // sees which candidate depends only on the particle, so per-lane sums
 // combined in a fixed order are deterministic.  Offsets from mi_diff.
 template <typename T, typename F>
@@ -439,7 +443,7 @@ __device__ __forceinline__ void for_candidates_lanes(const Grid& g, const BoxInf
     };
     const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
     const int ncube = ex * ey * ez;
-    if (ncube >= 64) {
+    if (ncube >= kLaneCells) {
         for (int f = lane; f < ncube; f += 32) {
             const int cx = lo[0] + f % ex, cy = lo[1] + (f / ex) % ey, cz = lo[2] + f / (ex * ey);
             int2 se;
@@ -512,7 +516,7 @@ __device__ __forceinline__ int for_hits_lanes_ordered(const Grid& g, const BoxIn
     int base = 0;
     const int ex = hi[0] - lo[0] + 1, ey = hi[1] - lo[1] + 1, ez = hi[2] - lo[2] + 1;
     const int ncube = ex * ey * ez;
-    if (ncube >= 64) {
+    if (ncube >= kLaneCells) {
         for (int f0 = 0; f0 < ncube; f0 += 32) {
             const int f = f0 + lane;
             int2 se = make_int2(0, 0);
