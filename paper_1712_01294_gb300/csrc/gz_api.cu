@@ -300,6 +300,29 @@ Ckpt ckpt_view(const Ctx& c, void* base, int level) {
     return k;
 }
 
+// The groups of four list slots (group g of particle i at uint4 g N + i)
+// among the first `groups` that hold part of particle i's list, from src to
+// dst; the groups past a particle's count are not copied (no pass reads
+// them).
+__global__ void k_copy_lists(int N, int groups, const int* __restrict__ ncount, const uint4* __restrict__ src,
+                             uint4* __restrict__ dst) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)N * groups) return;
+    const int g = (int)(idx / N);
+    const int i = (int)(idx - (long long)g * N);
+    if (4 * g < ncount[i]) dst[idx] = src[idx];
+}
+
+cudaError_t copy_lists(Ctx& c, const int* ncount, const unsigned* src, unsigned* dst, int slots,
+                       cudaStream_t st) {
+    const long long n = (long long)c.N * (slots / 4);
+    if (n == 0) return cudaSuccess;
+    c.launches += 1;
+    k_copy_lists<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c.N, slots / 4, ncount, (const uint4*)src,
+                                                              (uint4*)dst);
+    return cudaGetLastError();
+}
+
 // What the sort and the density pass leave that the backward pass would
 // otherwise recompute: the sort's keys and order, the neighbour counts and
 // the lists' first slots (groups of four slots across the particles:
@@ -310,8 +333,7 @@ cudaError_t save_lists(Ctx& c, const Ckpt& k, cudaStream_t st) {
     cudaError_t e = cudaMemcpyAsync(k.keys, c.keys, 4 * N, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(k.vals, c.vals, 4 * N, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(k.ncount, c.ncount, 4 * N, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(k.nbr, c.nbr, 4 * N * (size_t)k.slots, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = copy_lists(c, c.ncount, c.nbr, k.nbr, k.slots, st);
     return e;
 }
 
@@ -342,8 +364,7 @@ cudaError_t restore_lists(Ctx& c, const gz_particles& p, const Ckpt& k) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(c.sn, k.n, sizeof(T) * N, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c.ssd, k.sd, sizeof(T) * N, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c.ncount, k.ncount, 4 * N, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c.nbr, k.nbr, 4 * N * (size_t)k.slots, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = copy_lists(c, c.ncount, k.nbr, c.nbr, k.slots, st);
     if (e == cudaSuccess && k.slots < c.cap) e = run_lists_over<T>(c, k.slots);
     return e;
 }
