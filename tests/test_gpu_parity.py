@@ -354,6 +354,34 @@ def test_density_reads_only_positions_h_and_ids():
     assert torch.equal(n1, n2) and torch.equal(it1, it2) and torch.equal(ref["h"], d["h"])
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_planar_particles_make_E_singular_as_in_the_oracle(prec):
+    """The method's degenerate case: every particle on the plane z = 1/2, so
+    no E_i has a z-extent.  Given H and n, the gradient pass flags every
+    particle singular (status bit and counter) and returns B = 0 and zero
+    gradients, as the oracle does for the same inputs."""
+    m = gz()
+    import torch
+    p = I.sod(8)
+    p.z[:] = 0.5
+    p.x = (p.x * 4) % 1.0
+    q = cast_state(p, prec)
+    s = ostate(q)
+    H = np.full(q.N, 0.2)
+    n = np.full(q.N, float(q.N))
+    cnt = O.Counters()
+    ref = O.gradients(s, H, n, O.params(), counters=cnt)
+    assert cnt.singular == q.N
+    ctx = ctx_for(q.N, prec)
+    d = device(q, prec, H=H)
+    T = d["x"].dtype
+    grad, B = ctx.gradients(d, torch.as_tensor(n, dtype=T).cuda())
+    st = ctx.status(reset=True)
+    assert "singular" in st["bits"] and st["counters"]["singular"] == q.N
+    assert bool((B == 0).all()) and bool((grad == 0).all())
+    assert np.all(ref["B"] == 0.0) and np.all(ref["grad"] == 0.0)
+
+
 def test_invalid_positions_are_flagged():
     m = gz()
     q = cast_state(I.sod(8), m.GZ_MIXED32)
