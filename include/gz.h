@@ -344,7 +344,12 @@ gz_status gz_checkpoint_bytes(gz_ctx* ctx, int32_t level, int64_t* bytes);
 gz_status gz_checkpoint_limiters(gz_ctx* ctx, const void* ckpt, int64_t* ids_out);
 
 /* gz_step (same arguments and effect) that also fills the checkpoint ckpt
- * at the given level.  Host synchronisation: none. */
+ * at the given level.  At GZ_CKPT_LISTS the list copies run on a second
+ * stream of the context (created, with two events, on the first such call;
+ * released by gz_destroy), forked from and joined back to the context's
+ * stream by events within the call, so work issued on the context's stream
+ * after the call sees a complete checkpoint.  Make the first such call
+ * outside any stream capture.  Host synchronisation: none. */
 gz_status gz_step_checkpoint(gz_ctx* ctx, gz_particles* p, double dt_fixed, double* dt_used_dev,
                              void* ckpt, int32_t level);
 
