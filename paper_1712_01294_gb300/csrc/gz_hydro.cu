@@ -481,7 +481,7 @@ __global__ void k_reverse(int N, Sorted<T> s, KParams p, const unsigned* __restr
     const int cnt = min(ncount[i], p.cap);
     const unsigned* L = nbr + 4 * (size_t)i;
     for (int k0 = 0; k0 < cnt; k0 += 4) {
-        const uint4 jj = col4(L, k0, N);
+        const uint4 jj = col4_once(L, k0, N);
         const unsigned js[4] = {jj.x, jj.y, jj.z, jj.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -935,7 +935,7 @@ __global__ void __launch_bounds__(kFluxBlock)
         const unsigned* L = list == 0 ? nbr + 4 * (size_t)i : rnbr + 4 * (size_t)i;
         const int cnt = list == 0 ? min(ncount[i], p.cap) : min(rcount[i], p.rcap);
         for (int k0 = 0; k0 < cnt; k0 += 4) {
-            const uint4 jj = col4(L, k0, N);
+            const uint4 jj = col4_once(L, k0, N);
             const unsigned js[4] = {jj.x, jj.y, jj.z, jj.w};
 #pragma unroll
             for (int u = 0; u < 4; ++u) {

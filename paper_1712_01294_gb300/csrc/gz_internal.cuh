@@ -267,6 +267,16 @@ __device__ __forceinline__ size_t lslot(int k, int i, int N) { return 4 * (size_
 __device__ __forceinline__ uint4 col4(const unsigned* __restrict__ L, int k0, int N) {
     return *reinterpret_cast<const uint4*>(L + lcol(k0, N));
 }
+// The same slots for a pass that reads each list once: not kept in L1, which
+// stays for the records and positions the pass gathers (a pass that reads
+// its lists twice, like the gradient pass, keeps col4).
+__device__ __forceinline__ uint4 col4_once(const unsigned* __restrict__ L, int k0, int N) {
+    uint4 r;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(L + lcol(k0, N)));
+    return r;
+}
 
 // ordered-integer image of a non-negative double (for atomicMin)
 __device__ __forceinline__ unsigned long long dbits(double v) {
