@@ -140,13 +140,14 @@ __device__ __forceinline__ void load_row32(const double* __restrict__ p, double*
 
 // n values (a multiple of 32 bytes) to 32-byte-aligned global memory with
 // 32-byte vector stores: a per-particle row written by its thread fills
-// whole sectors instead of one 4-byte piece per store.
+// whole sectors instead of one 4-byte piece per store.  The rows are read
+// by later passes, not by the writing one: not allocated in L1.
 template <int n>
 __device__ __forceinline__ void store_row32(float* p, const float* v) {
     static_assert(n % 8 == 0, "rows of whole 32-byte vectors");
 #pragma unroll
     for (int k = 0; k < n / 8; ++k)
-        asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+        asm volatile("st.global.L1::no_allocate.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
                      :
                      : "l"(p + 8 * k), "f"(v[8 * k]), "f"(v[8 * k + 1]), "f"(v[8 * k + 2]), "f"(v[8 * k + 3]),
                        "f"(v[8 * k + 4]), "f"(v[8 * k + 5]), "f"(v[8 * k + 6]), "f"(v[8 * k + 7])
@@ -157,7 +158,7 @@ __device__ __forceinline__ void store_row32(double* p, const double* v) {
     static_assert(n % 4 == 0, "rows of whole 32-byte vectors");
 #pragma unroll
     for (int k = 0; k < n / 4; ++k)
-        asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};"
+        asm volatile("st.global.L1::no_allocate.v4.f64 [%0], {%1,%2,%3,%4};"
                      :
                      : "l"(p + 4 * k), "d"(v[4 * k]), "d"(v[4 * k + 1]), "d"(v[4 * k + 2]), "d"(v[4 * k + 3])
                      : "memory");

@@ -77,7 +77,7 @@ __device__ __noinline__ void dens_eval_cells(const Grid& g, const BoxInfo& bx, c
             dens_terms(q, w, qdw);
             sw.add(w);
             sd += qdw;
-            if (c < cap) col[lcol(c, N)] = (unsigned)j;
+            if (c < cap) store_slot(col + lcol(c, N), (unsigned)j);
             ++c;
         }
     });
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kDensBlock, sizeof(T) == 4 ? 10 : 1)
         int c = 0;
         for (int k = 0; k < ncache; ++k) {
             if (c_r2[k][t] < H2) {
-                if (c < p.cap) nbr[lslot(c, i, N)] = c_j[k][t];
+                if (c < p.cap) store_slot(nbr + lslot(c, i, N), c_j[k][t]);
                 ++c;
             }
         }
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kWarpDensBlock)
            // order of k_density, k_dens_given and k_lists)
             const T Ht = (T)Hev;
             for_hits_lanes_ordered<T>(g, bx, s.pos, i, xi, yi, zi, Ht, Ht * Ht, lane, [&](int k, int j) {
-                if (k < p.cap) nbr[lslot(k, i, N)] = (unsigned)j;
+                if (k < p.cap) store_slot(nbr + lslot(k, i, N), (unsigned)j);
             });
         }
         if (lane == 0) {
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(128)
     for_candidates<T>(g, bx, s.pos, i, me.x, me.y, me.z, Hi,
                       [&](int j, T, T, T, T r2) {
                           if (r2 < H2) {
-                              if (c < p.cap) nbr[lslot(c, i, N)] = (unsigned)j;
+                              if (c < p.cap) store_slot(nbr + lslot(c, i, N), (unsigned)j);
                               ++c;
                           }
                       });
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(128)
                               dens_terms(q, w, qdw);
                               sw.add(w);
                               sd += qdw;
-                              if (c < p.cap) nbr[lslot(c, i, N)] = (unsigned)j;
+                              if (c < p.cap) store_slot(nbr + lslot(c, i, N), (unsigned)j);
                               ++c;
                           }
                       });

@@ -278,6 +278,12 @@ __device__ __forceinline__ uint4 col4_once(const unsigned* __restrict__ L, int k
     return r;
 }
 
+// A list slot written by the pass that builds the list: not allocated in
+// L1, which stays for the candidates' positions the pass is scanning.
+__device__ __forceinline__ void store_slot(unsigned* p, unsigned v) {
+    asm volatile("st.global.L1::no_allocate.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // ordered-integer image of a non-negative double (for atomicMin)
 __device__ __forceinline__ unsigned long long dbits(double v) {
     return (unsigned long long)__double_as_longlong(v);
