@@ -50,7 +50,7 @@ FLOPS_PER_GRAD_PARTICLE = 60    # gradient pass, per particle
 # summarised in TRAFFIC_SOURCE (64^3 turbulence, one launch each), scaled to a
 # launch by the work units of the run; to be emptied whenever one of these
 # kernels changes after that capture
-TRAFFIC_PER_UNIT = {"density": 0.454, "gradients": 7.71, "fluxes": 20.45}
+TRAFFIC_PER_UNIT = {"density": 0.455, "gradients": 7.75, "fluxes": 20.41}
 TRAFFIC_SOURCE = "profiles/kernels_turb64_fp32.md (64^3 capture, scaled by work units)"
 FP32_LANES = 128  # FP32 lanes per SM (Blackwell)
 
